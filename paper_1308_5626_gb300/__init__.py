@@ -1,0 +1,13 @@
+"""GB300-native PSP-GMRES: one implicit-Euler step (I - dt*L) u^{n+1} = u^n solved by
+matrix-free restarted GMRES with the progressive statistical banded preconditioner
+(Ghasemi & Taylor, arXiv:1308.5626, Algorithms 1 and 2).
+
+The compute path lives in ``libpsp.so`` (hand-written CUDA for sm_103a behind a C ABI
+declared in ``include/psp.h``).  ``paper_1308_5626_gb300.psp`` is the thin ctypes
+binding; ``paper_1308_5626_gb300.inputs`` holds the seeded synthetic workloads.
+
+Importing this package loads nothing: the shared library is opened on first use of
+``paper_1308_5626_gb300.psp``.
+"""
+
+__all__ = ["inputs", "psp", "build"]
