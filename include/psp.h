@@ -1,0 +1,184 @@
+/*
+ * psp.h -- C ABI of libpsp, a GB300 (sm_103a) implementation of PSP-GMRES
+ * (Ghasemi & Taylor, "A Progressive Statistical Method for Preconditioning Matrix-Free
+ * Solution of High-Order Discretization of Linear Time-Dependent Problems",
+ * arXiv:1308.5626).
+ *
+ * One call of psp_step solves the implicit-Euler system of Eq. 4,
+ *     A u^{n+1} = u^n,   A = I - dt L,
+ * where L is the high-order finite-difference operator of Eqs. 1-2 on a periodic grid,
+ * by the restarted, right-preconditioned, matrix-free GMRES of Algorithm 1.  Every
+ * matvec pair (x, A x) is kept as a history; after the step the banded preconditioner N
+ * is fitted to that history row by row (Algorithm 2, MREP) and preconditions the next
+ * step.
+ *
+ * Conventions shared by every entry point:
+ *  - Vectors are flattened grids with x fastest (index = ix + nx*(iy + ny*iz)).
+ *  - Pointers named *_host are host memory; every other array pointer is DEVICE memory
+ *    owned by the caller (e.g. a torch tensor's data_ptr).  The library never frees
+ *    caller memory and keeps no pointer to it after the call returns.
+ *  - Band storage of an n x n banded matrix with half-width b is row-major
+ *    n x (2b+1) doubles: band[i*(2b+1) + p] = N(i, i + p - b).  Entries whose column
+ *    falls outside [0, n) are ignored on input and written as 0 on output.
+ *  - The library owns its workspace (Krylov basis, history ring, Hessenberg data, band
+ *    factors) and allocates all of it in psp_create; no other call allocates device
+ *    memory.
+ *  - All device work is enqueued on the stream given to psp_create.  psp_step,
+ *    psp_fit_band*, psp_set_band and psp_step_host synchronise that stream before they
+ *    return; the other calls are asynchronous.
+ *  - No exception crosses the ABI.  A failing call returns a status other than PSP_OK
+ *    and leaves a thread-local message for psp_last_error().
+ *  - A handle must not be used by two host threads at once.
+ */
+#ifndef PSP_H
+#define PSP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct psp_ctx *psp_handle;
+
+typedef enum {
+  PSP_OK = 0,
+  PSP_ERR_ARG = 1,     /* invalid argument; nothing was enqueued */
+  PSP_ERR_CUDA = 2,    /* a CUDA runtime call failed */
+  PSP_ERR_OOM = 3,     /* device allocation failed (psp_create only) */
+  PSP_ERR_NOCONV = 4,  /* max_restarts reached; the output holds the last iterate */
+  PSP_ERR_NUMERIC = 5, /* NaN/Inf in a residual norm, or a singular band factor */
+  PSP_ERR_DEVICE = 6   /* the device reported an internal error flag */
+} psp_status;
+
+enum { PSP_FP64 = 0, PSP_MIXED = 1 };
+
+/* psp_step_info.flags bits */
+#define PSP_FLAG_SINGULAR_FIT 0x1       /* the last fit had degenerate rows (identity rows written) */
+#define PSP_FLAG_CANDIDATE_TRIED 0x2    /* this step tried a freshly fitted N on its first cycle */
+#define PSP_FLAG_CANDIDATE_ACCEPTED 0x4 /* ... and adopted it */
+#define PSP_FLAG_FACTOR_FAILED 0x8      /* a fitted N had a zero pivot and was dropped */
+#define PSP_FLAG_BREAKDOWN 0x10         /* an Arnoldi breakdown ended a cycle */
+
+/* Periodic grid of Eq. 1: ndim in {1,2,3}, n[d] points on [0, length[d]), h = length/n. */
+typedef struct {
+  int ndim;
+  int64_t n[3];
+  double length[3];
+} psp_grid;
+
+/* One term alpha * d^k u / dx_dir^k of the operator L (Eq. 1); k in 1..4. */
+typedef struct {
+  int k;
+  int dir;
+  double alpha;
+} psp_term;
+
+typedef struct {
+  int precision;     /* PSP_FP64 (default): every vector in FP64.  PSP_MIXED: Krylov
+                        vectors, history, stencil and band solve in FP32 with FP32
+                        accumulation; Hessenberg/Givens, band fit and the per-restart true
+                        residual and solution update in FP64. */
+  int intercept;     /* 1 (default): Algorithm 2's design row of ones; 0: without it */
+  int max_restarts;  /* n_r of Algorithm 1 (default 200) */
+  int max_hist_cols; /* history ring length M_max (default 2(m+1)) */
+  double inner_tol;  /* PSP_MIXED: a cycle ends once R(k) <= inner_tol * ||r_restart||
+                        (default 1e-5); the step ends on the FP64 true residual */
+  int accept_rule;   /* 1 (default): a fitted N is adopted only if it converges at least
+                        as fast on the next step's first cycle; 0: always adopt */
+} psp_opts;
+
+typedef struct {
+  int iters;         /* Arnoldi iterations (preconditioned matvecs) of the step */
+  int cycles;        /* restart cycles */
+  int status;        /* psp_status of the step */
+  int flags;         /* PSP_FLAG_* */
+  double rel_res;    /* PSP_FP64: Givens estimate R(k)/||u^n|| at exit;
+                        PSP_MIXED: FP64 true residual ||u^n - A u^{n+1}|| / ||u^n|| */
+  int hist_cols;     /* valid history columns after the step */
+  int singular_rows; /* degenerate rows in the fit made after the step */
+} psp_step_info;
+
+/* Fill *opts with the defaults listed above.  Returns PSP_ERR_ARG for NULL. */
+psp_status psp_default_opts(psp_opts *opts);
+
+/*
+ * Create a solver for A = I - dt L on `grid`, L = sum over `terms` of
+ * alpha * h^-k * (central difference of accuracy `order`) (Eqs. 1-2; order in
+ * {2,4,6,8}), band half-width b in 1..4 (the paper's d of Algorithm 2), restart length
+ * m in 1..128 (n_A of Algorithm 1).  `opts` may be NULL (defaults).  `cuda_stream` is a
+ * cudaStream_t (NULL = legacy default stream).  Every direction needs n[d] >= 2r+1 for
+ * the widest stencil radius r and the grid needs at least 2b+1 points.  Allocates all
+ * workspace on the current device; PSP_ERR_OOM if it does not fit.
+ */
+psp_status psp_create(const psp_grid *grid, int order, const psp_term *terms, int nterms,
+                      int b, int m, const psp_opts *opts, void *cuda_stream, psp_handle *out);
+
+/* Release every resource of the handle.  NULL is accepted. */
+psp_status psp_destroy(psp_handle h);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *psp_last_error(void);
+
+/*
+ * One implicit-Euler step (Eq. 4): u_np1 = A^{-1} u_n to the relative tolerance tol
+ * (||u_n - A u_np1|| <= tol ||u_n||), by Algorithm 1 with X_0 = u_n, B = u_n and the
+ * adopted preconditioner N (identity until a fit was adopted), followed by the
+ * Algorithm 2 fit of a candidate N for the next step.  u_n and u_np1 are device arrays
+ * of n doubles and must not overlap.  `info` (host) may be NULL.  The history persists
+ * across steps while dt is unchanged and is cleared when dt changes.
+ * Returns PSP_ERR_NOCONV after max_restarts cycles (u_np1 = last iterate).
+ */
+psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, double tol,
+                    psp_step_info *info);
+
+/* psp_step on host arrays: copies u_n_host to the device, steps, copies the result to
+ * u_np1_host (both n doubles, pageable or pinned). */
+psp_status psp_step_host(psp_handle h, const double *u_n_host, double *u_np1_host, double dt,
+                         double tol, psp_step_info *info);
+
+/* y = A x = x - dt L x (the matrix-free product of Algorithm 1), FP64 / FP32 device
+ * arrays of n elements; x and y must not overlap. */
+psp_status psp_matvec(psp_handle h, const double *x, double *y, double dt);
+psp_status psp_matvec_f32(psp_handle h, const float *x, float *y, double dt);
+
+/*
+ * Algorithm 2 (MREP) on a caller-given history: Px, Py are n x M column-major device
+ * arrays (column c starts at c*ld, ld >= n), N_band is the device output (band storage,
+ * half-width b of the handle).  Rows 0..b-1 and n-b..n-1 get the slope of a simple
+ * linear fit on the diagonal; interior rows the least-squares fit on
+ * [1; Px(i-b..i+b, :)] (or without the row of ones when opts.intercept = 0).  Rows whose
+ * normal equations are degenerate (relative Cholesky pivot <= 1e-12) get the identity
+ * row; their count goes to *singular_rows (host, may be NULL).  Requires M >= 1.
+ * Does not change the handle's preconditioner.
+ */
+psp_status psp_fit_band(psp_handle h, const double *Px, const double *Py, int64_t ld, int M,
+                        double *N_band, int *singular_rows);
+psp_status psp_fit_band_f32(psp_handle h, const float *Px, const float *Py, int64_t ld, int M,
+                            double *N_band, int *singular_rows);
+
+/* Factor the device band N_band (half-width b) and adopt it as the preconditioner.
+ * Returns PSP_ERR_NUMERIC (and keeps the previous N) if a pivot of the partitioned
+ * factorisation is zero or not finite. */
+psp_status psp_set_band(psp_handle h, const double *N_band);
+
+/* Copy the adopted N to the device array N_band (identity band if none is adopted). */
+psp_status psp_get_band(psp_handle h, double *N_band);
+
+/* y = N^{-1} v with the adopted N (the preconditioner solve of Algorithm 1), device
+ * arrays of n elements; v and y may be the same array.  transpose must be 0. */
+psp_status psp_apply_precond(psp_handle h, const double *v, double *y, int transpose);
+psp_status psp_apply_precond_f32(psp_handle h, const float *v, float *y, int transpose);
+
+/* Stencil of L without dt: w_host[d*(2R+1) + (j+R)] is the weight of u(x + j h e_d) in
+ * (L u)(x) for d < ndim and j in -R..R, R = *radius (host).  w_host holds 3*(2R+1)
+ * doubles; pass NULL to query only the radius. */
+psp_status psp_get_stencil(psp_handle h, double *w_host, int *radius);
+
+/* Forget the adopted N, the candidate and the history (back to N = I). */
+psp_status psp_reset(psp_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSP_H */

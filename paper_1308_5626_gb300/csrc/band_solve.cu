@@ -1,0 +1,740 @@
+// The preconditioner solve y = N^{-1} v of Algorithm 1 for the banded N of Algorithm 2.
+//
+// The paper solves the tridiagonal case (d = 1) with the sequential Thomas algorithm.  On
+// a GPU the solve is partitioned instead (nested dissection in one dimension, a
+// multi-level form of the SPIKE / cyclic-reduction family):
+//
+//  * Rows are grouped in blocks of b rows; a matrix of half-bandwidth b is block
+//    tridiagonal with b x b blocks (Lo_i, Di_i, Up_i).
+//  * A level splits its blocks into groups of q interior blocks followed by one
+//    separator block.  Given the separator values, the interiors of different groups
+//    are independent: one thread per group runs block Thomas (forward elimination,
+//    back substitution) over its q blocks.
+//  * Eliminating the interiors leaves a block-tridiagonal Schur system on the separators
+//    (b x b blocks again), which is the next level.  Levels recurse until one group is
+//    left; the top levels with few blocks run inside one CTA.
+//
+// Factorisation (once per fitted N, FP64): per group the block-Thomas pivots
+// Minv_i = S_i^{-1} and multipliers Mul_i = Lo_i S_{i-1}^{-1}, and the two spikes
+// W = T^{-1} [Lo_0; 0..] and V = T^{-1} [0..; Up_{q-1}] (response of the interior to the
+// left and right separators); then the separator system Lo', Di', Up' of the next level.
+// No pivoting across blocks (within a b x b inverse, partial pivoting); a zero or
+// non-finite pivot marks the factorisation as failed.
+//
+// Apply (per preconditioner solve, FP32 in the mixed form or FP64):
+//   down: per group p = T^{-1} f_I, separator right-hand sides f_s - Lo_s p_last - Up_s p_first;
+//   up:   x_I = p - W x_{s-1} - V x_s.
+// Arrays of a level are stored group-interleaved (element e of block i of group g at
+// (i*b*b + e)*G + g) so that the one-thread-per-group sweeps read coalesced.
+#include <vector>
+
+#include "band_solve.cuh"
+
+namespace psp {
+
+// ---------------------------------------------------------------------------------------
+// small dense helpers (b x b, row-major)
+// ---------------------------------------------------------------------------------------
+
+template <int B>
+__device__ __forceinline__ bool inv_block(const double (&A)[B][B], double (&X)[B][B]) {
+  double M[B][2 * B];
+#pragma unroll
+  for (int r = 0; r < B; ++r)
+#pragma unroll
+    for (int c = 0; c < 2 * B; ++c) M[r][c] = c < B ? A[r][c] : (c - B == r ? 1.0 : 0.0);
+  double scale = 0.0;
+#pragma unroll
+  for (int r = 0; r < B; ++r)
+#pragma unroll
+    for (int c = 0; c < B; ++c) scale = fmax(scale, fabs(A[r][c]));
+  bool ok = isfinite(scale) && scale > 0.0;
+#pragma unroll
+  for (int col = 0; col < B; ++col) {
+    int piv = col;
+    double best = fabs(M[col][col]);
+#pragma unroll
+    for (int r = 0; r < B; ++r)
+      if (r > col && fabs(M[r][col]) > best) { best = fabs(M[r][col]); piv = r; }
+    if (!(best > 1e-13 * scale)) ok = false;
+#pragma unroll
+    for (int c = 0; c < 2 * B; ++c) {
+      double t = M[col][c];
+      // swap rows col and piv (piv >= col), written without dynamic indexing
+#pragma unroll
+      for (int r = 0; r < B; ++r)
+        if (r == piv && r != col) { M[col][c] = M[r][c]; M[r][c] = t; }
+    }
+    const double p = M[col][col];
+    const double ip = (p != 0.0) ? 1.0 / p : 0.0;
+#pragma unroll
+    for (int c = 0; c < 2 * B; ++c) M[col][c] *= ip;
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+      if (r != col) {
+        const double f = M[r][col];
+#pragma unroll
+        for (int c = 0; c < 2 * B; ++c) M[r][c] -= f * M[col][c];
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < B; ++r)
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+      X[r][c] = M[r][B + c];
+      if (!isfinite(X[r][c])) ok = false;
+    }
+  return ok;
+}
+
+template <int B>
+__device__ __forceinline__ void mm(const double (&A)[B][B], const double (&C)[B][B], double (&X)[B][B]) {
+#pragma unroll
+  for (int r = 0; r < B; ++r)
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+      double s = 0.0;
+#pragma unroll
+      for (int l = 0; l < B; ++l) s += A[r][l] * C[l][c];
+      X[r][c] = s;
+    }
+}
+
+// element e of block i of group g (group-interleaved)
+__device__ __forceinline__ int64_t gi(int i, int e, int G, int g, int BB) {
+  return ((int64_t)i * BB + e) * G + g;
+}
+
+template <int B>
+__device__ __forceinline__ void store_blk(double *dst, float *dstf, int i, int G, int g,
+                                          const double (&M)[B][B]) {
+#pragma unroll
+  for (int r = 0; r < B; ++r)
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+      const int64_t o = gi(i, r * B + c, G, g, B * B);
+      dst[o] = M[r][c];
+      if (dstf) dstf[o] = (float)M[r][c];
+    }
+}
+
+template <int B>
+__device__ __forceinline__ void load_blk(const double *src, int i, int G, int g, double (&M)[B][B]) {
+#pragma unroll
+  for (int r = 0; r < B; ++r)
+#pragma unroll
+    for (int c = 0; c < B; ++c) M[r][c] = src[gi(i, r * B + c, G, g, B * B)];
+}
+
+// Blocks of the level input.  Level 0 reads the band (rows >= n are identity rows,
+// columns outside [0, n) are zero); higher levels read natural-order block arrays.
+struct LevelInput {
+  const double *band;     // level 0: n x (2b+1) band, else nullptr
+  int64_t n;
+  const double *bLo, *bDi, *bUp;   // levels >= 1: [blk * b*b + e]
+  int nb;
+};
+
+template <int B>
+__device__ __forceinline__ void input_blocks(const LevelInput &in, int blk, double (&Lo)[B][B],
+                                             double (&Di)[B][B], double (&Up)[B][B]) {
+  if (in.band) {
+    constexpr int W = 2 * B + 1;
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+      const int64_t row = (int64_t)blk * B + r;
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        const int64_t cl = (int64_t)(blk - 1) * B + c, cd = (int64_t)blk * B + c, cu = (int64_t)(blk + 1) * B + c;
+        double lo = 0.0, di = 0.0, up = 0.0;
+        if (row < in.n) {
+          const double *br = in.band + row * W;
+          if (cl >= 0 && cl - row >= -B) lo = br[cl - row + B];
+          if (cd < in.n && cd - row >= -B && cd - row <= B) di = br[cd - row + B];
+          if (cu < in.n && cu - row <= B) up = br[cu - row + B];
+        } else {
+          di = (r == c) ? 1.0 : 0.0;
+        }
+        Lo[r][c] = lo; Di[r][c] = di; Up[r][c] = up;
+      }
+    }
+  } else {
+    const bool real = blk < in.nb;
+#pragma unroll
+    for (int r = 0; r < B; ++r)
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        const int64_t o = (int64_t)blk * B * B + r * B + c;
+        Lo[r][c] = real ? in.bLo[o] : 0.0;
+        Up[r][c] = real ? in.bUp[o] : 0.0;
+        Di[r][c] = real ? in.bDi[o] : (r == c ? 1.0 : 0.0);
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// factorisation
+// ---------------------------------------------------------------------------------------
+
+template <int B>
+__global__ void k_factor_level(LevelInput in, int q, int G, LevelF64 f, LevelF32 h, int *fail) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  double Lo[B][B], Di[B][B], Up[B][B], Minv[B][B], UpPrev[B][B], Mul[B][B], T1[B][B], S[B][B];
+  double E[B][B], F[B][B];
+  bool ok = true;
+  for (int i = 0; i < q; ++i) {
+    const int blk = g * (q + 1) + i;
+    input_blocks<B>(in, blk, Lo, Di, Up);
+    if (i == 0) {
+#pragma unroll
+      for (int r = 0; r < B; ++r)
+#pragma unroll
+        for (int c = 0; c < B; ++c) { S[r][c] = Di[r][c]; Mul[r][c] = 0.0; E[r][c] = Lo[r][c]; }
+    } else {
+      mm<B>(Lo, Minv, Mul);
+      mm<B>(Mul, UpPrev, T1);
+#pragma unroll
+      for (int r = 0; r < B; ++r)
+#pragma unroll
+        for (int c = 0; c < B; ++c) S[r][c] = Di[r][c] - T1[r][c];
+    }
+    ok = inv_block<B>(S, Minv) && ok;
+    store_blk<B>(f.Mul, h.Mul, i, G, g, Mul);
+    store_blk<B>(f.Minv, h.Minv, i, G, g, Minv);
+    store_blk<B>(f.Up, h.Up, i, G, g, Up);
+#pragma unroll
+    for (int r = 0; r < B; ++r)
+#pragma unroll
+      for (int c = 0; c < B; ++c) { UpPrev[r][c] = Up[r][c]; F[r][c] = Up[r][c]; }
+  }
+  // separator couplings of this group
+  {
+    double L2[B][B], D2[B][B], U2[B][B];
+    if (g < G - 1) {
+      input_blocks<B>(in, g * (q + 1) + q, L2, D2, U2);
+      store_blk<B>(f.LoSep, h.LoSep, 0, G, g, L2);
+    }
+    if (g > 0) {
+      input_blocks<B>(in, g * (q + 1) - 1, L2, D2, U2);
+      store_blk<B>(f.UpSepPrev, h.UpSepPrev, 0, G, g, U2);
+    }
+  }
+  // spike W = T^{-1} [E; 0; ...]: forward Y_0 = E, Y_i = -Mul_i Y_{i-1} (kept in W),
+  // backward W_{q-1} = Minv Y_{q-1}, W_i = Minv_i (Y_i - Up_i W_{i+1})
+  double Y[B][B], Xn[B][B];
+  if (g > 0) {
+#pragma unroll
+    for (int r = 0; r < B; ++r)
+#pragma unroll
+      for (int c = 0; c < B; ++c) Y[r][c] = E[r][c];
+    store_blk<B>(f.W, nullptr, 0, G, g, Y);
+    for (int i = 1; i < q; ++i) {
+      load_blk<B>(f.Mul, i, G, g, Mul);
+      mm<B>(Mul, Y, T1);
+#pragma unroll
+      for (int r = 0; r < B; ++r)
+#pragma unroll
+        for (int c = 0; c < B; ++c) Y[r][c] = -T1[r][c];
+      store_blk<B>(f.W, nullptr, i, G, g, Y);
+    }
+    for (int i = q - 1; i >= 0; --i) {
+      load_blk<B>(f.W, i, G, g, Y);
+      if (i < q - 1) {
+        load_blk<B>(f.Up, i, G, g, Up);
+        mm<B>(Up, Xn, T1);
+#pragma unroll
+        for (int r = 0; r < B; ++r)
+#pragma unroll
+          for (int c = 0; c < B; ++c) Y[r][c] -= T1[r][c];
+      }
+      load_blk<B>(f.Minv, i, G, g, Minv);
+      mm<B>(Minv, Y, Xn);
+      store_blk<B>(f.W, h.W, i, G, g, Xn);
+    }
+  } else {
+    double Z0[B][B] = {};
+    for (int i = 0; i < q; ++i) store_blk<B>(f.W, h.W, i, G, g, Z0);
+  }
+  // spike V = T^{-1} [0; ...; F]: V_{q-1} = Minv F, V_i = -Minv_i Up_i V_{i+1}
+  if (g < G - 1) {
+    load_blk<B>(f.Minv, q - 1, G, g, Minv);
+    mm<B>(Minv, F, Xn);
+    store_blk<B>(f.Vs, h.Vs, q - 1, G, g, Xn);
+    for (int i = q - 2; i >= 0; --i) {
+      load_blk<B>(f.Up, i, G, g, Up);
+      mm<B>(Up, Xn, T1);
+      load_blk<B>(f.Minv, i, G, g, Minv);
+      mm<B>(Minv, T1, Y);
+#pragma unroll
+      for (int r = 0; r < B; ++r)
+#pragma unroll
+        for (int c = 0; c < B; ++c) Xn[r][c] = -Y[r][c];
+      store_blk<B>(f.Vs, h.Vs, i, G, g, Xn);
+    }
+  } else {
+    double Z0[B][B] = {};
+    for (int i = 0; i < q; ++i) store_blk<B>(f.Vs, h.Vs, i, G, g, Z0);
+  }
+  if (!ok) atomicOr(fail, 1);
+}
+
+// Separator system of the next level: for separator t (block s = t(q+1)+q)
+//   Lo' = -LoSep_t W_t[q-1],  Di' = Di_s - LoSep_t V_t[q-1] - UpSep_t W_{t+1}[0],
+//   Up' = -UpSep_t V_{t+1}[0],  UpSep_t = UpSepPrev_{t+1}.
+template <int B>
+__global__ void k_assemble(LevelInput in, int q, int G, LevelF64 f, double *nLo, double *nDi, double *nUp,
+                           int *fail) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= G - 1) return;
+  double Lo[B][B], Di[B][B], Up[B][B], Ls[B][B], Us[B][B], Wl[B][B], Vl[B][B], Wn[B][B], Vn[B][B];
+  double T1[B][B], T2[B][B], T3[B][B];
+  input_blocks<B>(in, t * (q + 1) + q, Lo, Di, Up);
+  load_blk<B>(f.LoSep, 0, G, t, Ls);
+  load_blk<B>(f.UpSepPrev, 0, G, t + 1, Us);
+  load_blk<B>(f.W, q - 1, G, t, Wl);
+  load_blk<B>(f.Vs, q - 1, G, t, Vl);
+  load_blk<B>(f.W, 0, G, t + 1, Wn);
+  load_blk<B>(f.Vs, 0, G, t + 1, Vn);
+  mm<B>(Ls, Wl, T1);
+  mm<B>(Ls, Vl, T2);
+  mm<B>(Us, Wn, T3);
+  bool ok = true;
+#pragma unroll
+  for (int r = 0; r < B; ++r)
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+      const int64_t o = (int64_t)t * B * B + r * B + c;
+      nLo[o] = -T1[r][c];
+      nDi[o] = Di[r][c] - T2[r][c] - T3[r][c];
+      if (!isfinite(nDi[o]) || !isfinite(nLo[o])) ok = false;
+    }
+  mm<B>(Us, Vn, T1);
+#pragma unroll
+  for (int r = 0; r < B; ++r)
+#pragma unroll
+    for (int c = 0; c < B; ++c) nUp[(int64_t)t * B * B + r * B + c] = -T1[r][c];
+  if (!ok) atomicOr(fail, 1);
+}
+
+// ---------------------------------------------------------------------------------------
+// apply
+// ---------------------------------------------------------------------------------------
+
+template <typename T, int B>
+__device__ __forceinline__ void mv_sub(T (&y)[B], const T *M, int i, int G, int g, const T (&x)[B]) {
+#pragma unroll
+  for (int r = 0; r < B; ++r) {
+    T s = y[r];
+#pragma unroll
+    for (int c = 0; c < B; ++c) s -= M[gi(i, r * B + c, G, g, B * B)] * x[c];
+    y[r] = s;
+  }
+}
+
+template <typename T, int B>
+__device__ __forceinline__ void mv(T (&y)[B], const T *M, int i, int G, int g, const T (&x)[B]) {
+#pragma unroll
+  for (int r = 0; r < B; ++r) {
+    T s = (T)0;
+#pragma unroll
+    for (int c = 0; c < B; ++c) s += M[gi(i, r * B + c, G, g, B * B)] * x[c];
+    y[r] = s;
+  }
+}
+
+// Down sweep of group g.  `rhs(i, r)` is a reference to the right-hand side of interior
+// block i (i < q) or of the separator block (i == q); the forward sweep overwrites it with
+// y.  The back substitution writes p to L.p (group-interleaved).
+template <typename T, int B, typename Acc>
+__device__ __forceinline__ void down_group(const LevelApply<T> &L, int g, Acc rhs) {
+  const int q = L.q, G = L.G;
+  T y[B], yp[B];
+  for (int i = 0; i < q; ++i) {
+#pragma unroll
+    for (int r = 0; r < B; ++r) y[r] = rhs(i, r);
+    if (i > 0) mv_sub<T, B>(y, L.Mul, i, G, g, yp);
+#pragma unroll
+    for (int r = 0; r < B; ++r) { rhs(i, r) = y[r]; yp[r] = y[r]; }
+  }
+  T x[B], xn[B], x0[B], xl[B];
+  for (int i = q - 1; i >= 0; --i) {
+#pragma unroll
+    for (int r = 0; r < B; ++r) y[r] = rhs(i, r);
+    if (i < q - 1) mv_sub<T, B>(y, L.Up, i, G, g, xn);
+    mv<T, B>(x, L.Minv, i, G, g, y);
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+      L.p[gi(i, r, G, g, B)] = x[r];
+      xn[r] = x[r];
+      if (i == q - 1) xl[r] = x[r];
+      if (i == 0) x0[r] = x[r];
+    }
+  }
+  if (G > 1) {
+    if (g < G - 1) {
+      T c[B];
+      mv<T, B>(c, L.LoSep, 0, G, g, xl);
+#pragma unroll
+      for (int r = 0; r < B; ++r) { L.cR[g * B + r] = -c[r]; L.seprhs[g * B + r] = rhs(q, r); }
+    }
+    if (g > 0) {
+      T c[B];
+      mv<T, B>(c, L.UpSepPrev, 0, G, g, x0);
+#pragma unroll
+      for (int r = 0; r < B; ++r) L.cL[g * B + r] = -c[r];
+    }
+  }
+}
+
+// Up sweep of group g: x_i = p_i - W_i sl - V_i sr; out(i, r) receives interior block i
+// (i < q) and the separator block (i == q, only for g < G-1).
+template <typename T, int B, typename Out>
+__device__ __forceinline__ void up_group(const LevelApply<T> &L, int g, const T *solnext, Out out) {
+  const int q = L.q, G = L.G;
+  T sl[B], sr[B];
+#pragma unroll
+  for (int r = 0; r < B; ++r) {
+    sl[r] = (g > 0) ? solnext[(g - 1) * B + r] : (T)0;
+    sr[r] = (g < G - 1) ? solnext[g * B + r] : (T)0;
+  }
+  for (int i = 0; i < q; ++i) {
+    T x[B];
+#pragma unroll
+    for (int r = 0; r < B; ++r) x[r] = L.p[gi(i, r, G, g, B)];
+    if (G > 1) {
+      mv_sub<T, B>(x, L.W, i, G, g, sl);
+      mv_sub<T, B>(x, L.Vs, i, G, g, sr);
+    }
+#pragma unroll
+    for (int r = 0; r < B; ++r) out(i, r, x[r]);
+  }
+  if (g < G - 1) {
+#pragma unroll
+    for (int r = 0; r < B; ++r) out(q, r, sr[r]);
+  }
+}
+
+// Level >= 1 down: right-hand side of block j = prev.seprhs[j] + prev.cR[j] + prev.cL[j+1],
+// staged in L.p and swept in place.
+template <typename T, int B>
+__device__ __forceinline__ void down_level_group(const LevelApply<T> &L, const LevelApply<T> &P, int g) {
+  const int q = L.q, G = L.G;
+  // stage: p slots 0..q-1 hold the interior rhs; the separator rhs is computed on demand
+  for (int i = 0; i < q; ++i) {
+    const int j = g * (q + 1) + i;
+#pragma unroll
+    for (int r = 0; r < B; ++r)
+      L.p[gi(i, r, G, g, B)] = (j < L.nb) ? P.seprhs[j * B + r] + P.cR[j * B + r] + P.cL[(j + 1) * B + r] : (T)0;
+  }
+  T sep[B];
+  {
+    const int j = g * (q + 1) + q;
+#pragma unroll
+    for (int r = 0; r < B; ++r)
+      sep[r] = (g < G - 1) ? P.seprhs[j * B + r] + P.cR[j * B + r] + P.cL[(j + 1) * B + r] : (T)0;
+  }
+  T *p = L.p;
+  auto acc = [&](int i, int r) -> T & { return i < q ? p[gi(i, r, G, g, B)] : sep[r]; };
+  down_group<T, B>(L, g, acc);
+}
+
+template <typename T, int B>
+__device__ __forceinline__ void up_level_group(const LevelApply<T> &L, const T *solnext, int g) {
+  const int q = L.q;
+  T *sol = L.sol;
+  const int nb = L.nb;
+  auto out = [&](int i, int r, T v) {
+    const int j = g * (q + 1) + i;
+    if (j < nb) sol[j * B + r] = v;
+  };
+  up_group<T, B>(L, g, solnext, out);
+}
+
+constexpr int kQ0 = 16;          // interior blocks per group on level 0
+constexpr int kGroupsPerCta = 64;
+
+// Level 0 down: stage the CTA's rows of v (times *scale) in shared memory, one group per thread.
+template <typename T, int B>
+__global__ void __launch_bounds__(kGroupsPerCta) k_down0(const T *__restrict__ v, const double *scale,
+                                                         const int *active, LevelApply<T> L, int64_t n) {
+  if (active && *active == 0) return;
+  constexpr int SPAN = (kQ0 + 1) * B;
+  constexpr int PITCH = SPAN + 1;
+  __shared__ T tile[kGroupsPerCta * PITCH];
+  const T sc = scale ? (T)(*scale) : (T)1;
+  const int g0 = blockIdx.x * kGroupsPerCta;
+  const int64_t row0 = (int64_t)g0 * SPAN;
+  for (int e = threadIdx.x; e < kGroupsPerCta * SPAN; e += kGroupsPerCta) {
+    const int64_t row = row0 + e;
+    tile[(e / SPAN) * PITCH + (e % SPAN)] = (row < n) ? sc * v[row] : (T)0;
+  }
+  __syncthreads();
+  const int g = g0 + threadIdx.x;
+  if (g < L.G) {
+    T *mine = tile + threadIdx.x * PITCH;
+    auto acc = [&](int i, int r) -> T & { return mine[i * B + r]; };
+    down_group<T, B>(L, g, acc);
+  }
+}
+
+// Level 0 up: x for the CTA's groups staged in shared memory, then written in row order
+// through the epilogue: mode 0 y = x (fixed or ring-column output), mode 1 X += x (FP64).
+template <typename T, int B>
+__global__ void __launch_bounds__(kGroupsPerCta) k_up0(const int *active, LevelApply<T> L, const T *solnext,
+                                                       OutRef<T> yref, double *X, int mode, int64_t n) {
+  if (active && *active == 0) return;
+  constexpr int SPAN = (kQ0 + 1) * B;
+  constexpr int PITCH = SPAN + 1;
+  __shared__ T tile[kGroupsPerCta * PITCH];
+  const int g0 = blockIdx.x * kGroupsPerCta;
+  const int g = g0 + threadIdx.x;
+  if (g < L.G) {
+    T *mine = tile + threadIdx.x * PITCH;
+    auto out = [&](int i, int r, T v) { mine[i * B + r] = v; };
+    up_group<T, B>(L, g, solnext, out);
+  }
+  __syncthreads();
+  const int64_t row0 = (int64_t)g0 * SPAN;
+  T *y = (mode == 0) ? yref.get() : nullptr;
+  for (int e = threadIdx.x; e < kGroupsPerCta * SPAN; e += kGroupsPerCta) {
+    const int64_t row = row0 + e;
+    if (row < n && (g0 + e / SPAN) < L.G) {
+      const T v = tile[(e / SPAN) * PITCH + (e % SPAN)];
+      if (mode == 0) y[row] = v;
+      else X[row] += (double)v;
+    }
+  }
+}
+
+template <typename T, int B>
+__global__ void k_down_level(const int *active, LevelApply<T> L, LevelApply<T> P) {
+  if (active && *active == 0) return;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < L.G) down_level_group<T, B>(L, P, g);
+}
+
+template <typename T, int B>
+__global__ void k_up_level(const int *active, LevelApply<T> L, const T *solnext) {
+  if (active && *active == 0) return;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < L.G) up_level_group<T, B>(L, solnext, g);
+}
+
+// Levels first..last (last = top, one group) in one CTA: down sweeps, then up sweeps.
+template <typename T, int B>
+__global__ void __launch_bounds__(512) k_tail(const int *active, const LevelApply<T> *lv, int first, int last) {
+  if (active && *active == 0) return;
+  for (int l = first; l <= last; ++l) {
+    const LevelApply<T> L = lv[l];
+    const LevelApply<T> P = lv[l - 1];
+    for (int g = threadIdx.x; g < L.G; g += blockDim.x) down_level_group<T, B>(L, P, g);
+    __threadfence_block();
+    __syncthreads();
+  }
+  for (int l = last; l >= first; --l) {
+    const LevelApply<T> L = lv[l];
+    const T *solnext = (l < last) ? lv[l + 1].sol : nullptr;
+    for (int g = threadIdx.x; g < L.G; g += blockDim.x) up_level_group<T, B>(L, solnext, g);
+    __threadfence_block();
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------
+
+void BandSolver::plan(int64_t n_, int b_) {
+  n = n_;
+  b = b_;
+  levels.clear();
+  int nb = (int)((n + b - 1) / b);
+  int q = kQ0;
+  while (true) {
+    LevelShape s;
+    s.nb = nb;
+    s.q = q;
+    s.G = (nb <= q) ? 1 : (nb + 1 + q) / (q + 1);
+    levels.push_back(s);
+    if (s.G == 1) break;
+    nb = s.G - 1;
+    q = 32;
+  }
+  // levels whose block count is small run in the single-CTA tail
+  tail_first = (int)levels.size() - 1;
+  while (tail_first > 1 && levels[tail_first - 1].nb <= 2048) --tail_first;
+  if (levels.size() == 1) tail_first = 1;  // no tail: level 0 is the top
+}
+
+template <typename T>
+static T *carve(char *&p, size_t count) {
+  T *r = reinterpret_cast<T *>(p);
+  p += ((count * sizeof(T) + 255) / 256) * 256;
+  return r;
+}
+
+size_t BandSolver::slot_bytes() const {
+  size_t total = 0;
+  const int BB = b * b;
+  for (size_t l = 0; l < levels.size(); ++l) {
+    const LevelShape &s = levels[l];
+    const size_t gq = (size_t)s.G * s.q * BB;
+    const size_t gs = (size_t)s.G * BB;
+    total += 5 * (((gq * 8 + 255) / 256) * 256) + 2 * (((gs * 8 + 255) / 256) * 256);  // FP64
+    total += 5 * (((gq * 4 + 255) / 256) * 256) + 2 * (((gs * 4 + 255) / 256) * 256);  // FP32
+    if (l + 1 < levels.size()) total += 3 * ((((size_t)(s.G - 1) * BB * 8 + 255) / 256) * 256);
+  }
+  return total + 4096;
+}
+
+template <typename T>
+static size_t apply_bytes_t(const std::vector<LevelShape> &lv, int b) {
+  size_t total = 0;
+  for (const LevelShape &s : lv) {
+    total += ((((size_t)s.G * s.q * b * sizeof(T)) + 255) / 256) * 256;
+    total += 3 * (((((size_t)s.G * b + 64) * sizeof(T)) + 255) / 256) * 256;
+    total += ((((size_t)(s.nb + 1) * b * sizeof(T)) + 255) / 256) * 256;
+  }
+  return total + 2 * ((((size_t)lv.size() * sizeof(LevelApply<T>)) + 255) / 256) * 256 + 4096;
+}
+
+size_t BandSolver::apply_bytes() const { return apply_bytes_t<double>(levels, b) + apply_bytes_t<float>(levels, b); }
+
+void BandSolver::bind(void *slot_mem, int slot) {
+  char *p = reinterpret_cast<char *>(slot_mem);
+  const int BB = b * b;
+  Slot &S = slots[slot];
+  S.f.assign(levels.size(), LevelF64{});
+  S.h.assign(levels.size(), LevelF32{});
+  S.nLo.assign(levels.size(), nullptr);
+  S.nDi.assign(levels.size(), nullptr);
+  S.nUp.assign(levels.size(), nullptr);
+  for (size_t l = 0; l < levels.size(); ++l) {
+    const LevelShape &s = levels[l];
+    const size_t gq = (size_t)s.G * s.q * BB, gs = (size_t)s.G * BB;
+    LevelF64 &f = S.f[l];
+    f.Mul = carve<double>(p, gq); f.Minv = carve<double>(p, gq); f.Up = carve<double>(p, gq);
+    f.W = carve<double>(p, gq); f.Vs = carve<double>(p, gq);
+    f.LoSep = carve<double>(p, gs); f.UpSepPrev = carve<double>(p, gs);
+    LevelF32 &h = S.h[l];
+    h.Mul = carve<float>(p, gq); h.Minv = carve<float>(p, gq); h.Up = carve<float>(p, gq);
+    h.W = carve<float>(p, gq); h.Vs = carve<float>(p, gq);
+    h.LoSep = carve<float>(p, gs); h.UpSepPrev = carve<float>(p, gs);
+    if (l + 1 < levels.size()) {
+      const size_t nn = (size_t)(s.G - 1) * BB;
+      S.nLo[l] = carve<double>(p, nn); S.nDi[l] = carve<double>(p, nn); S.nUp[l] = carve<double>(p, nn);
+    }
+  }
+}
+
+template <typename T, typename FS>
+static void bind_apply_t(const std::vector<LevelShape> &lv, int b, char *&p, const FS (&fac)[2],
+                         std::vector<LevelApply<T>> (&out)[2], LevelApply<T> *(&dev)[2]) {
+  std::vector<LevelApply<T>> scratch(lv.size(), LevelApply<T>{});
+  for (size_t l = 0; l < lv.size(); ++l) {
+    LevelApply<T> &a = scratch[l];
+    a.nb = lv[l].nb; a.q = lv[l].q; a.G = lv[l].G;
+    a.p = carve<T>(p, (size_t)lv[l].G * lv[l].q * b);
+    a.cR = carve<T>(p, (size_t)lv[l].G * b + 64);
+    a.cL = carve<T>(p, (size_t)lv[l].G * b + 64);
+    a.seprhs = carve<T>(p, (size_t)lv[l].G * b + 64);
+    a.sol = carve<T>(p, (size_t)(lv[l].nb + 1) * b);
+  }
+  for (int s = 0; s < 2; ++s) {
+    out[s] = scratch;
+    for (size_t l = 0; l < lv.size(); ++l) {
+      const auto &f = fac[s][l];
+      LevelApply<T> &a = out[s][l];
+      a.Mul = f.Mul; a.Minv = f.Minv; a.Up = f.Up; a.W = f.W; a.Vs = f.Vs;
+      a.LoSep = f.LoSep; a.UpSepPrev = f.UpSepPrev;
+    }
+    dev[s] = carve<LevelApply<T>>(p, lv.size());
+    cudaMemcpy(dev[s], out[s].data(), lv.size() * sizeof(LevelApply<T>), cudaMemcpyHostToDevice);
+  }
+}
+
+void BandSolver::bind_apply(void *mem) {
+  char *p = reinterpret_cast<char *>(mem);
+  const std::vector<LevelF64> f64[2] = {slots[0].f, slots[1].f};
+  const std::vector<LevelF32> f32[2] = {slots[0].h, slots[1].h};
+  bind_apply_t<double>(levels, b, p, f64, app64, dev_app64);
+  bind_apply_t<float>(levels, b, p, f32, app32, dev_app32);
+}
+
+template <int B>
+static void factor_b(BandSolver &bs, int slot, const double *band, int *fail, cudaStream_t s) {
+  BandSolver::Slot &S = bs.slots[slot];
+  for (size_t l = 0; l < bs.levels.size(); ++l) {
+    const LevelShape &sh = bs.levels[l];
+    LevelInput in;
+    if (l == 0) {
+      in.band = band; in.n = bs.n; in.bLo = in.bDi = in.bUp = nullptr; in.nb = sh.nb;
+    } else {
+      in.band = nullptr; in.n = 0; in.bLo = S.nLo[l - 1]; in.bDi = S.nDi[l - 1]; in.bUp = S.nUp[l - 1];
+      in.nb = sh.nb;
+    }
+    const int th = 64;
+    k_factor_level<B><<<(sh.G + th - 1) / th, th, 0, s>>>(in, sh.q, sh.G, S.f[l], S.h[l], fail);
+    if (l + 1 < bs.levels.size())
+      k_assemble<B><<<(sh.G - 1 + th - 1) / th, th, 0, s>>>(in, sh.q, sh.G, S.f[l], S.nLo[l], S.nDi[l],
+                                                            S.nUp[l], fail);
+  }
+}
+
+void BandSolver::factor(int slot, const double *band, int *fail, cudaStream_t s) {
+  switch (b) {
+    case 1: factor_b<1>(*this, slot, band, fail, s); break;
+    case 2: factor_b<2>(*this, slot, band, fail, s); break;
+    case 3: factor_b<3>(*this, slot, band, fail, s); break;
+    case 4: factor_b<4>(*this, slot, band, fail, s); break;
+    default: break;
+  }
+}
+
+template <typename T, int B>
+static void apply_b(const BandSolver &bs, const std::vector<LevelApply<T>> &a, const LevelApply<T> *dev,
+                    const T *v, const double *scale, const int *active, OutRef<T> y, double *X, int mode,
+                    cudaStream_t s) {
+  const int L = (int)a.size();
+  const int g0 = (a[0].G + kGroupsPerCta - 1) / kGroupsPerCta;
+  k_down0<T, B><<<g0, kGroupsPerCta, 0, s>>>(v, scale, active, a[0], bs.n);
+  const int tf = bs.tail_first;
+  for (int l = 1; l < tf && l < L; ++l)
+    k_down_level<T, B><<<(a[l].G + 63) / 64, 64, 0, s>>>(active, a[l], a[l - 1]);
+  if (L > 1) k_tail<T, B><<<1, 512, 0, s>>>(active, dev, tf, L - 1);
+  for (int l = std::min(tf, L) - 1; l >= 1; --l)
+    k_up_level<T, B><<<(a[l].G + 63) / 64, 64, 0, s>>>(active, a[l], a[l + 1].sol);
+  k_up0<T, B><<<g0, kGroupsPerCta, 0, s>>>(active, a[0], L > 1 ? a[1].sol : nullptr, y, X, mode, bs.n);
+}
+
+template <typename T>
+static const std::vector<LevelApply<T>> &apps_of(const BandSolver &bs, int slot);
+template <>
+const std::vector<LevelApply<double>> &apps_of<double>(const BandSolver &bs, int slot) { return bs.app64[slot]; }
+template <>
+const std::vector<LevelApply<float>> &apps_of<float>(const BandSolver &bs, int slot) { return bs.app32[slot]; }
+static const LevelApply<double> *dev_of(const BandSolver &bs, int slot, double *) { return bs.dev_app64[slot]; }
+static const LevelApply<float> *dev_of(const BandSolver &bs, int slot, float *) { return bs.dev_app32[slot]; }
+
+template <typename T>
+void BandSolver::apply(int slot, const T *v, const double *scale, const int *active, OutRef<T> y, double *X,
+                       int mode, cudaStream_t s) const {
+  const std::vector<LevelApply<T>> &a = apps_of<T>(*this, slot);
+  const LevelApply<T> *dev = dev_of(*this, slot, (T *)nullptr);
+  switch (b) {
+    case 1: apply_b<T, 1>(*this, a, dev, v, scale, active, y, X, mode, s); break;
+    case 2: apply_b<T, 2>(*this, a, dev, v, scale, active, y, X, mode, s); break;
+    case 3: apply_b<T, 3>(*this, a, dev, v, scale, active, y, X, mode, s); break;
+    case 4: apply_b<T, 4>(*this, a, dev, v, scale, active, y, X, mode, s); break;
+    default: break;
+  }
+}
+
+template void BandSolver::apply<float>(int, const float *, const double *, const int *, OutRef<float>, double *,
+                                       int, cudaStream_t) const;
+template void BandSolver::apply<double>(int, const double *, const double *, const int *, OutRef<double>,
+                                        double *, int, cudaStream_t) const;
+
+}  // namespace psp

@@ -1,0 +1,607 @@
+// C ABI of libpsp (include/psp.h): handle, workspace, captured restart cycles and the host
+// loop of one implicit-Euler step (Eq. 4) solved by Algorithm 1 with the progressive
+// preconditioner of Algorithm 2.
+//
+// One restart cycle of Algorithm 1 is captured once as a CUDA graph: the FP64 restart
+// residual, then for k = 1..m the preconditioner solve (or a scaled copy when N = I), the
+// stencil matvec and the three Gram-Schmidt passes whose last CTA runs the Givens step,
+// then the update Z = V Q, X = X_0 + N^{-1} Z and a copy of the cycle summary to pinned
+// host memory.  Kernels after the finish test see DevState::active == 0 and return at
+// once, so the host waits once per cycle, not once per iteration.  Three graphs exist:
+// N = I and one per factor slot (the adopted N and a freshly fitted candidate).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "band_solve.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+psp_status fail(psp_status s, const std::string &msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define PSP_CUDA(call)                                                                           \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      return fail(PSP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));            \
+  } while (0)
+
+// Finite-difference weights of the derivatives 0..M at z on the nodes x[0..n-1]
+// (Fornberg's recursion, Math. Comp. 51 (1988) 699-706), c[j*(M+1) + m].
+void fornberg(int M, long double z, const std::vector<long double> &x, std::vector<long double> &c) {
+  const int n = (int)x.size();
+  c.assign((size_t)n * (M + 1), 0.0L);
+  long double c1 = 1.0L, c4 = x[0] - z;
+  c[0] = 1.0L;
+  for (int i = 1; i < n; ++i) {
+    const int mn = std::min(i, M);
+    long double c2 = 1.0L;
+    const long double c5 = c4;
+    c4 = x[i] - z;
+    for (int j = 0; j < i; ++j) {
+      const long double c3 = x[i] - x[j];
+      c2 *= c3;
+      if (j == i - 1) {
+        for (int k = mn; k >= 1; --k)
+          c[(size_t)i * (M + 1) + k] = c1 * (k * c[(size_t)(i - 1) * (M + 1) + k - 1] -
+                                             c5 * c[(size_t)(i - 1) * (M + 1) + k]) / c2;
+        c[(size_t)i * (M + 1)] = -c1 * c5 * c[(size_t)(i - 1) * (M + 1)] / c2;
+      }
+      for (int k = mn; k >= 1; --k)
+        c[(size_t)j * (M + 1) + k] = (c4 * c[(size_t)j * (M + 1) + k] - k * c[(size_t)j * (M + 1) + k - 1]) / c3;
+      c[(size_t)j * (M + 1)] = c4 * c[(size_t)j * (M + 1)] / c3;
+    }
+    c1 = c2;
+  }
+}
+
+// Central weights w_{-r..r} for d^k/dx^k of even accuracy order p, r = (k-1)/2 + p/2.
+std::vector<double> central_weights(int k, int p) {
+  const int r = (k - 1) / 2 + p / 2;
+  std::vector<long double> x;
+  for (int j = -r; j <= r; ++j) x.push_back((long double)j);
+  std::vector<long double> c;
+  fornberg(k, 0.0L, x, c);
+  std::vector<double> w(2 * r + 1);
+  for (int j = 0; j < 2 * r + 1; ++j) w[j] = (double)c[(size_t)j * (k + 1) + k];
+  return w;
+}
+
+int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+using namespace psp;
+
+struct psp_ctx {
+  Geometry geo{};
+  double h[3] = {0, 0, 0};
+  double wdir[3][2 * kMaxR + 1] = {};   // stencil of L per direction (no dt)
+  int order = 0, b = 0, m = 0;
+  psp_opts opts{};
+  bool mixed = false;
+  cudaStream_t stream = nullptr;     // caller's stream
+  cudaStream_t cap = nullptr;        // internal capture stream
+  int64_t ld = 0;                    // leading dimension of every n-vector column
+  int mmax = 0;
+
+  // device workspace
+  void *V = nullptr, *Px = nullptr, *Py = nullptr, *Z = nullptr;   // Krylov precision
+  double *X = nullptr, *B = nullptr;                               // FP64 solution / rhs
+  double *partial = nullptr;
+  DevState *st = nullptr;
+  DevState *api_st = nullptr;        // coefficients for psp_matvec
+  double *moments = nullptr;
+  double *band_adopted = nullptr, *band_cand = nullptr;
+  int *dev_int = nullptr;            // [0] factor failure, [1] singular rows
+  void *slot_mem[2] = {nullptr, nullptr};
+  void *apply_mem = nullptr;
+  BandSolver bs;
+
+  // host mirrors
+  CycleSummary *sum_host = nullptr;  // pinned
+  DevState *st_host = nullptr;       // pinned staging for parameter uploads
+  int *int_host = nullptr;           // pinned
+
+  // preconditioner state
+  int adopted = -1;      // slot of the adopted N, -1: N = I
+  int cand = -1;         // slot of an untried candidate, -1: none
+  double rate_ref = -1;  // reference per-iteration residual reduction
+  int wait = 0, wait_len = 1;
+  double hist_dt = NAN;
+  int last_singular = 0;
+
+  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};   // [0] N = I, [1] slot 0, [2] slot 1
+  double *hostbuf = nullptr;   // pinned staging for psp_step_host
+  double *dev_un = nullptr, *dev_unp1 = nullptr;
+};
+
+namespace {
+
+void set_coef(const psp_ctx *h, double dt, double (*coef)[2 * kMaxR + 1]) {
+  for (int d = 0; d < 3; ++d)
+    for (int j = 0; j < 2 * kMaxR + 1; ++j) coef[d][j] = (d < h->geo.ndim) ? -dt * h->wdir[d][j] : 0.0;
+  double centre = 1.0;
+  for (int d = 0; d < 3; ++d) {
+    centre += coef[d][kMaxR];
+    coef[d][kMaxR] = 0.0;
+  }
+  coef[0][kMaxR] = centre;
+}
+
+template <typename T>
+void enqueue_cycle(psp_ctx *h, int slot, cudaStream_t s) {
+  T *V = reinterpret_cast<T *>(h->V);
+  T *Px = reinterpret_cast<T *>(h->Px);
+  T *Py = reinterpret_cast<T *>(h->Py);
+  T *Z = reinterpret_cast<T *>(h->Z);
+  const Geometry &g = h->geo;
+  launch_restart<T, T>(g, h->X, h->B, Px, Py, h->ld, V, h->st, h->partial, h->mixed ? 1 : 0, s);
+  const int *active = &h->st->active;
+  for (int k = 1; k <= h->m; ++k) {
+    OutRef<T> pxcol = ring_out<T>(Px, h->ld, &h->st->hist_count, h->mmax);
+    OutRef<T> pycol = ring_out<T>(Py, h->ld, &h->st->hist_count, h->mmax);
+    if (slot < 0) {
+      launch_scale_copy<T>(k, g.n, V, h->ld, pxcol, h->st, s);
+    } else {
+      h->bs.apply<T>(slot, V + (int64_t)(k - 1) * h->ld, &h->st->sigma[k - 1], active, pxcol, nullptr, 0, s);
+    }
+    // U_k = A Y_k, read back from the ring column just written
+    launch_stencil<T, T, T>(g, ring_in<T>(Px, h->ld, &h->st->hist_count, h->mmax), pycol, h->st, active, s);
+    launch_arnoldi<T>(k, g.n, V, h->ld, Py, h->ld, h->st, h->partial, h->mixed ? 1 : 0, s);
+  }
+  if (slot < 0) {
+    launch_update_z<T>(g.n, V, h->ld, Z, h->X, 1, h->st, s);
+  } else {
+    launch_update_z<T>(g.n, V, h->ld, Z, h->X, 0, h->st, s);
+    h->bs.apply<T>(slot, Z, nullptr, &h->st->k_end, fixed_out<T>(nullptr), h->X, 1, s);
+  }
+  cudaMemcpyAsync(h->sum_host, &h->st->sum, sizeof(CycleSummary), cudaMemcpyDeviceToHost, s);
+}
+
+psp_status capture(psp_ctx *h, int which) {
+  cudaGraph_t graph;
+  PSP_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+  const int slot = which - 1;
+  if (h->mixed) enqueue_cycle<float>(h, slot, h->cap);
+  else enqueue_cycle<double>(h, slot, h->cap);
+  cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+  if (e != cudaSuccess) return fail(PSP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&h->graph[which], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(PSP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  return PSP_OK;
+}
+
+psp_status ensure_graph(psp_ctx *h, int which) {
+  if (h->graph[which]) return PSP_OK;
+  return capture(h, which);
+}
+
+// Factor band (device) into `slot`; returns PSP_ERR_NUMERIC on a failed pivot.
+psp_status factor_into(psp_ctx *h, int slot, const double *band) {
+  PSP_CUDA(cudaMemsetAsync(h->dev_int, 0, sizeof(int), h->stream));
+  h->bs.factor(slot, band, h->dev_int, h->stream);
+  PSP_CUDA(cudaGetLastError());
+  PSP_CUDA(cudaMemcpyAsync(h->int_host, h->dev_int, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  PSP_CUDA(cudaStreamSynchronize(h->stream));
+  if (h->int_host[0]) return fail(PSP_ERR_NUMERIC, "band factorisation: zero or non-finite pivot");
+  return PSP_OK;
+}
+
+template <typename TH>
+psp_status fit_into(psp_ctx *h, const TH *Px, const TH *Py, int64_t ld, int M, double *band, int *singular) {
+  PSP_CUDA(cudaMemsetAsync(h->dev_int + 1, 0, sizeof(int), h->stream));
+  launch_fit<TH>(h->b, h->opts.intercept, h->geo.n, M, Px, Py, ld, h->moments, band, h->dev_int + 1, h->stream);
+  PSP_CUDA(cudaGetLastError());
+  PSP_CUDA(cudaMemcpyAsync(h->int_host + 1, h->dev_int + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  PSP_CUDA(cudaStreamSynchronize(h->stream));
+  if (singular) *singular = h->int_host[1];
+  return PSP_OK;
+}
+
+double rate_of(double R_end, double beta, int k) {
+  if (k <= 0 || !(beta > 0.0)) return 1.0;
+  return std::pow(std::max(R_end, 1e-300) / beta, 1.0 / k);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *psp_last_error(void) { return g_last_error.c_str(); }
+
+psp_status psp_default_opts(psp_opts *o) {
+  if (!o) return fail(PSP_ERR_ARG, "opts is NULL");
+  o->precision = PSP_FP64;
+  o->intercept = 1;
+  o->max_restarts = 200;
+  o->max_hist_cols = 0;
+  o->inner_tol = 1e-5;
+  o->accept_rule = 1;
+  return PSP_OK;
+}
+
+psp_status psp_destroy(psp_handle h) {
+  if (!h) return PSP_OK;
+  for (auto &g : h->graph)
+    if (g) cudaGraphExecDestroy(g);
+  void *dev[] = {h->V, h->Px, h->Py, h->Z, h->X, h->B, h->partial, h->st, h->api_st, h->moments,
+                 h->band_adopted, h->band_cand, h->dev_int, h->slot_mem[0], h->slot_mem[1], h->apply_mem,
+                 h->dev_un, h->dev_unp1};
+  for (void *p : dev)
+    if (p) cudaFree(p);
+  if (h->sum_host) cudaFreeHost(h->sum_host);
+  if (h->st_host) cudaFreeHost(h->st_host);
+  if (h->int_host) cudaFreeHost(h->int_host);
+  if (h->hostbuf) cudaFreeHost(h->hostbuf);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  delete h;
+  return PSP_OK;
+}
+
+psp_status psp_create(const psp_grid *grid, int order, const psp_term *terms, int nterms, int b, int m,
+                      const psp_opts *opts, void *cuda_stream, psp_handle *out) {
+  if (!grid || !terms || !out) return fail(PSP_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  if (grid->ndim < 1 || grid->ndim > 3) return fail(PSP_ERR_ARG, "ndim must be 1, 2 or 3");
+  if (order != 2 && order != 4 && order != 6 && order != 8) return fail(PSP_ERR_ARG, "order must be 2, 4, 6 or 8");
+  if (b < 1 || b > kMaxB) return fail(PSP_ERR_ARG, "band half-width b must be in 1..4");
+  if (m < 1 || m > kMaxM) return fail(PSP_ERR_ARG, "restart length m must be in 1..64");
+  if (nterms < 1) return fail(PSP_ERR_ARG, "need at least one term");
+  psp_opts o;
+  psp_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.precision != PSP_FP64 && o.precision != PSP_MIXED) return fail(PSP_ERR_ARG, "bad precision");
+  if (o.max_restarts < 1) return fail(PSP_ERR_ARG, "max_restarts must be >= 1");
+  if (!(o.inner_tol > 0.0 && o.inner_tol < 1.0)) return fail(PSP_ERR_ARG, "inner_tol must be in (0, 1)");
+
+  psp_ctx *h = new psp_ctx();
+  h->order = order;
+  h->b = b;
+  h->m = m;
+  h->opts = o;
+  h->mixed = (o.precision == PSP_MIXED);
+  h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  int64_t nn[3] = {1, 1, 1};
+  for (int d = 0; d < grid->ndim; ++d) {
+    if (grid->n[d] < 1 || !(grid->length[d] > 0.0)) {
+      delete h;
+      return fail(PSP_ERR_ARG, "grid sizes and lengths must be positive");
+    }
+    nn[d] = grid->n[d];
+    h->h[d] = grid->length[d] / (double)grid->n[d];
+  }
+  const int64_t n = nn[0] * nn[1] * nn[2];
+  if (n > (int64_t)1 << 31) { delete h; return fail(PSP_ERR_ARG, "at most 2^31 unknowns"); }
+  if (n < 2 * b + 1) { delete h; return fail(PSP_ERR_ARG, "need n >= 2b+1"); }
+  int R = 1;
+  for (int t = 0; t < nterms; ++t) {
+    const psp_term &tm = terms[t];
+    if (tm.k < 1 || tm.k > 4 || tm.dir < 0 || tm.dir >= grid->ndim) {
+      delete h;
+      return fail(PSP_ERR_ARG, "term needs k in 1..4 and 0 <= dir < ndim");
+    }
+    const int r = (tm.k - 1) / 2 + order / 2;
+    if (2 * r + 1 > nn[tm.dir]) { delete h; return fail(PSP_ERR_ARG, "stencil wider than the grid"); }
+    const std::vector<double> w = central_weights(tm.k, order);
+    const double sc = tm.alpha * std::pow(h->h[tm.dir], -(double)tm.k);
+    for (int j = -r; j <= r; ++j) h->wdir[tm.dir][kMaxR + j] += sc * w[j + r];
+    R = std::max(R, r);
+  }
+  h->geo.ndim = grid->ndim;
+  h->geo.nx = (int)nn[0];
+  h->geo.ny = (int)nn[1];
+  h->geo.nz = (int)nn[2];
+  h->geo.n = n;
+  h->geo.R = R;
+  h->ld = round_up(n, 64);
+  h->mmax = o.max_hist_cols > 0 ? o.max_hist_cols : 2 * (m + 1);
+  if (h->mmax < m + 1) h->mmax = m + 1;
+  const size_t es = h->mixed ? sizeof(float) : sizeof(double);
+
+  auto dalloc = [&](void **p, size_t bytes) -> bool {
+    if (cudaMalloc(p, bytes) != cudaSuccess) return false;
+    return cudaMemset(*p, 0, bytes) == cudaSuccess;
+  };
+  bool ok = true;
+  ok = ok && dalloc(&h->V, (size_t)h->ld * (m + 1) * es);
+  ok = ok && dalloc(&h->Px, (size_t)h->ld * h->mmax * es);
+  ok = ok && dalloc(&h->Py, (size_t)h->ld * h->mmax * es);
+  ok = ok && dalloc(&h->Z, (size_t)h->ld * es);
+  ok = ok && dalloc((void **)&h->X, (size_t)h->ld * 8);
+  ok = ok && dalloc((void **)&h->B, (size_t)h->ld * 8);
+  ok = ok && dalloc((void **)&h->partial, (size_t)(kMaxM + 2) * kMaxCta * 8);
+  ok = ok && dalloc((void **)&h->st, sizeof(DevState));
+  ok = ok && dalloc((void **)&h->api_st, sizeof(DevState));
+  ok = ok && dalloc((void **)&h->moments, (size_t)n * (4 * b + 4) * 8);
+  ok = ok && dalloc((void **)&h->band_adopted, (size_t)n * (2 * b + 1) * 8);
+  ok = ok && dalloc((void **)&h->band_cand, (size_t)n * (2 * b + 1) * 8);
+  ok = ok && dalloc((void **)&h->dev_int, 64);
+  if (ok) {
+    h->bs.plan(n, b);
+    for (int s = 0; s < 2 && ok; ++s) {
+      ok = dalloc(&h->slot_mem[s], h->bs.slot_bytes());
+      if (ok) h->bs.bind(h->slot_mem[s], s);
+    }
+    ok = ok && dalloc(&h->apply_mem, h->bs.apply_bytes());
+    if (ok) h->bs.bind_apply(h->apply_mem);
+  }
+  ok = ok && cudaMallocHost((void **)&h->sum_host, sizeof(CycleSummary)) == cudaSuccess;
+  ok = ok && cudaMallocHost((void **)&h->st_host, sizeof(DevState)) == cudaSuccess;
+  ok = ok && cudaMallocHost((void **)&h->int_host, 64) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    psp_destroy(h);
+    return fail(PSP_ERR_OOM, "device or pinned allocation failed");
+  }
+  std::memset(h->st_host, 0, sizeof(DevState));
+  h->st_host->mmax = h->mmax;
+  h->st_host->m = m;
+  h->st_host->inner_tol = o.inner_tol;
+  if (cudaMemcpy(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(h->api_st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
+    psp_destroy(h);
+    return fail(PSP_ERR_CUDA, "state upload failed");
+  }
+  *out = h;
+  return PSP_OK;
+}
+
+psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, double tol, psp_step_info *info) {
+  if (!h || !u_n || !u_np1) return fail(PSP_ERR_ARG, "NULL argument");
+  if (!(tol > 0.0) || !std::isfinite(dt)) return fail(PSP_ERR_ARG, "tol must be > 0 and dt finite");
+  const int64_t n = h->geo.n;
+  if ((u_n < u_np1 + n) && (u_np1 < u_n + n)) return fail(PSP_ERR_ARG, "u_n and u_np1 overlap");
+  cudaStream_t s = h->stream;
+
+  // parameters of this step
+  if (!(h->hist_dt == dt)) {   // A changed: the history no longer describes it
+    h->hist_dt = dt;
+    h->cand = -1;
+    h->rate_ref = -1.0;
+    h->wait = 0;
+    h->wait_len = 1;
+    PSP_CUDA(cudaMemsetAsync(&h->st->hist_count, 0, sizeof(int), s));
+  }
+  set_coef(h, dt, h->st_host->coef);
+  h->st_host->tol = tol;
+  h->st_host->first = 1;
+  PSP_CUDA(cudaMemcpyAsync(h->st->coef, h->st_host->coef, sizeof(h->st_host->coef), cudaMemcpyHostToDevice, s));
+  PSP_CUDA(cudaMemcpyAsync(&h->st->tol, &h->st_host->tol, sizeof(double), cudaMemcpyHostToDevice, s));
+  PSP_CUDA(cudaMemcpyAsync(&h->st->first, &h->st_host->first, sizeof(int), cudaMemcpyHostToDevice, s));
+  PSP_CUDA(cudaMemcpyAsync(h->B, u_n, n * 8, cudaMemcpyDeviceToDevice, s));
+  PSP_CUDA(cudaMemcpyAsync(h->X, u_n, n * 8, cudaMemcpyDeviceToDevice, s));
+
+  int iters = 0, cycles = 0, flags = 0;
+  bool converged = false, numeric = false;
+  double last_R = 0.0, bnorm = 0.0;
+  // the first cycle may try the candidate (acceptance rule: see the design notes)
+  const bool try_cand = (h->cand >= 0 && h->wait == 0);
+  if (!try_cand && h->wait > 0) h->wait -= 1;
+  int cur = try_cand ? h->cand : h->adopted;
+  double trial_beta = -1.0, trial_R = 0.0, main_beta = -1.0, main_R = 0.0;
+  int trial_iters = 0, main_iters = 0;
+  for (int c = 0; c < h->opts.max_restarts; ++c) {
+    const int which = cur < 0 ? 0 : cur + 1;
+    psp_status ps = ensure_graph(h, which);
+    if (ps != PSP_OK) return ps;
+    PSP_CUDA(cudaGraphLaunch(h->graph[which], s));
+    PSP_CUDA(cudaStreamSynchronize(s));
+    const CycleSummary sm = *h->sum_host;
+    cycles += 1;
+    iters += sm.k_end;
+    bnorm = sm.bnorm;
+    if (sm.status & kStNumeric) { numeric = true; break; }
+    if (sm.status & kStBreakdown) flags |= PSP_FLAG_BREAKDOWN;
+    // residual at the end of the cycle: the FP64 true residual of a converged restart
+    // (mixed form) or the Givens estimate R(k_end)
+    const double R_now = (h->mixed && sm.k_end == 0) ? sm.beta : sm.R_end;
+    last_R = h->mixed ? sm.beta : sm.R_end;
+    if (sm.status & kStConverged) converged = true;
+    if (c == 0 && try_cand) {
+      trial_beta = sm.beta;
+      trial_iters = sm.k_end;
+      trial_R = R_now;
+      flags |= PSP_FLAG_CANDIDATE_TRIED;
+      const double r1 = rate_of(sm.R_end, sm.beta, sm.k_end);
+      const bool cycle_done = converged || (sm.R_end <= tol * sm.bnorm);
+      if (!h->opts.accept_rule || cycle_done || h->rate_ref < 0.0 || r1 <= h->rate_ref) {
+        h->adopted = h->cand;
+        h->wait_len = 1;
+        flags |= PSP_FLAG_CANDIDATE_ACCEPTED;
+        PSP_CUDA(cudaMemcpyAsync(h->band_adopted, h->band_cand, (size_t)n * (2 * h->b + 1) * 8,
+                                 cudaMemcpyDeviceToDevice, s));
+      } else {
+        h->wait = h->wait_len;
+        h->wait_len *= 2;
+      }
+      cur = h->adopted;
+      h->cand = -1;
+    } else {
+      if (main_beta < 0.0) main_beta = sm.beta;
+      main_iters += sm.k_end;
+      main_R = R_now;
+    }
+    if (converged) break;
+  }
+  if (main_iters > 0 && main_beta > 0.0) h->rate_ref = rate_of(main_R, main_beta, main_iters);
+  else if (trial_iters > 0 && trial_beta > 0.0) h->rate_ref = rate_of(trial_R, trial_beta, trial_iters);
+
+  psp_status result = PSP_OK;
+  if (numeric) result = fail(PSP_ERR_NUMERIC, "non-finite residual");
+  else if (!converged) result = fail(PSP_ERR_NOCONV, "max_restarts reached");
+  PSP_CUDA(cudaMemcpyAsync(u_np1, h->X, n * 8, cudaMemcpyDeviceToDevice, s));
+
+  // progressive fit of the candidate for the next step (Algorithm 2)
+  int hist = 0;
+  {
+    PSP_CUDA(cudaMemcpyAsync(h->int_host + 2, &h->st->hist_count, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PSP_CUDA(cudaStreamSynchronize(s));
+    hist = std::min(h->int_host[2], h->mmax);
+  }
+  const int need = 2 * h->b + (h->opts.intercept ? 2 : 1);
+  int singular = 0;
+  if (!numeric && hist >= need) {
+    psp_status fs = h->mixed ? fit_into<float>(h, (const float *)h->Px, (const float *)h->Py, h->ld, hist,
+                                               h->band_cand, &singular)
+                             : fit_into<double>(h, (const double *)h->Px, (const double *)h->Py, h->ld, hist,
+                                                h->band_cand, &singular);
+    if (fs != PSP_OK) return fs;
+    if (singular) flags |= PSP_FLAG_SINGULAR_FIT;
+    const int slot = (h->adopted == 0) ? 1 : 0;
+    psp_status f2 = factor_into(h, slot, h->band_cand);
+    if (f2 == PSP_OK) h->cand = slot;
+    else if (f2 == PSP_ERR_NUMERIC) { flags |= PSP_FLAG_FACTOR_FAILED; h->cand = -1; }
+    else return f2;
+  }
+  h->last_singular = singular;
+  if (info) {
+    info->iters = iters;
+    info->cycles = cycles;
+    info->status = result;
+    info->flags = flags;
+    info->rel_res = bnorm > 0.0 ? last_R / bnorm : 0.0;
+    info->hist_cols = hist;
+    info->singular_rows = singular;
+  }
+  return result;
+}
+
+psp_status psp_step_host(psp_handle h, const double *u_n_host, double *u_np1_host, double dt, double tol,
+                         psp_step_info *info) {
+  if (!h || !u_n_host || !u_np1_host) return fail(PSP_ERR_ARG, "NULL argument");
+  const int64_t n = h->geo.n;
+  if (!h->dev_un) {
+    if (cudaMalloc((void **)&h->dev_un, n * 8) != cudaSuccess || cudaMalloc((void **)&h->dev_unp1, n * 8) != cudaSuccess)
+      return fail(PSP_ERR_OOM, "host-step buffers");
+  }
+  PSP_CUDA(cudaMemcpyAsync(h->dev_un, u_n_host, n * 8, cudaMemcpyHostToDevice, h->stream));
+  psp_status st = psp_step(h, h->dev_un, h->dev_unp1, dt, tol, info);
+  if (st != PSP_OK && st != PSP_ERR_NOCONV) return st;
+  PSP_CUDA(cudaMemcpyAsync(u_np1_host, h->dev_unp1, n * 8, cudaMemcpyDeviceToHost, h->stream));
+  PSP_CUDA(cudaStreamSynchronize(h->stream));
+  return st;
+}
+
+psp_status psp_matvec(psp_handle h, const double *x, double *y, double dt) {
+  if (!h || !x || !y) return fail(PSP_ERR_ARG, "NULL argument");
+  set_coef(h, dt, h->st_host->coef);
+  PSP_CUDA(cudaMemcpyAsync(h->api_st->coef, h->st_host->coef, sizeof(h->st_host->coef), cudaMemcpyHostToDevice,
+                           h->stream));
+  launch_stencil<double, double, double>(h->geo, fixed_in<double>(x), fixed_out<double>(y), h->api_st, nullptr, h->stream);
+  PSP_CUDA(cudaGetLastError());
+  PSP_CUDA(cudaStreamSynchronize(h->stream));
+  return PSP_OK;
+}
+
+psp_status psp_matvec_f32(psp_handle h, const float *x, float *y, double dt) {
+  if (!h || !x || !y) return fail(PSP_ERR_ARG, "NULL argument");
+  set_coef(h, dt, h->st_host->coef);
+  PSP_CUDA(cudaMemcpyAsync(h->api_st->coef, h->st_host->coef, sizeof(h->st_host->coef), cudaMemcpyHostToDevice,
+                           h->stream));
+  launch_stencil<float, float, float>(h->geo, fixed_in<float>(x), fixed_out<float>(y), h->api_st, nullptr, h->stream);
+  PSP_CUDA(cudaGetLastError());
+  PSP_CUDA(cudaStreamSynchronize(h->stream));
+  return PSP_OK;
+}
+
+psp_status psp_fit_band(psp_handle h, const double *Px, const double *Py, int64_t ld, int M, double *N_band,
+                        int *singular_rows) {
+  if (!h || !Px || !Py || !N_band) return fail(PSP_ERR_ARG, "NULL argument");
+  if (M < 1 || ld < h->geo.n) return fail(PSP_ERR_ARG, "need M >= 1 and ld >= n");
+  return fit_into<double>(h, Px, Py, ld, M, N_band, singular_rows);
+}
+
+psp_status psp_fit_band_f32(psp_handle h, const float *Px, const float *Py, int64_t ld, int M, double *N_band,
+                            int *singular_rows) {
+  if (!h || !Px || !Py || !N_band) return fail(PSP_ERR_ARG, "NULL argument");
+  if (M < 1 || ld < h->geo.n) return fail(PSP_ERR_ARG, "need M >= 1 and ld >= n");
+  return fit_into<float>(h, Px, Py, ld, M, N_band, singular_rows);
+}
+
+psp_status psp_set_band(psp_handle h, const double *N_band) {
+  if (!h || !N_band) return fail(PSP_ERR_ARG, "NULL argument");
+  const size_t bytes = (size_t)h->geo.n * (2 * h->b + 1) * 8;
+  const int slot = (h->adopted == 0) ? 1 : 0;
+  psp_status s = factor_into(h, slot, N_band);
+  if (s != PSP_OK) return s;
+  PSP_CUDA(cudaMemcpyAsync(h->band_adopted, N_band, bytes, cudaMemcpyDeviceToDevice, h->stream));
+  PSP_CUDA(cudaStreamSynchronize(h->stream));
+  h->adopted = slot;
+  if (h->cand == slot) h->cand = -1;
+  return PSP_OK;
+}
+
+psp_status psp_get_band(psp_handle h, double *N_band) {
+  if (!h || !N_band) return fail(PSP_ERR_ARG, "NULL argument");
+  const int64_t n = h->geo.n;
+  const int W = 2 * h->b + 1;
+  if (h->adopted < 0) {
+    std::vector<double> id((size_t)n * W, 0.0);
+    for (int64_t i = 0; i < n; ++i) id[(size_t)i * W + h->b] = 1.0;
+    PSP_CUDA(cudaMemcpy(N_band, id.data(), id.size() * 8, cudaMemcpyHostToDevice));
+    return PSP_OK;
+  }
+  PSP_CUDA(cudaMemcpyAsync(N_band, h->band_adopted, (size_t)n * W * 8, cudaMemcpyDeviceToDevice, h->stream));
+  PSP_CUDA(cudaStreamSynchronize(h->stream));
+  return PSP_OK;
+}
+
+psp_status psp_apply_precond(psp_handle h, const double *v, double *y, int transpose) {
+  if (!h || !v || !y) return fail(PSP_ERR_ARG, "NULL argument");
+  if (transpose) return fail(PSP_ERR_ARG, "transposed solve is not available");
+  if (h->adopted < 0) {
+    if (v != y) PSP_CUDA(cudaMemcpyAsync(y, v, h->geo.n * 8, cudaMemcpyDeviceToDevice, h->stream));
+    return PSP_OK;
+  }
+  h->bs.apply<double>(h->adopted, v, nullptr, nullptr, fixed_out<double>(y), nullptr, 0, h->stream);
+  PSP_CUDA(cudaGetLastError());
+  return PSP_OK;
+}
+
+psp_status psp_apply_precond_f32(psp_handle h, const float *v, float *y, int transpose) {
+  if (!h || !v || !y) return fail(PSP_ERR_ARG, "NULL argument");
+  if (transpose) return fail(PSP_ERR_ARG, "transposed solve is not available");
+  if (h->adopted < 0) {
+    if (v != y) PSP_CUDA(cudaMemcpyAsync(y, v, h->geo.n * 4, cudaMemcpyDeviceToDevice, h->stream));
+    return PSP_OK;
+  }
+  h->bs.apply<float>(h->adopted, v, nullptr, nullptr, fixed_out<float>(y), nullptr, 0, h->stream);
+  PSP_CUDA(cudaGetLastError());
+  return PSP_OK;
+}
+
+psp_status psp_get_stencil(psp_handle h, double *w_host, int *radius) {
+  if (!h || !radius) return fail(PSP_ERR_ARG, "NULL argument");
+  const int R = h->geo.R;
+  *radius = R;
+  if (w_host)
+    for (int d = 0; d < 3; ++d)
+      for (int j = -R; j <= R; ++j) w_host[d * (2 * R + 1) + j + R] = (d < h->geo.ndim) ? h->wdir[d][kMaxR + j] : 0.0;
+  return PSP_OK;
+}
+
+psp_status psp_reset(psp_handle h) {
+  if (!h) return fail(PSP_ERR_ARG, "NULL argument");
+  h->adopted = -1;
+  h->cand = -1;
+  h->rate_ref = -1.0;
+  h->wait = 0;
+  h->wait_len = 1;
+  h->hist_dt = NAN;
+  PSP_CUDA(cudaMemsetAsync(&h->st->hist_count, 0, sizeof(int), h->stream));
+  PSP_CUDA(cudaStreamSynchronize(h->stream));
+  return PSP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,80 @@
+// Launchers of the libpsp kernels (internal).
+#pragma once
+
+#include "psp_common.cuh"
+
+namespace psp {
+
+// Grid geometry and stencil radius as the kernels see them.
+struct Geometry {
+  int ndim;
+  int nx, ny, nz;
+  int64_t n;
+  int R;   // stencil radius (max over directions)
+};
+
+// Output array that is either a fixed pointer or the ring column selected at run time by
+// a device counter (the history column of the current matvec).
+template <typename T>
+struct OutRef {
+  T *base;
+  int64_t ld;
+  const int *counter;  // nullptr: fixed output `base`
+  int mmax;
+  __device__ __forceinline__ T *get() const {
+    return counter ? base + (int64_t)((*counter) % mmax) * ld : base;
+  }
+};
+
+template <typename T>
+inline OutRef<T> fixed_out(T *p) { return OutRef<T>{p, 0, nullptr, 1}; }
+
+// Read-only counterpart of OutRef.
+template <typename T>
+struct InRef {
+  const T *base;
+  int64_t ld;
+  const int *counter;
+  int mmax;
+  __device__ __forceinline__ const T *get() const {
+    return counter ? base + (int64_t)((*counter) % mmax) * ld : base;
+  }
+};
+template <typename T>
+inline InRef<T> fixed_in(const T *p) { return InRef<T>{p, 0, nullptr, 1}; }
+template <typename T>
+inline InRef<T> ring_in(const T *base, int64_t ld, const int *counter, int mmax) {
+  return InRef<T>{base, ld, counter, mmax};
+}
+template <typename T>
+inline OutRef<T> ring_out(T *base, int64_t ld, const int *counter, int mmax) {
+  return OutRef<T>{base, ld, counter, mmax};
+}
+
+int reduce_grid(int64_t n);
+
+// stencil.cu
+template <typename TI, typename TO, typename TC>
+void launch_stencil(const Geometry &g, InRef<TI> x, OutRef<TO> y, const DevState *st, const int *active,
+                    cudaStream_t s);
+template <typename TH, typename TV>
+void launch_restart(const Geometry &g, const double *X, const double *B, TH *Px, TH *Py, int64_t ldh,
+                    TV *V1, DevState *st, double *partial, int mixed, cudaStream_t s);
+
+// arnoldi.cu
+template <typename T>
+void launch_arnoldi(int k, int64_t n, const T *V, int64_t ldv, const T *Py, int64_t ldh, DevState *st,
+                    double *partial, int mixed, cudaStream_t s);
+template <typename T>
+void launch_scale_copy(int k, int64_t n, const T *V, int64_t ldv, OutRef<T> y, const DevState *st,
+                       cudaStream_t s);
+template <typename T>
+void launch_update_z(int64_t n, const T *V, int64_t ldv, T *Z, double *X, int add_to_x, const DevState *st,
+                     cudaStream_t s);
+
+// band_fit.cu
+template <typename TH>
+void launch_fit(int b, int intercept, int64_t n, int M, const TH *Px, const TH *Py, int64_t ld,
+                double *moments, double *band, int *singular_count, cudaStream_t s);
+
+}  // namespace psp

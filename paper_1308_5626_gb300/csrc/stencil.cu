@@ -1,0 +1,227 @@
+// The matrix-free product A x = x - dt L x (Eqs. 1, 2, 4) on a periodic grid, and the
+// restart residual of Algorithm 1 (P_x(:,i) = X_0, P_y(:,i) = A X_0, R_bar = B - A X_0,
+// V(:,1) = R_bar / ||R_bar||, G(1) = ||R_bar||).
+//
+// L is a sum over directions d of a 1D stencil of radius R (central differences of the
+// configured order, all terms of one direction pre-summed); the coefficients of A for the
+// current dt live in DevState::coef, the centre weight of all directions folded into
+// coef[0][R].  One thread computes one grid point; neighbour loads go through the
+// read-only cache, and the y/z neighbours of a warp's 32 consecutive x points are reused
+// from L1/L2 by the warps of the neighbouring rows.
+#include "psp_kernels.cuh"
+
+namespace psp {
+
+template <typename TI, int NDIM, int R, typename TC>
+__device__ __forceinline__ TC stencil_point(const TI *__restrict__ x, const TC (*c)[2 * R + 1], int ix,
+                                            int iy, int iz, int nx, int ny, int nz) {
+  const int64_t plane = (int64_t)nx * ny;
+  const int64_t base = (int64_t)iz * plane + (int64_t)iy * nx;
+  TC acc = c[0][R] * (TC)__ldg(x + base + ix);
+#pragma unroll
+  for (int j = 1; j <= R; ++j) {
+    int xm = ix - j; xm += (xm < 0) ? nx : 0;
+    int xp = ix + j; xp -= (xp >= nx) ? nx : 0;
+    acc += c[0][R - j] * (TC)__ldg(x + base + xm) + c[0][R + j] * (TC)__ldg(x + base + xp);
+  }
+  if (NDIM >= 2) {
+    const int64_t rowx = (int64_t)iz * plane + ix;
+#pragma unroll
+    for (int j = 1; j <= R; ++j) {
+      int ym = iy - j; ym += (ym < 0) ? ny : 0;
+      int yp = iy + j; yp -= (yp >= ny) ? ny : 0;
+      acc += c[1][R - j] * (TC)__ldg(x + rowx + (int64_t)ym * nx) +
+             c[1][R + j] * (TC)__ldg(x + rowx + (int64_t)yp * nx);
+    }
+  }
+  if (NDIM >= 3) {
+    const int64_t colx = (int64_t)iy * nx + ix;
+#pragma unroll
+    for (int j = 1; j <= R; ++j) {
+      int zm = iz - j; zm += (zm < 0) ? nz : 0;
+      int zp = iz + j; zp -= (zp >= nz) ? nz : 0;
+      acc += c[2][R - j] * (TC)__ldg(x + colx + (int64_t)zm * plane) +
+             c[2][R + j] * (TC)__ldg(x + colx + (int64_t)zp * plane);
+    }
+  }
+  return acc;
+}
+
+template <typename TC, int R>
+__device__ __forceinline__ void load_coef(const DevState *st, TC (*c)[2 * R + 1]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int j = -R; j <= R; ++j) c[d][R + j] = (TC)st->coef[d][kMaxR + j];
+}
+
+// y = A x.  TC is the arithmetic type (float in the mixed form, double otherwise).
+template <typename TI, typename TO, typename TC, int NDIM, int R>
+__global__ void __launch_bounds__(kThreads) k_stencil(InRef<TI> xref, OutRef<TO> yref,
+                                                      const DevState *__restrict__ st, int nx, int ny,
+                                                      int nz, const int *active) {
+  if (active && *active == 0) return;
+  TC c[3][2 * R + 1];
+  load_coef<TC, R>(st, c);
+  const TI *__restrict__ x = xref.get();
+  TO *y = yref.get();
+  const int64_t n = (int64_t)nx * ny * nz;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int ix = (int)(i % nx);
+    int64_t t = i / nx;
+    int iy = (int)(t % ny);
+    int iz = (int)(t / ny);
+    y[i] = (TO)stencil_point<TI, NDIM, R, TC>(x, c, ix, iy, iz, nx, ny, nz);
+  }
+}
+
+// Restart of Algorithm 1 in FP64: AX = A X_0, r = B - AX; store the history pair
+// (X_0, AX) in the ring column hist_count, V~(:,1) = r (normalised lazily through
+// sigma[0] = 1/||r||), G(1) = ||r||; ||B|| sets the step bound eps_abs = tol ||B||.
+template <typename TH, typename TV, int NDIM, int R>
+__global__ void __launch_bounds__(kThreads) k_restart(const double *__restrict__ X,
+                                                      const double *__restrict__ B, TH *Px, TH *Py,
+                                                      int64_t ldh, TV *V1, DevState *st, double *partial,
+                                                      int nx, int ny, int nz, int mixed) {
+  double c[3][2 * R + 1];
+  load_coef<double, R>(st, c);
+  const int col = st->hist_count;
+  TH *px = ring_col(Px, ldh, col, st->mmax);
+  TH *py = ring_col(Py, ldh, col, st->mmax);
+  const int64_t n = (int64_t)nx * ny * nz;
+  double rr = 0.0, bb = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int ix = (int)(i % nx);
+    int64_t t = i / nx;
+    int iy = (int)(t % ny);
+    int iz = (int)(t / ny);
+    double ax = stencil_point<double, NDIM, R, double>(X, c, ix, iy, iz, nx, ny, nz);
+    double b = B[i];
+    double r = b - ax;
+    px[i] = (TH)X[i];
+    py[i] = (TH)ax;
+    V1[i] = (TV)r;
+    rr += r * r;
+    bb += b * b;
+  }
+  __shared__ double s_rr[kThreads / 32], s_bb[kThreads / 32];
+  rr = warp_sum(rr);
+  bb = warp_sum(bb);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { s_rr[wid] = rr; s_bb[wid] = bb; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b2 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += s_rr[w]; b2 += s_bb[w]; }
+    partial[blockIdx.x] = a;
+    partial[kMaxCta + blockIdx.x] = b2;
+  }
+  if (!last_block_arrive(&st->counter[0])) return;
+  __shared__ double s_tot[2];
+  if (wid < 2) {  // warp 0: ||r||^2, warp 1: ||B||^2, fixed order over CTAs
+    double a = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) a += partial[wid * kMaxCta + b];
+    a = warp_sum(a);
+    if (lane == 0) s_tot[wid] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double a = s_tot[0], b2 = s_tot[1];
+    const double beta = sqrt(a);
+    if (st->first) {
+      st->bnorm = sqrt(b2);
+      st->eps_abs = st->tol * st->bnorm;
+      st->first = 0;
+    }
+    st->beta = beta;
+    st->G[0] = beta;
+    st->sigma[0] = beta > 0.0 ? 1.0 / beta : 0.0;
+    st->eps_cycle = mixed ? fmax(st->eps_abs, st->inner_tol * beta) : st->eps_abs;
+    st->k_end = 0;
+    st->status = 0;
+    st->hist_count = col + 1;
+    if (!isfinite(beta)) {
+      st->status = kStNumeric;
+      st->active = 0;
+    } else if (beta == 0.0 || (mixed && beta <= st->eps_abs)) {
+      st->status = kStConverged;
+      st->active = 0;
+    } else {
+      st->active = 1;
+    }
+    st->sum.beta = beta;
+    st->sum.bnorm = st->bnorm;
+    st->sum.k_end = 0;
+    st->sum.status = st->status;
+    st->sum.hist_count = st->hist_count;
+    st->sum.R_end = beta;
+    last_block_reset(&st->counter[0]);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------
+
+int reduce_grid(int64_t n) {
+  int64_t g = (n + kThreads * 4 - 1) / (kThreads * 4);
+  if (g < 1) g = 1;
+  if (g > kMaxCta) g = kMaxCta;
+  return (int)g;
+}
+
+static int stencil_grid(int64_t n) {
+  int64_t g = (n + kThreads - 1) / kThreads;
+  if (g > 152 * 16) g = 152 * 16;
+  return (int)(g < 1 ? 1 : g);
+}
+
+#define PSP_DISPATCH_R(R_, ...)                   \
+  switch (R_) {                                   \
+    case 1: { constexpr int RR = 1; __VA_ARGS__; } break; \
+    case 2: { constexpr int RR = 2; __VA_ARGS__; } break; \
+    case 3: { constexpr int RR = 3; __VA_ARGS__; } break; \
+    case 4: { constexpr int RR = 4; __VA_ARGS__; } break; \
+    case 5: { constexpr int RR = 5; __VA_ARGS__; } break; \
+    default: break;                               \
+  }
+
+#define PSP_DISPATCH_NDIM(D_, ...)                \
+  switch (D_) {                                   \
+    case 1: { constexpr int DD = 1; __VA_ARGS__; } break; \
+    case 2: { constexpr int DD = 2; __VA_ARGS__; } break; \
+    case 3: { constexpr int DD = 3; __VA_ARGS__; } break; \
+    default: break;                               \
+  }
+
+template <typename TI, typename TO, typename TC>
+void launch_stencil(const Geometry &g, InRef<TI> x, OutRef<TO> y, const DevState *st, const int *active,
+                    cudaStream_t s) {
+  const int grid = stencil_grid(g.n);
+  PSP_DISPATCH_NDIM(g.ndim, PSP_DISPATCH_R(g.R, (k_stencil<TI, TO, TC, DD, RR><<<grid, kThreads, 0, s>>>(
+                                                    x, y, st, g.nx, g.ny, g.nz, active))));
+}
+
+template <typename TH, typename TV>
+void launch_restart(const Geometry &g, const double *X, const double *B, TH *Px, TH *Py, int64_t ldh,
+                    TV *V1, DevState *st, double *partial, int mixed, cudaStream_t s) {
+  const int grid = reduce_grid(g.n);
+  PSP_DISPATCH_NDIM(g.ndim, PSP_DISPATCH_R(g.R, (k_restart<TH, TV, DD, RR><<<grid, kThreads, 0, s>>>(
+                                                    X, B, Px, Py, ldh, V1, st, partial, g.nx, g.ny,
+                                                    g.nz, mixed))));
+}
+
+template void launch_stencil<double, double, double>(const Geometry &, InRef<double>, OutRef<double>,
+                                                     const DevState *, const int *, cudaStream_t);
+template void launch_stencil<float, float, float>(const Geometry &, InRef<float>, OutRef<float>,
+                                                  const DevState *, const int *, cudaStream_t);
+template void launch_restart<double, double>(const Geometry &, const double *, const double *, double *,
+                                             double *, int64_t, double *, DevState *, double *, int,
+                                             cudaStream_t);
+template void launch_restart<float, float>(const Geometry &, const double *, const double *, float *,
+                                           float *, int64_t, float *, DevState *, double *, int,
+                                           cudaStream_t);
+
+}  // namespace psp

@@ -1,0 +1,236 @@
+"""ctypes binding of libpsp (the C ABI declared in include/psp.h).
+
+Argument marshalling only: every function below forwards to the C entry point of the
+same name, and every step of the solver runs in libpsp's CUDA kernels.  Device arrays are
+passed as torch CUDA tensors (their data_ptr); the caller's current torch stream is the
+stream handed to psp_create.
+
+There is no CPU fallback: if libpsp.so is missing or was not built, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpsp.so")
+
+PSP_OK, PSP_ERR_ARG, PSP_ERR_CUDA, PSP_ERR_OOM, PSP_ERR_NOCONV, PSP_ERR_NUMERIC, PSP_ERR_DEVICE = range(7)
+PSP_FP64, PSP_MIXED = 0, 1
+PSP_FLAG_SINGULAR_FIT = 0x1
+PSP_FLAG_CANDIDATE_TRIED = 0x2
+PSP_FLAG_CANDIDATE_ACCEPTED = 0x4
+PSP_FLAG_FACTOR_FAILED = 0x8
+PSP_FLAG_BREAKDOWN = 0x10
+
+STATUS_NAMES = {0: "PSP_OK", 1: "PSP_ERR_ARG", 2: "PSP_ERR_CUDA", 3: "PSP_ERR_OOM", 4: "PSP_ERR_NOCONV",
+                5: "PSP_ERR_NUMERIC", 6: "PSP_ERR_DEVICE"}
+
+
+class psp_grid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("length", ctypes.c_double * 3)]
+
+
+class psp_term(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("dir", ctypes.c_int), ("alpha", ctypes.c_double)]
+
+
+class psp_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("intercept", ctypes.c_int), ("max_restarts", ctypes.c_int),
+                ("max_hist_cols", ctypes.c_int), ("inner_tol", ctypes.c_double), ("accept_rule", ctypes.c_int)]
+
+
+class psp_step_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("cycles", ctypes.c_int), ("status", ctypes.c_int),
+                ("flags", ctypes.c_int), ("rel_res", ctypes.c_double), ("hist_cols", ctypes.c_int),
+                ("singular_rows", ctypes.c_int)]
+
+
+# name -> (argtypes)
+_VP = ctypes.c_void_p
+_SIGS = {
+    "psp_default_opts": [ctypes.POINTER(psp_opts)],
+    "psp_create": [ctypes.POINTER(psp_grid), ctypes.c_int, ctypes.POINTER(psp_term), ctypes.c_int, ctypes.c_int,
+                   ctypes.c_int, ctypes.POINTER(psp_opts), _VP, ctypes.POINTER(_VP)],
+    "psp_destroy": [_VP],
+    "psp_step": [_VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(psp_step_info)],
+    "psp_step_host": [_VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(psp_step_info)],
+    "psp_matvec": [_VP, _VP, _VP, ctypes.c_double],
+    "psp_matvec_f32": [_VP, _VP, _VP, ctypes.c_double],
+    "psp_fit_band": [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_int)],
+    "psp_fit_band_f32": [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_int)],
+    "psp_set_band": [_VP, _VP],
+    "psp_get_band": [_VP, _VP],
+    "psp_apply_precond": [_VP, _VP, _VP, ctypes.c_int],
+    "psp_apply_precond_f32": [_VP, _VP, _VP, ctypes.c_int],
+    "psp_get_stencil": [_VP, _VP, ctypes.POINTER(ctypes.c_int)],
+    "psp_reset": [_VP],
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libpsp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libpsp.so is not built; run paper_1308_5626_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, argtypes in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = argtypes
+            fn.restype = ctypes.c_int
+        L.psp_last_error.argtypes = []
+        L.psp_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+class PspError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = lib().psp_last_error().decode(errors="replace")
+        super().__init__("%s: %s (%s)" % (where, STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def _check(status: int, where: str, allow=(PSP_OK,)) -> int:
+    if status not in allow:
+        raise PspError(status, where)
+    return status
+
+
+def _ptr(t) -> int:
+    return int(t.data_ptr())
+
+
+# --------------------------------------------------------------------------------------
+# thin wrappers with the C names
+# --------------------------------------------------------------------------------------
+
+def psp_default_opts() -> psp_opts:
+    o = psp_opts()
+    _check(lib().psp_default_opts(ctypes.byref(o)), "psp_default_opts")
+    return o
+
+
+def psp_create(shape: Sequence[int], order: int, terms: Sequence, b: int, m: int,
+               opts: Optional[psp_opts] = None, stream: int = 0, lengths: Optional[Sequence[float]] = None):
+    g = psp_grid()
+    g.ndim = len(shape)
+    for d in range(3):
+        g.n[d] = int(shape[d]) if d < len(shape) else 1
+        g.length[d] = float(lengths[d]) if lengths is not None and d < len(shape) else (2.0 * math.pi)
+    tt = (psp_term * len(terms))()
+    for i, t in enumerate(terms):
+        k, d, a = (t.k, t.dir, t.alpha) if hasattr(t, "k") else t
+        tt[i].k, tt[i].dir, tt[i].alpha = int(k), int(d), float(a)
+    h = ctypes.c_void_p()
+    _check(lib().psp_create(ctypes.byref(g), int(order), tt, len(terms), int(b), int(m),
+                            ctypes.byref(opts) if opts is not None else None, ctypes.c_void_p(stream),
+                            ctypes.byref(h)), "psp_create")
+    return h
+
+
+def psp_destroy(h) -> None:
+    lib().psp_destroy(h)
+
+
+def psp_step(h, u_n, u_np1, dt: float, tol: float, allow_noconv: bool = False) -> psp_step_info:
+    info = psp_step_info()
+    allow = (PSP_OK, PSP_ERR_NOCONV) if allow_noconv else (PSP_OK,)
+    _check(lib().psp_step(h, _ptr(u_n), _ptr(u_np1), float(dt), float(tol), ctypes.byref(info)), "psp_step", allow)
+    return info
+
+
+def psp_step_host(h, u_n_host, u_np1_host, dt: float, tol: float) -> psp_step_info:
+    """u_n_host / u_np1_host: CPU tensors or numpy arrays of n float64 (contiguous)."""
+    info = psp_step_info()
+    pin = u_n_host.data_ptr() if hasattr(u_n_host, "data_ptr") else u_n_host.ctypes.data
+    pout = u_np1_host.data_ptr() if hasattr(u_np1_host, "data_ptr") else u_np1_host.ctypes.data
+    _check(lib().psp_step_host(h, ctypes.c_void_p(pin), ctypes.c_void_p(pout), float(dt), float(tol),
+                               ctypes.byref(info)), "psp_step_host")
+    return info
+
+
+def psp_matvec(h, x, y, dt: float) -> None:
+    fn = lib().psp_matvec_f32 if str(x.dtype) == "torch.float32" else lib().psp_matvec
+    _check(fn(h, _ptr(x), _ptr(y), float(dt)), "psp_matvec")
+
+
+def psp_fit_band(h, Px, Py, N_band, ld: Optional[int] = None, M: Optional[int] = None) -> int:
+    """Px, Py: torch tensors shaped (M, ld) (row c = history column c); returns singular rows."""
+    M = int(Px.shape[0]) if M is None else int(M)
+    ld = int(Px.shape[1]) if ld is None else int(ld)
+    sing = ctypes.c_int(0)
+    fn = lib().psp_fit_band_f32 if str(Px.dtype) == "torch.float32" else lib().psp_fit_band
+    _check(fn(h, _ptr(Px), _ptr(Py), ld, M, _ptr(N_band), ctypes.byref(sing)), "psp_fit_band")
+    return sing.value
+
+
+def psp_set_band(h, N_band) -> None:
+    _check(lib().psp_set_band(h, _ptr(N_band)), "psp_set_band")
+
+
+def psp_get_band(h, N_band) -> None:
+    _check(lib().psp_get_band(h, _ptr(N_band)), "psp_get_band")
+
+
+def psp_apply_precond(h, v, y, transpose: int = 0) -> None:
+    fn = lib().psp_apply_precond_f32 if str(v.dtype) == "torch.float32" else lib().psp_apply_precond
+    _check(fn(h, _ptr(v), _ptr(y), int(transpose)), "psp_apply_precond")
+
+
+def psp_get_stencil(h):
+    r = ctypes.c_int(0)
+    _check(lib().psp_get_stencil(h, None, ctypes.byref(r)), "psp_get_stencil")
+    w = (ctypes.c_double * (3 * (2 * r.value + 1)))()
+    _check(lib().psp_get_stencil(h, w, ctypes.byref(r)), "psp_get_stencil")
+    R = r.value
+    return [[w[d * (2 * R + 1) + j] for j in range(2 * R + 1)] for d in range(3)], R
+
+
+def psp_reset(h) -> None:
+    _check(lib().psp_reset(h), "psp_reset")
+
+
+# --------------------------------------------------------------------------------------
+# convenience: a handle bound to torch tensors
+# --------------------------------------------------------------------------------------
+
+class Solver:
+    """Owns one psp handle for a workload; vectors are torch CUDA float64 tensors."""
+
+    def __init__(self, shape, order, terms, b, m, precision=PSP_FP64, intercept=1, max_restarts=200,
+                 max_hist_cols=0, inner_tol=1e-5, accept_rule=1, stream=None):
+        import torch
+        o = psp_default_opts()
+        o.precision, o.intercept, o.max_restarts = int(precision), int(intercept), int(max_restarts)
+        o.max_hist_cols, o.inner_tol, o.accept_rule = int(max_hist_cols), float(inner_tol), int(accept_rule)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        self.shape = tuple(int(v) for v in shape)
+        self.n = 1
+        for v in self.shape:
+            self.n *= v
+        self.b = int(b)
+        self.handle = psp_create(self.shape, order, terms, b, m, o, int(s.cuda_stream))
+
+    def step(self, u_n, dt, tol, out=None, allow_noconv=False):
+        import torch
+        out = torch.empty_like(u_n) if out is None else out
+        info = psp_step(self.handle, u_n, out, dt, tol, allow_noconv)
+        return out, info
+
+    def close(self):
+        if self.handle is not None:
+            psp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,57 @@
+"""The C ABI library builds for sm_103a, loads without a GPU and exports every entry point
+that include/psp.h declares (no compute call is made here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "psp.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:psp_status|const char \*|void)\s*\*?\s*(psp_\w+)\s*\(", src, re.M)))
+
+
+@pytest.fixture(scope="module")
+def libpsp():
+    from paper_1308_5626_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("psp_create", "psp_step", "psp_fit_band", "psp_apply_precond", "psp_destroy",
+              "psp_get_band", "psp_set_band", "psp_last_error"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(libpsp):
+    for name in _declared():
+        assert hasattr(libpsp, name), name
+
+
+def test_binding_covers_the_header():
+    from paper_1308_5626_gb300 import psp
+    for name in _declared():
+        if name in ("psp_last_error",):
+            continue
+        assert name in psp._SIGS, name
+
+
+def test_default_opts_without_gpu(libpsp):
+    from paper_1308_5626_gb300 import psp
+    o = psp.psp_default_opts()
+    assert o.precision == psp.PSP_FP64 and o.intercept == 1 and o.max_restarts == 200
+    assert o.accept_rule == 1 and abs(o.inner_tol - 1e-5) < 1e-20
+
+
+def test_argument_errors_need_no_gpu(libpsp):
+    from paper_1308_5626_gb300 import psp
+    h = ctypes.c_void_p()
+    st = psp.lib().psp_create(None, 4, None, 0, 2, 30, None, None, ctypes.byref(h))
+    assert st == psp.PSP_ERR_ARG
+    assert b"NULL" in psp.lib().psp_last_error()
+    assert psp.lib().psp_step(None, None, None, 0.1, 1e-8, None) == psp.PSP_ERR_ARG

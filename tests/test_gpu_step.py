@@ -1,0 +1,164 @@
+"""GPU parity of whole implicit-Euler steps (Algorithm 1 + Algorithm 2) through the C ABI.
+
+* FP64: the step result equals the exact solve A^{-1} u^n within cond(A) * 2 tol (the
+  bound two solutions of relative residual <= tol can differ by); at tol = 1e-12 that is
+  about 1e-10 relative for these workloads.
+* Mixed (FP32 Krylov, FP64 restart residual and update): within 1e-8 relative of the
+  exact solve at tol 1e-10.
+* Iteration counts and the adoption of fitted preconditioners follow the FP64 oracle
+  step by step (CGS2 on the GPU vs MGS in the oracle: equal in exact arithmetic; counts
+  within max(2, 10%) because restarts amplify rounding differences).
+* A short cycle (m <= 8) matches the oracle's R(m) and X to rounding.
+"""
+import numpy as np
+import pytest
+
+from gpu_common import rel, t64, torch_dev
+from oracle import exact
+from oracle.operator import Operator
+from oracle.step import Stepper
+from paper_1308_5626_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return torch_dev()
+
+
+def _solver(w, precision=0, **kw):
+    from paper_1308_5626_gb300 import psp
+    return psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=precision, **kw)
+
+
+def _dt(w, op):
+    return w.dt if w.dt is not None else w.with_dt(op.spectral_radius())
+
+
+SMALL = [inputs.c1(1000), inputs.c2(48, 40), inputs.c3(16, kmax=4)]
+
+
+@pytest.mark.parametrize("w", SMALL, ids=lambda w: w.name)
+def test_fp64_steps_match_exact(dev, w):
+    op = Operator(w.shape, w.order, w.terms)
+    dt = _dt(w, op)
+    kappa = exact.condition_number(op, dt)
+    s = _solver(w)
+    u = t64(w.u0, dev)
+    un = w.u0
+    for step in range(4):
+        u, info = s.step(u, dt, 1e-12)
+        ref = exact.solve_fourier(op, un, dt)
+        got = u.cpu().numpy()
+        assert info.status == 0
+        assert rel(got, ref) <= kappa * 2e-12, (step, rel(got, ref), info.iters)
+        un = got
+    s.close()
+
+
+@pytest.mark.parametrize("w", SMALL, ids=lambda w: w.name)
+def test_mixed_steps_match_exact(dev, w):
+    from paper_1308_5626_gb300 import psp
+    op = Operator(w.shape, w.order, w.terms)
+    dt = _dt(w, op)
+    s = _solver(w, precision=psp.PSP_MIXED)
+    u = t64(w.u0, dev)
+    un = w.u0
+    for step in range(4):
+        u, info = s.step(u, dt, 1e-10)
+        ref = exact.solve_fourier(op, un, dt)
+        got = u.cpu().numpy()
+        assert info.status == 0
+        assert info.rel_res <= 1e-10
+        assert rel(got, ref) <= 1e-8, (step, rel(got, ref))
+        un = got
+    s.close()
+
+
+@pytest.mark.parametrize("w", [inputs.c1(1000), inputs.c3(12, kmax=3)], ids=lambda w: w.name)
+def test_iterations_follow_the_oracle(dev, w):
+    from paper_1308_5626_gb300 import psp
+    op = Operator(w.shape, w.order, w.terms)
+    dt = _dt(w, op)
+    st = Stepper(op, b=w.b, m=w.m)
+    s = _solver(w)
+    u = t64(w.u0, dev)
+    un = w.u0
+    for step in range(6):
+        un, oinfo = st.step(un, dt, w.tol)
+        u, info = s.step(u, dt, w.tol)
+        # restarted cycles amplify rounding differences (see test_long_cycle_invariants)
+        assert abs(info.iters - oinfo.iterations) <= max(2, oinfo.iterations // 10), \
+            (step, info.iters, oinfo.iterations)
+        assert bool(info.flags & psp.PSP_FLAG_CANDIDATE_TRIED) == oinfo.tried_candidate, step
+        assert bool(info.flags & psp.PSP_FLAG_CANDIDATE_ACCEPTED) == oinfo.accepted, step
+        assert rel(u.cpu().numpy(), un) <= exact.condition_number(op, dt) * 4 * w.tol
+    s.close()
+
+
+@pytest.mark.parametrize("m", [3, 5, 8])
+def test_one_short_cycle_matches_oracle(dev, m):
+    """N = I, one restart cycle of m iterations: R(m) and X equal the oracle's to rounding.
+
+    Over short cycles the Krylov basis is well conditioned; over long ones the rounding
+    differences between orthogonalisation orders are amplified (the oracle's own MGS and
+    CGS2 differ by 5e-8 in R(30) on this workload), so long cycles are checked by
+    invariants instead (test_long_cycle_invariants)."""
+    from oracle import gmres
+    from paper_1308_5626_gb300 import psp
+    w = inputs.c1(512)
+    op = Operator(w.shape, w.order, w.terms)
+    s = psp.Solver(w.shape, w.order, w.terms, w.b, m, max_restarts=1)
+    out, info = s.step(t64(w.u0, dev), w.dt, 1e-30, allow_noconv=True)
+    res = gmres.pspgmres(lambda x: op.apply_A(x, w.dt), w.u0, None, 1e-30, m, w.u0, 1, gs="cgs2")
+    assert info.iters == len(res.R) == m
+    np.testing.assert_allclose(info.rel_res * np.linalg.norm(w.u0), res.R[-1], rtol=1e-9)
+    assert rel(out.cpu().numpy(), res.X) <= 1e-11
+    s.close()
+
+
+def test_long_cycle_invariants(dev):
+    """One cycle of m = 30: the GPU's R(m) is a valid GMRES residual (it equals the true
+    residual of the returned X) and lies within 1e-3 of the oracle's."""
+    from oracle import gmres
+    from paper_1308_5626_gb300 import psp
+    w = inputs.c1(512)
+    op = Operator(w.shape, w.order, w.terms)
+    s = psp.Solver(w.shape, w.order, w.terms, w.b, w.m, max_restarts=1)
+    out, info = s.step(t64(w.u0, dev), w.dt, 1e-30, allow_noconv=True)
+    x = out.cpu().numpy()
+    true_res = np.linalg.norm(w.u0 - op.apply_A(x, w.dt))
+    R_gpu = info.rel_res * np.linalg.norm(w.u0)
+    assert abs(true_res - R_gpu) <= 1e-9 * np.linalg.norm(w.u0)
+    res = gmres.pspgmres(lambda x: op.apply_A(x, w.dt), w.u0, None, 1e-30, w.m, w.u0, 1)
+    assert abs(R_gpu / res.R[-1] - 1) <= 1e-3
+    s.close()
+
+
+def test_history_and_dt_change(dev):
+    w = inputs.c1(256)
+    s = _solver(w)
+    u = t64(w.u0, dev)
+    u1, i1 = s.step(u, w.dt, 1e-10)
+    assert i1.hist_cols == min(i1.iters + i1.cycles, 2 * (w.m + 1))
+    u2, i2 = s.step(u1, w.dt * 0.5, 1e-10)
+    assert not (i2.flags & 0x2)             # history cleared: no candidate tried
+    assert i2.hist_cols == min(i2.iters + i2.cycles, 2 * (w.m + 1))
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_2d_step(dev, precision):
+    """The 1024 x 1024 anisotropic workload at the launch configuration the benchmark times."""
+    w = inputs.c2()
+    op = Operator(w.shape, w.order, w.terms)
+    s = _solver(w, precision=precision)
+    u = t64(w.u0, dev)
+    tol = 1e-12 if precision == 0 else 1e-10
+    out, info = s.step(u, w.dt, tol)
+    ref = exact.solve_fourier(op, w.u0, w.dt)
+    bound = exact.condition_number(op, w.dt) * 2 * tol if precision == 0 else 1e-8
+    assert info.status == 0
+    assert rel(out.cpu().numpy(), ref) <= bound
+    s.close()
