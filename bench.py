@@ -1,0 +1,447 @@
+#!/usr/bin/env python
+"""Benchmark: implicit-Euler steps per second of PSP-GMRES on the 2D workload.
+
+Workload (inputs.c2): 2D periodic anisotropic advection-diffusion, 6th-order central FD
+(13-point cross), 1024 x 1024 grid (1,048,576 unknowns, x fastest), GMRES restart m = 40,
+band half-width b = 4, CFL 20, relative tolerance 1e-10, u^0 a seeded Gaussian random
+field with k^-2 spectrum.  One benchmark step = one implicit-Euler step: every restart
+cycle of Algorithm 1 (stencil matvecs, preconditioner solves, CGS2 Arnoldi, Givens,
+update), the Algorithm 2 fit of the next preconditioner and its partitioned
+factorisation, continuing the time series u^{n+1} -> next step.
+
+Arms
+* default (``--impl psp``): the mixed form (FP32 Krylov vectors and kernels, FP64
+  Hessenberg, fit, restart residual and update) timed on the GPU; the plain FP64 GPU form
+  is timed in the same run and reported under "fp64_form"; ``e2e`` repeats the chosen
+  form through psp_step_host with pinned host buffers; ``cpu_baseline`` times the oracle
+  (numpy FP64) on a bounded sample on the host cores.
+* ``--impl reference``: the oracle, as it stands, on the host cores (rank 0 only).
+
+Multi-GPU: replicas (the step does not shard; see the design notes).  Every rank runs
+its own copy of the workload; value = total steps of all ranks / max-over-ranks time.
+
+Timing: W untimed warm-up steps, then K steps between CUDA events on the solver's stream,
+bracketed by a barrier and a device synchronise; the working set (Krylov basis 168 MB,
+history ring 688 MB in the mixed form) is larger than the 129 MB L2, so no flush is used.
+Per-kernel device times come from the library's profiling mode (CUDA event records
+captured inside the cycle graphs), switched on for the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="psp", choices=["psp", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-form", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--nx", type=int, default=1024, help="grid points per direction (default: the full workload)")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------------------
+# clocks
+# --------------------------------------------------------------------------------------
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------------------
+# helpers
+# --------------------------------------------------------------------------------------
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def _kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    cdir = os.path.join(ROOT, "paper_1308_5626_gb300", "csrc")
+    for f in sorted(os.listdir(cdir)):
+        with open(os.path.join(cdir, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_for(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on
+    the current kernel sources; otherwise None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    if d.get("source_hash") != _kernel_source_hash():
+        return None
+    ent = d.get("kernels", {}).get(workload, {}).get(kernel)
+    return None if ent is None else ent.get("dram_bytes_per_launch")
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x: float, world: int, device) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------------------
+
+def _time_form(w, precision, steps, warmup, device, world, profile):
+    import torch
+    from paper_1308_5626_gb300 import psp
+    stream = torch.cuda.Stream(device=device)
+    with torch.cuda.stream(stream):
+        solver = psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=precision, stream=stream)
+        u = torch.tensor(w.u0, dtype=torch.float64, device=device)
+        out = torch.empty_like(u)
+        infos = []
+        for _ in range(warmup):
+            solver.step(u, w.dt, w.tol, out=out)
+            u, out = out, u
+        if profile:
+            psp.psp_set_profiling(solver.handle, True)
+            psp.psp_get_profile(solver.handle, reset=True)
+        torch.cuda.synchronize(device)
+        _barrier(world)
+        torch.cuda.synchronize(device)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        t_host0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(steps):
+            _, info = solver.step(u, w.dt, w.tol, out=out)
+            infos.append(info)
+            u, out = out, u
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        t_host = time.perf_counter() - t_host0
+        _barrier(world)
+        ms = e0.elapsed_time(e1)
+        prof = psp.psp_get_profile(solver.handle, reset=True) if profile else None
+    res = {"ms_total": ms, "host_s": t_host, "infos": infos, "prof": prof, "solver": solver, "u": u,
+           "stream": stream}
+    return res
+
+
+def _e2e(w, precision, steps, device):
+    """Same metric through the C ABI with host buffers: psp_step_host copies u^n from pinned
+    host memory to the device and u^{n+1} back every step."""
+    import torch
+    from paper_1308_5626_gb300 import psp
+    stream = torch.cuda.Stream(device=device)
+    with torch.cuda.stream(stream):
+        solver = psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=precision, stream=stream)
+        a = torch.tensor(w.u0, dtype=torch.float64).pin_memory()
+        b = torch.empty_like(a).pin_memory()
+        for _ in range(2):
+            psp.psp_step_host(solver.handle, a, b, w.dt, w.tol)
+            a, b = b, a
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            psp.psp_step_host(solver.handle, a, b, w.dt, w.tol)
+            a, b = b, a
+        torch.cuda.synchronize(device)
+        dt_s = time.perf_counter() - t0
+        solver.close()
+    n = w.n
+    return {"seconds": dt_s, "unit": "implicit steps/s", "h2d_bytes_per_step": 8 * n,
+            "d2h_bytes_per_step": 8 * n}
+
+
+# --------------------------------------------------------------------------------------
+# CPU oracle (bounded sample)
+# --------------------------------------------------------------------------------------
+
+def _oracle_iterations_per_step(w):
+    """Mean Arnoldi iterations per implicit step of the oracle on this workload, from the
+    committed record written by oracle/record_iterations.py (None if absent)."""
+    p = os.path.join(ROOT, "oracle", "%s_series.json" % w.name.split("_")[0])
+    if not os.path.exists(p):
+        return None, None
+    with open(p) as fh:
+        d = json.load(fh)
+    if d.get("workload") != w.name:
+        return None, None
+    return float(d["mean_iterations"]), float(d["mean_cycles"])
+
+
+def _oracle_sample(w, iters_per_step=None, cycles_per_step=None):
+    """Times the oracle on a bounded sample of one implicit step and scales it to steps/s:
+    one restart cycle of Algorithm 1 (m preconditioned matvecs with MGS, N = I) and one
+    Algorithm 2 fit of the full history ring.  Per-step time = time per Arnoldi iteration
+    x iterations per step + time per restart x restarts per step + fit time."""
+    import numpy as np
+    from oracle import gmres, mrep
+    from oracle.operator import Operator
+    op = Operator(w.shape, w.order, w.terms)
+    A = lambda x: op.apply_A(x, w.dt)
+    t0 = time.perf_counter()
+    res = gmres.pspgmres(A, w.u0, None, 0.0, w.m, w.u0, 1)
+    t_cycle = time.perf_counter() - t0
+    cols = min(len(res.Px), 2 * (w.m + 1))
+    Px = np.stack(res.Px[-cols:], axis=1)
+    Py = np.stack(res.Py[-cols:], axis=1)
+    t1 = time.perf_counter()
+    mrep.mrep(Px, Py, w.b, True)
+    t_fit = time.perf_counter() - t1
+    t_iter = t_cycle / res.iterations
+    if iters_per_step is None:
+        iters_per_step, cycles_per_step = float(w.m), 1.0
+    t_step = t_iter * iters_per_step + t_fit
+    return {"t_iter": t_iter, "t_fit": t_fit, "t_step": t_step, "sample_s": t_cycle + t_fit,
+            "iters_per_step": iters_per_step, "cycles_per_step": cycles_per_step}
+
+
+def _cores_used():
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
+        if os.environ.get(v):
+            return int(os.environ[v])
+    return 1
+
+
+def run_reference(a):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    from paper_1308_5626_gb300 import inputs
+    w = inputs.c2(a.nx)
+    ips, cps = _oracle_iterations_per_step(w)
+    times = []
+    for i in range(a.warmup + a.steps):
+        s = _oracle_sample(w, ips, cps)
+        if i >= a.warmup:
+            times.append(s["t_step"])
+    t = sum(times) / len(times)
+    value = 1.0 / t
+    sample = ("per step: one restart cycle (m=%d Arnoldi iterations, MGS, N=I) and one Algorithm-2 fit timed, "
+              "scaled to %.1f iterations/step from the oracle's own record of this workload" % (w.m, s["iters_per_step"]))
+    line = {"impl": "reference", "metric": "implicit steps/s", "value": value, "unit": "implicit steps/s",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 * t,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "grid": list(w.shape), "order": w.order,
+                                            "m": w.m, "b": w.b, "tol": w.tol},
+            "cpu_baseline": {"value": value, "unit": "implicit steps/s", "cores": _cores_used(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "implicit steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------------------
+# main
+# --------------------------------------------------------------------------------------
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    world, rank, local = _dist()
+    # host-side oracle threads are fixed before numpy loads
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    device = torch.device("cuda:%d" % local)
+    torch.cuda.set_device(device)
+    from paper_1308_5626_gb300 import build, inputs, psp
+    if rank == 0:
+        build.build()
+    _barrier(world)
+    build.build()
+    w = inputs.c2(a.nx)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    mixed = _time_form(w, psp.PSP_MIXED, a.steps, a.warmup, device, world, not a.no_profile)
+    clk = clocks.stop()
+    ms_max = _max_over_ranks(mixed["ms_total"], world, device)
+    value = world * a.steps / (ms_max / 1000.0)
+    infos = mixed["infos"]
+    prof = mixed["prof"]
+    mixed["solver"].close()
+
+    fp64 = None
+    if not a.no_fp64_form:
+        r = _time_form(w, psp.PSP_FP64, a.steps, a.warmup, device, world, False)
+        ms64 = _max_over_ranks(r["ms_total"], world, device)
+        fp64 = {"value": world * a.steps / (ms64 / 1000.0), "ms_per_step": ms64 / a.steps,
+                "iters_per_step": sum(i.iters for i in r["infos"]) / a.steps,
+                "cycles_per_step": sum(i.cycles for i in r["infos"]) / a.steps}
+        r["solver"].close()
+
+    e2e = None
+    if not a.no_e2e:
+        e = _e2e(w, psp.PSP_MIXED, a.steps, device)
+        secs = _max_over_ranks(e.pop("seconds"), world, device)
+        e2e = {"value": world * a.steps / secs}
+        e2e.update(e)
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    hbm_peak, peak_kind = _peaks()
+    roofline = None
+    kernels = {}
+    if prof:
+        for name, d in prof.items():
+            if d["launches"] > 0 and d["ms"] > 0:
+                kernels[name] = {"ms_per_launch": d["ms"] / d["launches"], "launches": d["launches"],
+                                 "bytes_per_launch": d["bytes"] / d["launches"],
+                                 "gbs": d["bytes"] / (d["ms"] * 1e-3) / 1e9,
+                                 "frac": d["bytes"] / (d["ms"] * 1e-3) / 1e9 / hbm_peak,
+                                 "share_of_profiled": 0.0}
+        tot = sum(d["ms"] for d in prof.values()) or 1.0
+        for name in kernels:
+            kernels[name]["share_of_profiled"] = prof[name]["ms"] / tot
+        if kernels:
+            dom = max(kernels, key=lambda k: prof[k]["ms"])
+            kd = kernels[dom]
+            traffic = _traffic_for(dom, w.name)
+            roofline = {"kernel": dom, "bound": "hbm", "achieved": kd["gbs"], "peak": hbm_peak,
+                        "unit": "GB/s", "frac": kd["gbs"] / hbm_peak, "traffic": traffic,
+                        "peak_kind": peak_kind, "bytes_per_launch": kd["bytes_per_launch"],
+                        "ms_per_launch": kd["ms_per_launch"]}
+
+    cpu = None
+    if not a.no_cpu_baseline:
+        ips, cps = _oracle_iterations_per_step(w)
+        if ips is None:
+            ips = sum(i.iters for i in infos) / len(infos)
+            cps = sum(i.cycles for i in infos) / len(infos)
+            src = "the GPU FP64-algorithm count of this run (no oracle record present)"
+        else:
+            src = "the oracle's own record of this workload"
+        s = _oracle_sample(w, ips, cps)
+        cpu = {"value": 1.0 / s["t_step"], "unit": "implicit steps/s", "cores": _cores_used(), "kind": "oracle",
+               "sample": "one restart cycle (m=%d Arnoldi iterations, MGS, N=I) + one Algorithm-2 fit of %d columns "
+                         "timed (%.1f s), scaled to %.1f iterations per step from %s"
+                         % (w.m, min(w.m + 2, 2 * (w.m + 1)), s["sample_s"], ips, src)}
+
+    line = {
+        "metric": "implicit steps/s", "value": value, "unit": "implicit steps/s", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": w.name, "grid": list(w.shape), "order": w.order, "m": w.m, "b": w.b,
+                   "tol": w.tol, "form": "mixed (FP32 Krylov, FP64 Givens/fit/restart residual)",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "working set > L2 (basis 168 MB + history 688 MB), no flush"},
+        "iters_per_step": sum(i.iters for i in infos) / a.steps,
+        "cycles_per_step": sum(i.cycles for i in infos) / a.steps,
+        "rel_res_max": max(i.rel_res for i in infos),
+        "gpu_launches": int(sum(i.launches for i in infos)),
+        "fp64_form": fp64, "e2e": e2e, "roofline": roofline, "kernels": kernels,
+        "cpu_baseline": cpu, "clocks": clk,
+    }
+    if fp64:
+        line["speedup_vs_fp64_form"] = value / fp64["value"]
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

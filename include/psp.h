@@ -97,7 +97,25 @@ typedef struct {
                         PSP_MIXED: FP64 true residual ||u^n - A u^{n+1}|| / ||u^n|| */
   int hist_cols;     /* valid history columns after the step */
   int singular_rows; /* degenerate rows in the fit made after the step */
+  int launches;      /* CUDA kernels this step launched (every kernel node of every
+                        replayed cycle graph, plus the fit and factorisation kernels) */
 } psp_step_info;
+
+/* Kernel classes timed by the profiling mode (psp_set_profiling). */
+enum {
+  PSP_K_PRECOND = 0, /* preconditioner solve Y_k = N^{-1} V(:,k) (all its kernels) */
+  PSP_K_STENCIL = 1, /* matvec U_k = A Y_k */
+  PSP_K_CGS1 = 2,    /* Gram-Schmidt pass 1: h1 = V^T U */
+  PSP_K_CGS2 = 3,    /* pass 2: h2 = V^T (U - V h1) */
+  PSP_K_CGS3 = 4,    /* pass 3: V(:,k+1), Givens, finish test */
+  PSP_K_COUNT = 5
+};
+
+typedef struct {
+  double ms[PSP_K_COUNT];    /* summed device time per kernel class */
+  double bytes[PSP_K_COUNT]; /* summed algorithmic bytes per kernel class */
+  int64_t launches[PSP_K_COUNT]; /* timed launches per kernel class */
+} psp_profile;
 
 /* Fill *opts with the defaults listed above.  Returns PSP_ERR_ARG for NULL. */
 psp_status psp_default_opts(psp_opts *opts);
@@ -106,7 +124,7 @@ psp_status psp_default_opts(psp_opts *opts);
  * Create a solver for A = I - dt L on `grid`, L = sum over `terms` of
  * alpha * h^-k * (central difference of accuracy `order`) (Eqs. 1-2; order in
  * {2,4,6,8}), band half-width b in 1..4 (the paper's d of Algorithm 2), restart length
- * m in 1..128 (n_A of Algorithm 1).  `opts` may be NULL (defaults).  `cuda_stream` is a
+ * m in 1..64 (n_A of Algorithm 1).  `opts` may be NULL (defaults).  `cuda_stream` is a
  * cudaStream_t (NULL = legacy default stream).  Every direction needs n[d] >= 2r+1 for
  * the widest stencil radius r and the grid needs at least 2b+1 points.  Allocates all
  * workspace on the current device; PSP_ERR_OOM if it does not fit.
@@ -177,6 +195,20 @@ psp_status psp_get_stencil(psp_handle h, double *w_host, int *radius);
 
 /* Forget the adopted N, the candidate and the history (back to N = I). */
 psp_status psp_reset(psp_handle h);
+
+/* Profiling mode (off by default).  When on, the captured restart cycles carry CUDA
+ * event records around every kernel class of every fourth Arnoldi iteration (k = 1, 5,
+ * 9, ...), and psp_step adds the device time of those that ran (k <= k_end) to a running
+ * psp_profile,
+ * together with each launch's algorithmic bytes (the reads and writes the operation needs
+ * at least once: see the design notes).  psp_get_profile copies the running totals to
+ * *out (host) and, if reset != 0, zeroes them. */
+psp_status psp_set_profiling(psp_handle h, int enable);
+
+/* Diagnostics: the Givens residuals R(1..k_end) of the last restart cycle of the last
+ * psp_step (Algorithm 1), at most maxk of them, to R_host; *k_end (host) = k_end. */
+psp_status psp_last_cycle_residuals(psp_handle h, double *R_host, int maxk, int *k_end);
+psp_status psp_get_profile(psp_handle h, psp_profile *out, int reset);
 
 #ifdef __cplusplus
 }

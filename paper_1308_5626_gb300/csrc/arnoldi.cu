@@ -23,6 +23,14 @@ template <typename T> struct Vec;
 template <> struct Vec<float> {
   using type = float4;
   static constexpr int W = 4;
+  // A load the compiler may not merge with an earlier load of the same address (the
+  // second sweep of pass 2 re-reads V from L1/L2 instead of holding k vectors in registers).
+  __device__ static __forceinline__ float4 reload(const float4 *p) {
+    float4 r;
+    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "l"(p));
+    return r;
+  }
   __device__ static __forceinline__ float dot(float4 a, float4 b) {
     return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
   }
@@ -33,16 +41,25 @@ template <> struct Vec<float> {
 template <> struct Vec<double> {
   using type = double2;
   static constexpr int W = 2;
+  __device__ static __forceinline__ double2 reload(const double2 *p) {
+    double2 r;
+    asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2];" : "=d"(r.x), "=d"(r.y) : "l"(p));
+    return r;
+  }
   __device__ static __forceinline__ double dot(double2 a, double2 b) { return a.x * b.x + a.y * b.y; }
   __device__ static __forceinline__ double2 axpy(double c, double2 x, double2 y) {
     return make_double2(y.x - c * x.x, y.y - c * x.y);
   }
 };
 
+constexpr int kArnThreads = 512;                 // one CTA of 16 warps per SM
+constexpr int kArnWarps = kArnThreads / 32;
+constexpr int kMaxArnCta = 256;
+
 // Sum NV per-thread values over the CTA; thread j < nvals writes partial[j*kMaxCta + cta].
 template <typename T, int NV>
 __device__ __forceinline__ void cta_partials(const T (&acc)[NV], int nvals, double *partial) {
-  __shared__ double s_red[kThreads / 32][NV];
+  __shared__ double s_red[kArnWarps][NV];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int j = 0; j < NV; ++j) {
@@ -54,44 +71,68 @@ __device__ __forceinline__ void cta_partials(const T (&acc)[NV], int nvals, doub
   __syncthreads();
   for (int j = threadIdx.x; j < nvals; j += blockDim.x) {
     double a = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += s_red[w][j];
+#pragma unroll
+    for (int w = 0; w < kArnWarps; ++w) a += s_red[w][j];
     partial[(int64_t)j * kMaxCta + blockIdx.x] = a;
   }
 }
 
-// In the last CTA: out[j] = sum over CTAs of partial[j][cta], fixed order, j < nvals.
+// In the last CTA: out[j] = sum over CTAs of partial[j][cta] in a fixed order, j < nvals.
+// Every load is issued before any add (warp w takes j = w, w + 16, ...; lane l takes CTAs
+// l, l + 32, ...).
 __device__ __forceinline__ void grid_sums(const double *partial, int nvals, double *out) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  constexpr int MJ = (kMaxM + 2 + kArnWarps - 1) / kArnWarps;
+  constexpr int MB = kMaxArnCta / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nb = gridDim.x;
-  for (int j = wid; j < nvals; j += nw) {
-    const double *p = partial + (int64_t)j * kMaxCta;
-    double a = 0.0;
-    for (int b = lane; b < nb; b += 32) a += p[b];
-    a = warp_sum(a);
-    if (lane == 0) out[j] = a;
+  double a[MJ];
+#pragma unroll
+  for (int t = 0; t < MJ; ++t) {
+    const int j = wid + t * kArnWarps;
+    double s = 0.0;
+    if (j < nvals) {
+      const double *p = partial + (int64_t)j * kMaxCta;
+#pragma unroll
+      for (int q = 0; q < MB; ++q) {
+        const int b = lane + 32 * q;
+        if (b < nb) s += p[b];
+      }
+    }
+    a[t] = s;
+  }
+#pragma unroll
+  for (int t = 0; t < MJ; ++t) {
+    const double s = warp_sum(a[t]);
+    const int j = wid + t * kArnWarps;
+    if (lane == 0 && j < nvals) out[j] = s;
   }
   __syncthreads();
 }
 
 template <typename T, int KC>
-__global__ void __launch_bounds__(kThreads) k_cgs_pass1(const T *__restrict__ V, int64_t ldv, int k,
-                                                        const T *__restrict__ Pyb, int64_t ldh, DevState *st,
-                                                        double *partial, int64_t nv) {
+__global__ void __launch_bounds__(kArnThreads) k_cgs_pass1(const T *__restrict__ V, int64_t ldv, int k,
+                                                           const T *__restrict__ Pyb, int64_t ldh, DevState *st,
+                                                           double *partial, int64_t nv) {
   if (st->active == 0) return;
   using VT = typename Vec<T>::type;
   const VT *U = reinterpret_cast<const VT *>(ring_col(Pyb, ldh, st->hist_count, st->mmax));
   T acc[KC + 1];
 #pragma unroll
   for (int j = 0; j <= KC; ++j) acc[j] = (T)0;
-  for (int64_t iv = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; iv < nv;
-       iv += (int64_t)gridDim.x * blockDim.x) {
-    const VT u = U[iv];
-    acc[KC] += Vec<T>::dot(u, u);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t iv = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; iv < nv; iv += 2 * stride) {
+    const int64_t iv2 = iv + stride;
+    const bool two = iv2 < nv;
+    const VT u0 = U[iv];
+    const VT u1 = two ? U[iv2] : VT{};
+    acc[KC] += Vec<T>::dot(u0, u0) + Vec<T>::dot(u1, u1);
 #pragma unroll
     for (int j = 0; j < KC; ++j) {
       if (j < k) {
-        const VT v = reinterpret_cast<const VT *>(V + j * ldv)[iv];
-        acc[j] += Vec<T>::dot(v, u);
+        const VT *vj = reinterpret_cast<const VT *>(V + j * ldv);
+        const VT v0 = vj[iv];
+        const VT v1 = two ? vj[iv2] : VT{};
+        acc[j] += Vec<T>::dot(v0, u0) + Vec<T>::dot(v1, u1);
       }
     }
   }
@@ -101,7 +142,7 @@ __global__ void __launch_bounds__(kThreads) k_cgs_pass1(const T *__restrict__ V,
   for (int j = 0; j <= KC; ++j) acc2[j] = (j < k) ? acc[j] : ((j == k) ? acc[KC] : (T)0);
   cta_partials<T, KC + 1>(acc2, k + 1, partial);
   if (!last_block_arrive(&st->counter[1])) return;
-  __shared__ double s_sum[kMaxM + 1];
+  __shared__ double s_sum[kMaxM + 2];
   grid_sums(partial, k + 1, s_sum);
   for (int j = threadIdx.x; j <= k; j += blockDim.x) {
     if (j < k) st->h1[j] = st->sigma[j] * s_sum[j];
@@ -111,9 +152,9 @@ __global__ void __launch_bounds__(kThreads) k_cgs_pass1(const T *__restrict__ V,
 }
 
 template <typename T, int KC>
-__global__ void __launch_bounds__(kThreads) k_cgs_pass2(const T *__restrict__ V, int64_t ldv, int k,
-                                                        const T *__restrict__ Pyb, int64_t ldh, DevState *st,
-                                                        double *partial, int64_t nv) {
+__global__ void __launch_bounds__(kArnThreads) k_cgs_pass2(const T *__restrict__ V, int64_t ldv, int k,
+                                                           const T *__restrict__ Pyb, int64_t ldh, DevState *st,
+                                                           double *partial, int64_t nv) {
   if (st->active == 0) return;
   using VT = typename Vec<T>::type;
   __shared__ T s_c[KC];
@@ -123,19 +164,31 @@ __global__ void __launch_bounds__(kThreads) k_cgs_pass2(const T *__restrict__ V,
   T acc[KC];
 #pragma unroll
   for (int j = 0; j < KC; ++j) acc[j] = (T)0;
-  for (int64_t iv = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; iv < nv;
-       iv += (int64_t)gridDim.x * blockDim.x) {
-    VT u = U[iv];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t iv = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; iv < nv; iv += 2 * stride) {
+    const int64_t iv2 = iv + stride;
+    const bool two = iv2 < nv;
+    VT u0 = U[iv];
+    VT u1 = two ? U[iv2] : VT{};
 #pragma unroll
-    for (int j = 0; j < KC; ++j)
-      if (j < k) u = Vec<T>::axpy(s_c[j], reinterpret_cast<const VT *>(V + j * ldv)[iv], u);
+    for (int j = 0; j < KC; ++j) {
+      if (j < k) {
+        const VT *vj = reinterpret_cast<const VT *>(V + j * ldv);
+        u0 = Vec<T>::axpy(s_c[j], vj[iv], u0);
+        if (two) u1 = Vec<T>::axpy(s_c[j], vj[iv2], u1);
+      }
+    }
 #pragma unroll
-    for (int j = 0; j < KC; ++j)
-      if (j < k) acc[j] += Vec<T>::dot(reinterpret_cast<const VT *>(V + j * ldv)[iv], u);
+    for (int j = 0; j < KC; ++j) {
+      if (j < k) {
+        const VT *vj = reinterpret_cast<const VT *>(V + j * ldv);
+        acc[j] += Vec<T>::dot(Vec<T>::reload(vj + iv), u0) + (two ? Vec<T>::dot(Vec<T>::reload(vj + iv2), u1) : (T)0);
+      }
+    }
   }
   cta_partials<T, KC>(acc, k, partial);
   if (!last_block_arrive(&st->counter[2])) return;
-  __shared__ double s_sum[kMaxM + 1];
+  __shared__ double s_sum[kMaxM + 2];
   grid_sums(partial, k, s_sum);
   for (int j = threadIdx.x; j < k; j += blockDim.x) st->h2[j] = st->sigma[j] * s_sum[j];
   last_block_reset(&st->counter[2]);
@@ -196,9 +249,9 @@ __device__ void arnoldi_finish(DevState *st, int k, double nu, int mixed) {
 }
 
 template <typename T, int KC>
-__global__ void __launch_bounds__(kThreads) k_cgs_pass3(T *__restrict__ V, int64_t ldv, int k,
-                                                        const T *__restrict__ Pyb, int64_t ldh, DevState *st,
-                                                        double *partial, int64_t nv, int mixed) {
+__global__ void __launch_bounds__(kArnThreads) k_cgs_pass3(T *__restrict__ V, int64_t ldv, int k,
+                                                           const T *__restrict__ Pyb, int64_t ldh, DevState *st,
+                                                           double *partial, int64_t nv, int mixed) {
   if (st->active == 0) return;
   using VT = typename Vec<T>::type;
   __shared__ T s_c[KC];
@@ -208,18 +261,30 @@ __global__ void __launch_bounds__(kThreads) k_cgs_pass3(T *__restrict__ V, int64
   const VT *U = reinterpret_cast<const VT *>(ring_col(Pyb, ldh, st->hist_count, st->mmax));
   VT *Vout = reinterpret_cast<VT *>(V + (int64_t)k * ldv);
   T acc[1] = {(T)0};
-  for (int64_t iv = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; iv < nv;
-       iv += (int64_t)gridDim.x * blockDim.x) {
-    VT u = U[iv];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t iv = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; iv < nv; iv += 2 * stride) {
+    const int64_t iv2 = iv + stride;
+    const bool two = iv2 < nv;
+    VT u0 = U[iv];
+    VT u1 = two ? U[iv2] : VT{};
 #pragma unroll
-    for (int j = 0; j < KC; ++j)
-      if (j < k) u = Vec<T>::axpy(s_c[j], reinterpret_cast<const VT *>(V + j * ldv)[iv], u);
-    Vout[iv] = u;
-    acc[0] += Vec<T>::dot(u, u);
+    for (int j = 0; j < KC; ++j) {
+      if (j < k) {
+        const VT *vj = reinterpret_cast<const VT *>(V + j * ldv);
+        u0 = Vec<T>::axpy(s_c[j], vj[iv], u0);
+        if (two) u1 = Vec<T>::axpy(s_c[j], vj[iv2], u1);
+      }
+    }
+    Vout[iv] = u0;
+    acc[0] += Vec<T>::dot(u0, u0);
+    if (two) {
+      Vout[iv2] = u1;
+      acc[0] += Vec<T>::dot(u1, u1);
+    }
   }
   cta_partials<T, 1>(acc, 1, partial);
   if (!last_block_arrive(&st->counter[3])) return;
-  __shared__ double s_sum[1];
+  __shared__ double s_sum[kMaxM + 2];
   grid_sums(partial, 1, s_sum);
   if (threadIdx.x == 0) arnoldi_finish(st, k, s_sum[0], mixed);
   __syncthreads();
@@ -257,21 +322,38 @@ __global__ void __launch_bounds__(kThreads) k_update_z(int64_t n, const T *__res
 
 // ---------------------------------------------------------------------------------------
 
+int arnoldi_grid() {
+  static int g = 0;
+  if (g == 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    g = sms > 0 ? std::min(sms, kMaxArnCta) : 152;
+  }
+  return g;
+}
+
 template <typename T>
 void launch_arnoldi(int k, int64_t n, const T *V, int64_t ldv, const T *Py, int64_t ldh, DevState *st,
-                    double *partial, int mixed, cudaStream_t s) {
+                    double *partial, int mixed, cudaStream_t s, cudaEvent_t *ev) {
   const int64_t nv = (n + Vec<T>::W - 1) / Vec<T>::W;
-  int grid = (int)std::min<int64_t>((nv + kThreads - 1) / kThreads, 304);
+  int grid = (int)std::min<int64_t>((nv + kArnThreads - 1) / kArnThreads, arnoldi_grid());
   if (grid < 1) grid = 1;
-#define PSP_CGS(KC_)                                                                                  \
-  k_cgs_pass1<T, KC_><<<grid, kThreads, 0, s>>>(V, ldv, k, Py, ldh, st, partial, nv);              \
-  k_cgs_pass2<T, KC_><<<grid, kThreads, 0, s>>>(V, ldv, k, Py, ldh, st, partial, nv);              \
-  k_cgs_pass3<T, KC_><<<grid, kThreads, 0, s>>>(const_cast<T *>(V), ldv, k, Py, ldh, st, partial, nv, \
-                                                mixed);
-  if (k <= 8) { PSP_CGS(8) }
-  else if (k <= 16) { PSP_CGS(16) }
-  else if (k <= 32) { PSP_CGS(32) }
-  else { PSP_CGS(64) }
+#define PSP_CGS(KC_)                                                                                   \
+  case KC_ / 4:                                                                                        \
+    k_cgs_pass1<T, KC_><<<grid, kArnThreads, 0, s>>>(V, ldv, k, Py, ldh, st, partial, nv);             \
+    if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);                               \
+    k_cgs_pass2<T, KC_><<<grid, kArnThreads, 0, s>>>(V, ldv, k, Py, ldh, st, partial, nv);             \
+    if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);                               \
+    k_cgs_pass3<T, KC_><<<grid, kArnThreads, 0, s>>>(const_cast<T *>(V), ldv, k, Py, ldh, st, partial, \
+                                                     nv, mixed);                                       \
+    if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);                               \
+    break;
+  switch ((k + 3) / 4) {
+    PSP_CGS(4) PSP_CGS(8) PSP_CGS(12) PSP_CGS(16) PSP_CGS(20) PSP_CGS(24) PSP_CGS(28) PSP_CGS(32)
+    PSP_CGS(36) PSP_CGS(40) PSP_CGS(44) PSP_CGS(48) PSP_CGS(52) PSP_CGS(56) PSP_CGS(60) PSP_CGS(64)
+    default: break;
+  }
 #undef PSP_CGS
 }
 
@@ -290,9 +372,9 @@ void launch_update_z(int64_t n, const T *V, int64_t ldv, T *Z, double *X, int ad
 }
 
 template void launch_arnoldi<float>(int, int64_t, const float *, int64_t, const float *, int64_t, DevState *,
-                                    double *, int, cudaStream_t);
+                                    double *, int, cudaStream_t, cudaEvent_t *);
 template void launch_arnoldi<double>(int, int64_t, const double *, int64_t, const double *, int64_t,
-                                     DevState *, double *, int, cudaStream_t);
+                                     DevState *, double *, int, cudaStream_t, cudaEvent_t *);
 template void launch_scale_copy<float>(int, int64_t, const float *, int64_t, OutRef<float>, const DevState *,
                                        cudaStream_t);
 template void launch_scale_copy<double>(int, int64_t, const double *, int64_t, OutRef<double>,

@@ -80,6 +80,8 @@ int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
 using namespace psp;
 
+constexpr int kProfileEvery = 4;   // profiling samples iterations 1, 5, 9, ...
+
 struct psp_ctx {
   Geometry geo{};
   double h[3] = {0, 0, 0};
@@ -119,6 +121,10 @@ struct psp_ctx {
   int last_singular = 0;
 
   cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};   // [0] N = I, [1] slot 0, [2] slot 1
+  int graph_kernels[3] = {0, 0, 0};                          // kernel nodes per graph
+  bool profiling = false;
+  cudaEvent_t ev[3][kMaxM][6] = {};                          // profiling events per graph
+  psp_profile prof{};
   double *hostbuf = nullptr;   // pinned staging for psp_step_host
   double *dev_un = nullptr, *dev_unp1 = nullptr;
 };
@@ -145,17 +151,26 @@ void enqueue_cycle(psp_ctx *h, int slot, cudaStream_t s) {
   const Geometry &g = h->geo;
   launch_restart<T, T>(g, h->X, h->B, Px, Py, h->ld, V, h->st, h->partial, h->mixed ? 1 : 0, s);
   const int *active = &h->st->active;
+  const int which = slot + 1;
   for (int k = 1; k <= h->m; ++k) {
+    // profiling samples one iteration in kProfileEvery
+    cudaEvent_t *ev = (h->profiling && (k - 1) % kProfileEvery == 0) ? h->ev[which][k - 1] : nullptr;
     OutRef<T> pxcol = ring_out<T>(Px, h->ld, &h->st->hist_count, h->mmax);
     OutRef<T> pycol = ring_out<T>(Py, h->ld, &h->st->hist_count, h->mmax);
+    if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
     if (slot < 0) {
-      launch_scale_copy<T>(k, g.n, V, h->ld, pxcol, h->st, s);
+      // N = I: Y_k = V(:,k); one kernel writes P_x(:,i) = Y_k and P_y(:,i) = A Y_k
+      if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
+      launch_stencil<T, T, T>(g, fixed_in<T>(V + (int64_t)(k - 1) * h->ld), pycol, h->st, active, s, pxcol,
+                              &h->st->sigma[k - 1]);
     } else {
       h->bs.apply<T>(slot, V + (int64_t)(k - 1) * h->ld, &h->st->sigma[k - 1], active, pxcol, nullptr, 0, s);
+      if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
+      // U_k = A Y_k, read back from the ring column just written
+      launch_stencil<T, T, T>(g, ring_in<T>(Px, h->ld, &h->st->hist_count, h->mmax), pycol, h->st, active, s);
     }
-    // U_k = A Y_k, read back from the ring column just written
-    launch_stencil<T, T, T>(g, ring_in<T>(Px, h->ld, &h->st->hist_count, h->mmax), pycol, h->st, active, s);
-    launch_arnoldi<T>(k, g.n, V, h->ld, Py, h->ld, h->st, h->partial, h->mixed ? 1 : 0, s);
+    if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);
+    launch_arnoldi<T>(k, g.n, V, h->ld, Py, h->ld, h->st, h->partial, h->mixed ? 1 : 0, s, ev ? ev + 3 : nullptr);
   }
   if (slot < 0) {
     launch_update_z<T>(g.n, V, h->ld, Z, h->X, 1, h->st, s);
@@ -174,6 +189,16 @@ psp_status capture(psp_ctx *h, int which) {
   else enqueue_cycle<double>(h, slot, h->cap);
   cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
   if (e != cudaSuccess) return fail(PSP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  size_t nn = 0;
+  cudaGraphGetNodes(graph, nullptr, &nn);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  cudaGraphGetNodes(graph, nodes.data(), &nn);
+  int kn = 0;
+  for (size_t i = 0; i < nn; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kn;
+  }
+  h->graph_kernels[which] = kn;
   e = cudaGraphInstantiate(&h->graph[which], graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return fail(PSP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
@@ -189,7 +214,10 @@ psp_status ensure_graph(psp_ctx *h, int which) {
 psp_status factor_into(psp_ctx *h, int slot, const double *band) {
   PSP_CUDA(cudaMemsetAsync(h->dev_int, 0, sizeof(int), h->stream));
   h->bs.factor(slot, band, h->dev_int, h->stream);
-  PSP_CUDA(cudaGetLastError());
+  {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(PSP_ERR_CUDA, std::string("band factorisation launch: ") + cudaGetErrorString(e));
+  }
   PSP_CUDA(cudaMemcpyAsync(h->int_host, h->dev_int, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   PSP_CUDA(cudaStreamSynchronize(h->stream));
   if (h->int_host[0]) return fail(PSP_ERR_NUMERIC, "band factorisation: zero or non-finite pivot");
@@ -200,11 +228,40 @@ template <typename TH>
 psp_status fit_into(psp_ctx *h, const TH *Px, const TH *Py, int64_t ld, int M, double *band, int *singular) {
   PSP_CUDA(cudaMemsetAsync(h->dev_int + 1, 0, sizeof(int), h->stream));
   launch_fit<TH>(h->b, h->opts.intercept, h->geo.n, M, Px, Py, ld, h->moments, band, h->dev_int + 1, h->stream);
-  PSP_CUDA(cudaGetLastError());
+  {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(PSP_ERR_CUDA, std::string("band fit launch: ") + cudaGetErrorString(e));
+  }
   PSP_CUDA(cudaMemcpyAsync(h->int_host + 1, h->dev_int + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   PSP_CUDA(cudaStreamSynchronize(h->stream));
   if (singular) *singular = h->int_host[1];
   return PSP_OK;
+}
+
+// Add the device time of the sampled iterations among 1..k_end of the last replay of graph
+// `which`.
+void accumulate_profile(psp_ctx *h, int which, int k_end) {
+  const double s = h->mixed ? 4.0 : 8.0;
+  const double n = (double)h->geo.n;
+  for (int k = 1; k <= k_end; k += kProfileEvery) {
+    cudaEvent_t *ev = h->ev[which][k - 1];
+    float ms[5];
+    for (int c = 0; c < 5; ++c)
+      if (cudaEventElapsedTime(&ms[c], ev[c], ev[c + 1]) != cudaSuccess) {
+        ms[c] = 0.0f;
+        cudaGetLastError();   // a failed query must not surface as a later launch error
+      }
+    // N = I: the fused stencil reads V(:,k) and writes P_x and P_y columns (class 1;
+    // class 0 is then empty)
+    const double bytes[5] = {(which == 0 ? 0.0 : (2.0 * h->b + 3.0)) * s * n, (which == 0 ? 3.0 : 2.0) * s * n,
+                             (k + 1.0) * s * n, (k + 1.0) * s * n, (k + 2.0) * s * n};
+    for (int c = 0; c < 5; ++c) {
+      if (bytes[c] == 0.0) continue;
+      h->prof.ms[c] += ms[c];
+      h->prof.bytes[c] += bytes[c];
+      h->prof.launches[c] += 1;
+    }
+  }
 }
 
 double rate_of(double R_end, double beta, int k) {
@@ -233,6 +290,10 @@ psp_status psp_destroy(psp_handle h) {
   if (!h) return PSP_OK;
   for (auto &g : h->graph)
     if (g) cudaGraphExecDestroy(g);
+  for (auto &a : h->ev)
+    for (auto &b : a)
+      for (auto &e : b)
+        if (e) cudaEventDestroy(e);
   void *dev[] = {h->V, h->Px, h->Py, h->Z, h->X, h->B, h->partial, h->st, h->api_st, h->moments,
                  h->band_adopted, h->band_cand, h->dev_int, h->slot_mem[0], h->slot_mem[1], h->apply_mem,
                  h->dev_un, h->dev_unp1};
@@ -290,12 +351,13 @@ psp_status psp_create(const psp_grid *grid, int order, const psp_term *terms, in
       return fail(PSP_ERR_ARG, "term needs k in 1..4 and 0 <= dir < ndim");
     }
     const int r = (tm.k - 1) / 2 + order / 2;
-    if (2 * r + 1 > nn[tm.dir]) { delete h; return fail(PSP_ERR_ARG, "stencil wider than the grid"); }
     const std::vector<double> w = central_weights(tm.k, order);
     const double sc = tm.alpha * std::pow(h->h[tm.dir], -(double)tm.k);
     for (int j = -r; j <= r; ++j) h->wdir[tm.dir][kMaxR + j] += sc * w[j + r];
     R = std::max(R, r);
   }
+  for (int d = 0; d < grid->ndim; ++d)
+    if (2 * R + 1 > nn[d]) { delete h; return fail(PSP_ERR_ARG, "every direction needs n >= 2R+1 (R: widest stencil radius)"); }
   h->geo.ndim = grid->ndim;
   h->geo.nx = (int)nn[0];
   h->geo.ny = (int)nn[1];
@@ -306,6 +368,7 @@ psp_status psp_create(const psp_grid *grid, int order, const psp_term *terms, in
   h->mmax = o.max_hist_cols > 0 ? o.max_hist_cols : 2 * (m + 1);
   if (h->mmax < m + 1) h->mmax = m + 1;
   const size_t es = h->mixed ? sizeof(float) : sizeof(double);
+  arnoldi_grid();
 
   auto dalloc = [&](void **p, size_t bytes) -> bool {
     if (cudaMalloc(p, bytes) != cudaSuccess) return false;
@@ -382,7 +445,7 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
   PSP_CUDA(cudaMemcpyAsync(h->B, u_n, n * 8, cudaMemcpyDeviceToDevice, s));
   PSP_CUDA(cudaMemcpyAsync(h->X, u_n, n * 8, cudaMemcpyDeviceToDevice, s));
 
-  int iters = 0, cycles = 0, flags = 0;
+  int iters = 0, cycles = 0, flags = 0, launches = 0;
   bool converged = false, numeric = false;
   double last_R = 0.0, bnorm = 0.0;
   // the first cycle may try the candidate (acceptance rule: see the design notes)
@@ -400,6 +463,8 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
     const CycleSummary sm = *h->sum_host;
     cycles += 1;
     iters += sm.k_end;
+    launches += h->graph_kernels[which];
+    if (h->profiling) accumulate_profile(h, which, sm.k_end);
     bnorm = sm.bnorm;
     if (sm.status & kStNumeric) { numeric = true; break; }
     if (sm.status & kStBreakdown) flags |= PSP_FLAG_BREAKDOWN;
@@ -459,6 +524,7 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
     if (fs != PSP_OK) return fs;
     if (singular) flags |= PSP_FLAG_SINGULAR_FIT;
     const int slot = (h->adopted == 0) ? 1 : 0;
+    launches += 2 + 2 * (int)h->bs.levels.size() - 1;   // fit + factor/assemble per level
     psp_status f2 = factor_into(h, slot, h->band_cand);
     if (f2 == PSP_OK) h->cand = slot;
     else if (f2 == PSP_ERR_NUMERIC) { flags |= PSP_FLAG_FACTOR_FAILED; h->cand = -1; }
@@ -473,6 +539,7 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
     info->rel_res = bnorm > 0.0 ? last_R / bnorm : 0.0;
     info->hist_cols = hist;
     info->singular_rows = singular;
+    info->launches = launches;
   }
   return result;
 }
@@ -588,6 +655,41 @@ psp_status psp_get_stencil(psp_handle h, double *w_host, int *radius) {
   if (w_host)
     for (int d = 0; d < 3; ++d)
       for (int j = -R; j <= R; ++j) w_host[d * (2 * R + 1) + j + R] = (d < h->geo.ndim) ? h->wdir[d][kMaxR + j] : 0.0;
+  return PSP_OK;
+}
+
+psp_status psp_set_profiling(psp_handle h, int enable) {
+  if (!h) return fail(PSP_ERR_ARG, "NULL argument");
+  const bool on = enable != 0;
+  if (on == h->profiling) return PSP_OK;
+  PSP_CUDA(cudaStreamSynchronize(h->stream));
+  for (int w = 0; w < 3; ++w) {
+    if (h->graph[w]) { cudaGraphExecDestroy(h->graph[w]); h->graph[w] = nullptr; }
+  }
+  if (on && !h->ev[0][0][0]) {
+    for (int w = 0; w < 3; ++w)
+      for (int k = 0; k < h->m; ++k)
+        for (int c = 0; c < 6; ++c) PSP_CUDA(cudaEventCreate(&h->ev[w][k][c]));
+  }
+  h->profiling = on;
+  return PSP_OK;
+}
+
+psp_status psp_last_cycle_residuals(psp_handle h, double *R_host, int maxk, int *k_end) {
+  if (!h || !R_host || !k_end) return fail(PSP_ERR_ARG, "NULL argument");
+  PSP_CUDA(cudaStreamSynchronize(h->stream));
+  int k = 0;
+  PSP_CUDA(cudaMemcpy(&k, &h->st->k_end, sizeof(int), cudaMemcpyDeviceToHost));
+  *k_end = k;
+  if (k > maxk) k = maxk;
+  if (k > 0) PSP_CUDA(cudaMemcpy(R_host, h->st->R, k * sizeof(double), cudaMemcpyDeviceToHost));
+  return PSP_OK;
+}
+
+psp_status psp_get_profile(psp_handle h, psp_profile *out, int reset) {
+  if (!h || !out) return fail(PSP_ERR_ARG, "NULL argument");
+  *out = h->prof;
+  if (reset) h->prof = psp_profile{};
   return PSP_OK;
 }
 

@@ -56,15 +56,19 @@ int reduce_grid(int64_t n);
 // stencil.cu
 template <typename TI, typename TO, typename TC>
 void launch_stencil(const Geometry &g, InRef<TI> x, OutRef<TO> y, const DevState *st, const int *active,
-                    cudaStream_t s);
+                    cudaStream_t s, OutRef<TO> xcopy = OutRef<TO>{nullptr, 0, nullptr, 1},
+                    const double *scale = nullptr);
 template <typename TH, typename TV>
 void launch_restart(const Geometry &g, const double *X, const double *B, TH *Px, TH *Py, int64_t ldh,
                     TV *V1, DevState *st, double *partial, int mixed, cudaStream_t s);
 
 // arnoldi.cu
+int arnoldi_grid();   // CTAs of the Gram-Schmidt passes (one per SM); call once outside capture
+// Three Gram-Schmidt passes of iteration k; if ev != nullptr, ev[0..2] are recorded after
+// passes 1..3 (profiling).
 template <typename T>
 void launch_arnoldi(int k, int64_t n, const T *V, int64_t ldv, const T *Py, int64_t ldh, DevState *st,
-                    double *partial, int mixed, cudaStream_t s);
+                    double *partial, int mixed, cudaStream_t s, cudaEvent_t *ev = nullptr);
 template <typename T>
 void launch_scale_copy(int k, int64_t n, const T *V, int64_t ldv, OutRef<T> y, const DevState *st,
                        cudaStream_t s);

@@ -8,6 +8,8 @@
 // coef[0][R].  One thread computes one grid point; neighbour loads go through the
 // read-only cache, and the y/z neighbours of a warp's 32 consecutive x points are reused
 // from L1/L2 by the warps of the neighbouring rows.
+#include <type_traits>
+
 #include "psp_kernels.cuh"
 
 namespace psp {
@@ -55,24 +57,140 @@ __device__ __forceinline__ void load_coef(const DevState *st, TC (*c)[2 * R + 1]
     for (int j = -R; j <= R; ++j) c[d][R + j] = (TC)st->coef[d][kMaxR + j];
 }
 
-// y = A x.  TC is the arithmetic type (float in the mixed form, double otherwise).
+// y = A (s x) with s = *scale (1 if scale is null).  If xcopy is set, it receives s x (the
+// N = I preconditioner output Y_k = V(:,k), written together with U_k = A Y_k).  TC is
+// the arithmetic type (float in the mixed form, double otherwise).  Grids have fewer than
+// 2^31 points, so the index arithmetic is 32-bit.
 template <typename TI, typename TO, typename TC, int NDIM, int R>
-__global__ void __launch_bounds__(kThreads) k_stencil(InRef<TI> xref, OutRef<TO> yref,
-                                                      const DevState *__restrict__ st, int nx, int ny,
-                                                      int nz, const int *active) {
+__global__ void __launch_bounds__(kThreads) k_stencil(InRef<TI> xref, OutRef<TO> yref, OutRef<TO> xcopy,
+                                                      const double *scale, const DevState *__restrict__ st,
+                                                      int nx, int ny, int nz, const int *active) {
   if (active && *active == 0) return;
   TC c[3][2 * R + 1];
   load_coef<TC, R>(st, c);
   const TI *__restrict__ x = xref.get();
   TO *y = yref.get();
-  const int64_t n = (int64_t)nx * ny * nz;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int ix = (int)(i % nx);
-    int64_t t = i / nx;
-    int iy = (int)(t % ny);
-    int iz = (int)(t / ny);
-    y[i] = (TO)stencil_point<TI, NDIM, R, TC>(x, c, ix, iy, iz, nx, ny, nz);
+  TO *xc = xcopy.base ? xcopy.get() : nullptr;
+  const TC sc = scale ? (TC)(*scale) : (TC)1;
+  const int n = nx * ny * nz;
+  const int plane = nx * ny;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int iz = i / plane;
+    const int rem = i - iz * plane;
+    const int iy = rem / nx;
+    const int ix = rem - iy * nx;
+    const TC v = stencil_point<TI, NDIM, R, TC>(x, c, ix, iy, iz, nx, ny, nz);
+    if (scale) {
+      y[i] = (TO)(sc * v);
+      if (xc) xc[i] = (TO)(sc * (TC)x[i]);
+    } else {
+      y[i] = (TO)v;
+    }
+  }
+}
+
+// Vectorised y = A (s x): each thread computes VW consecutive x points from aligned
+// vector loads (a register window of the row for the x terms, one vector per y/z
+// neighbour row), coefficients staged once per CTA in shared memory.  Needs nx % VW == 0.
+template <typename T> struct SVec;
+template <> struct SVec<float> { using type = float4; static constexpr int W = 4; };
+template <> struct SVec<double> { using type = double2; static constexpr int W = 2; };
+
+template <typename T, int W>
+__device__ __forceinline__ void vload(const T *p, T (&o)[W]) {
+  using VT = typename SVec<T>::type;
+  const VT v = __ldg(reinterpret_cast<const VT *>(p));
+  const T *e = reinterpret_cast<const T *>(&v);
+#pragma unroll
+  for (int i = 0; i < W; ++i) o[i] = e[i];
+}
+
+template <typename T, int NDIM, int R>
+__global__ void __launch_bounds__(kThreads) k_stencil_vec(InRef<T> xref, OutRef<T> yref, OutRef<T> xcopy,
+                                                          const double *scale, const DevState *__restrict__ st,
+                                                          int nx, int ny, int nz, const int *active) {
+  constexpr int W = SVec<T>::W;
+  constexpr int NH = (R + W - 1) / W;          // halo vectors on each side along x
+  if (active && *active == 0) return;
+  __shared__ T s_c[3][2 * R + 1];
+  if (threadIdx.x < 3 * (2 * R + 1)) {
+    const int d = threadIdx.x / (2 * R + 1), j = threadIdx.x % (2 * R + 1);
+    s_c[d][j] = (T)st->coef[d][kMaxR - R + j];
+  }
+  __syncthreads();
+  T c[3][2 * R + 1];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int j = 0; j < 2 * R + 1; ++j) c[d][j] = s_c[d][j];
+  const T *__restrict__ x = xref.get();
+  T *y = yref.get();
+  T *xc = xcopy.base ? xcopy.get() : nullptr;
+  const T sc = scale ? (T)(*scale) : (T)1;
+  const int nxv = nx / W;
+  const int nvec = nxv * ny * nz;
+  const int plane = nx * ny;
+  for (int iv = blockIdx.x * blockDim.x + threadIdx.x; iv < nvec; iv += gridDim.x * blockDim.x) {
+    const int row = iv / nxv;               // row index iy + ny*iz
+    const int xv = iv - row * nxv;
+    const int iz = row / ny;
+    const int iy = row - iz * ny;
+    const int base = row * nx;
+    // x window: vectors xv-NH .. xv+NH (periodic)
+    T win[(2 * NH + 1) * W];
+#pragma unroll
+    for (int h = -NH; h <= NH; ++h) {
+      int v = xv + h;
+      v += (v < 0) ? nxv : 0;
+      v -= (v >= nxv) ? nxv : 0;
+      T t[W];
+      vload<T, W>(x + base + v * W, t);
+#pragma unroll
+      for (int i = 0; i < W; ++i) win[(h + NH) * W + i] = t[i];
+    }
+    T acc[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      T a = c[0][R] * win[NH * W + i];
+#pragma unroll
+      for (int j = 1; j <= R; ++j) a += c[0][R - j] * win[NH * W + i - j] + c[0][R + j] * win[NH * W + i + j];
+      acc[i] = a;
+    }
+    if (NDIM >= 2) {
+#pragma unroll
+      for (int j = 1; j <= R; ++j) {
+        int ym = iy - j; ym += (ym < 0) ? ny : 0;
+        int yp = iy + j; yp -= (yp >= ny) ? ny : 0;
+        T tm[W], tp[W];
+        vload<T, W>(x + iz * plane + ym * nx + xv * W, tm);
+        vload<T, W>(x + iz * plane + yp * nx + xv * W, tp);
+#pragma unroll
+        for (int i = 0; i < W; ++i) acc[i] += c[1][R - j] * tm[i] + c[1][R + j] * tp[i];
+      }
+    }
+    if (NDIM >= 3) {
+#pragma unroll
+      for (int j = 1; j <= R; ++j) {
+        int zm = iz - j; zm += (zm < 0) ? nz : 0;
+        int zp = iz + j; zp -= (zp >= nz) ? nz : 0;
+        T tm[W], tp[W];
+        vload<T, W>(x + zm * plane + iy * nx + xv * W, tm);
+        vload<T, W>(x + zp * plane + iy * nx + xv * W, tp);
+#pragma unroll
+        for (int i = 0; i < W; ++i) acc[i] += c[2][R - j] * tm[i] + c[2][R + j] * tp[i];
+      }
+    }
+    using VT = typename SVec<T>::type;
+    VT out;
+    T *oe = reinterpret_cast<T *>(&out);
+#pragma unroll
+    for (int i = 0; i < W; ++i) oe[i] = sc * acc[i];
+    reinterpret_cast<VT *>(y + base)[xv] = out;
+    if (xc) {
+#pragma unroll
+      for (int i = 0; i < W; ++i) oe[i] = sc * win[NH * W + i];
+      reinterpret_cast<VT *>(xc + base)[xv] = out;
+    }
   }
 }
 
@@ -89,14 +207,14 @@ __global__ void __launch_bounds__(kThreads) k_restart(const double *__restrict__
   const int col = st->hist_count;
   TH *px = ring_col(Px, ldh, col, st->mmax);
   TH *py = ring_col(Py, ldh, col, st->mmax);
-  const int64_t n = (int64_t)nx * ny * nz;
+  const int n = nx * ny * nz;
+  const int plane = nx * ny;
   double rr = 0.0, bb = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int ix = (int)(i % nx);
-    int64_t t = i / nx;
-    int iy = (int)(t % ny);
-    int iz = (int)(t / ny);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int iz = i / plane;
+    const int rem = i - iz * plane;
+    const int iy = rem / nx;
+    const int ix = rem - iy * nx;
     double ax = stencil_point<double, NDIM, R, double>(X, c, ix, iy, iz, nx, ny, nz);
     double b = B[i];
     double r = b - ax;
@@ -198,10 +316,29 @@ static int stencil_grid(int64_t n) {
 
 template <typename TI, typename TO, typename TC>
 void launch_stencil(const Geometry &g, InRef<TI> x, OutRef<TO> y, const DevState *st, const int *active,
-                    cudaStream_t s) {
+                    cudaStream_t s, OutRef<TO> xcopy, const double *scale) {
+  constexpr bool same = std::is_same<TI, TO>::value && std::is_same<TI, TC>::value;
+  if constexpr (same) {
+    constexpr int W = SVec<TI>::W;
+    // vector path: rows split into whole aligned vectors, and more vectors per row than
+    // halo vectors (so one periodic wrap suffices)
+    const int nh = (g.R + W - 1) / W;
+    auto al = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    const bool aligned = (x.counter ? (al(x.base) && (x.ld * sizeof(TI)) % 16 == 0) : al(x.base)) &&
+                         (y.counter ? (al(y.base) && (y.ld * sizeof(TO)) % 16 == 0) : al(y.base)) &&
+                         (!xcopy.base || (xcopy.counter ? (al(xcopy.base) && (xcopy.ld * sizeof(TO)) % 16 == 0)
+                                                        : al(xcopy.base)));
+    if (g.nx % W == 0 && g.nx / W > nh && aligned) {
+      const int64_t nvec = g.n / W;
+      int grid = (int)std::min<int64_t>((nvec + kThreads - 1) / kThreads, 152 * 8);
+      PSP_DISPATCH_NDIM(g.ndim, PSP_DISPATCH_R(g.R, (k_stencil_vec<TI, DD, RR><<<grid, kThreads, 0, s>>>(
+                                                        x, y, xcopy, scale, st, g.nx, g.ny, g.nz, active))));
+      return;
+    }
+  }
   const int grid = stencil_grid(g.n);
   PSP_DISPATCH_NDIM(g.ndim, PSP_DISPATCH_R(g.R, (k_stencil<TI, TO, TC, DD, RR><<<grid, kThreads, 0, s>>>(
-                                                    x, y, st, g.nx, g.ny, g.nz, active))));
+                                                    x, y, xcopy, scale, st, g.nx, g.ny, g.nz, active))));
 }
 
 template <typename TH, typename TV>
@@ -214,9 +351,11 @@ void launch_restart(const Geometry &g, const double *X, const double *B, TH *Px,
 }
 
 template void launch_stencil<double, double, double>(const Geometry &, InRef<double>, OutRef<double>,
-                                                     const DevState *, const int *, cudaStream_t);
+                                                     const DevState *, const int *, cudaStream_t,
+                                                     OutRef<double>, const double *);
 template void launch_stencil<float, float, float>(const Geometry &, InRef<float>, OutRef<float>,
-                                                  const DevState *, const int *, cudaStream_t);
+                                                  const DevState *, const int *, cudaStream_t, OutRef<float>,
+                                                  const double *);
 template void launch_restart<double, double>(const Geometry &, const double *, const double *, double *,
                                              double *, int64_t, double *, DevState *, double *, int,
                                              cudaStream_t);

@@ -45,7 +45,14 @@ class psp_opts(ctypes.Structure):
 class psp_step_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("cycles", ctypes.c_int), ("status", ctypes.c_int),
                 ("flags", ctypes.c_int), ("rel_res", ctypes.c_double), ("hist_cols", ctypes.c_int),
-                ("singular_rows", ctypes.c_int)]
+                ("singular_rows", ctypes.c_int), ("launches", ctypes.c_int)]
+
+
+PSP_K_NAMES = ["precond", "stencil", "cgs_pass1", "cgs_pass2", "cgs_pass3"]
+
+
+class psp_profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 5), ("bytes", ctypes.c_double * 5), ("launches", ctypes.c_int64 * 5)]
 
 
 # name -> (argtypes)
@@ -67,6 +74,9 @@ _SIGS = {
     "psp_apply_precond_f32": [_VP, _VP, _VP, ctypes.c_int],
     "psp_get_stencil": [_VP, _VP, ctypes.POINTER(ctypes.c_int)],
     "psp_reset": [_VP],
+    "psp_set_profiling": [_VP, ctypes.c_int],
+    "psp_get_profile": [_VP, ctypes.POINTER(psp_profile), ctypes.c_int],
+    "psp_last_cycle_residuals": [_VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
 }
 
 _lib = None
@@ -194,6 +204,24 @@ def psp_get_stencil(h):
 
 def psp_reset(h) -> None:
     _check(lib().psp_reset(h), "psp_reset")
+
+
+def psp_set_profiling(h, enable: bool) -> None:
+    _check(lib().psp_set_profiling(h, int(bool(enable))), "psp_set_profiling")
+
+
+def psp_last_cycle_residuals(h, maxk: int = 64):
+    R = (ctypes.c_double * maxk)()
+    k = ctypes.c_int(0)
+    _check(lib().psp_last_cycle_residuals(h, R, int(maxk), ctypes.byref(k)), "psp_last_cycle_residuals")
+    return [R[i] for i in range(min(k.value, maxk))]
+
+
+def psp_get_profile(h, reset: bool = False) -> dict:
+    p = psp_profile()
+    _check(lib().psp_get_profile(h, ctypes.byref(p), int(bool(reset))), "psp_get_profile")
+    return {name: {"ms": p.ms[i], "bytes": p.bytes[i], "launches": int(p.launches[i])}
+            for i, name in enumerate(PSP_K_NAMES)}
 
 
 # --------------------------------------------------------------------------------------

