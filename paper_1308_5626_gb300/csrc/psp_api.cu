@@ -125,6 +125,7 @@ struct psp_ctx {
   bool profiling = false;
   cudaEvent_t ev[3][kMaxM][6] = {};                          // profiling events per graph
   psp_profile prof{};
+  ArnoldiMaps maps{};
   double *hostbuf = nullptr;   // pinned staging for psp_step_host
   double *dev_un = nullptr, *dev_unp1 = nullptr;
 };
@@ -170,7 +171,7 @@ void enqueue_cycle(psp_ctx *h, int slot, cudaStream_t s) {
       launch_stencil<T, T, T>(g, ring_in<T>(Px, h->ld, &h->st->hist_count, h->mmax), pycol, h->st, active, s);
     }
     if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);
-    launch_arnoldi<T>(k, g.n, V, h->ld, Py, h->ld, h->st, h->partial, h->mixed ? 1 : 0, s, ev ? ev + 3 : nullptr);
+    launch_arnoldi<T>(k, g.n, h->maps, V, h->ld, h->st, h->partial, h->mixed ? 1 : 0, s, ev ? ev + 3 : nullptr);
   }
   if (slot < 0) {
     launch_update_z<T>(g.n, V, h->ld, Z, h->X, 1, h->st, s);
@@ -364,11 +365,11 @@ psp_status psp_create(const psp_grid *grid, int order, const psp_term *terms, in
   h->geo.nz = (int)nn[2];
   h->geo.n = n;
   h->geo.R = R;
-  h->ld = round_up(n, 64);
+  h->ld = round_up(n, 512);   // whole 1 KB tiles of the Gram-Schmidt pipeline (FP32 and FP64)
   h->mmax = o.max_hist_cols > 0 ? o.max_hist_cols : 2 * (m + 1);
   if (h->mmax < m + 1) h->mmax = m + 1;
   const size_t es = h->mixed ? sizeof(float) : sizeof(double);
-  arnoldi_grid();
+  arnoldi_setup();
 
   auto dalloc = [&](void **p, size_t bytes) -> bool {
     if (cudaMalloc(p, bytes) != cudaSuccess) return false;
@@ -376,12 +377,13 @@ psp_status psp_create(const psp_grid *grid, int order, const psp_term *terms, in
   };
   bool ok = true;
   ok = ok && dalloc(&h->V, (size_t)h->ld * (m + 1) * es);
+  const int vcols = m + 1;
   ok = ok && dalloc(&h->Px, (size_t)h->ld * h->mmax * es);
   ok = ok && dalloc(&h->Py, (size_t)h->ld * h->mmax * es);
   ok = ok && dalloc(&h->Z, (size_t)h->ld * es);
   ok = ok && dalloc((void **)&h->X, (size_t)h->ld * 8);
   ok = ok && dalloc((void **)&h->B, (size_t)h->ld * 8);
-  ok = ok && dalloc((void **)&h->partial, (size_t)(kMaxM + 2) * kMaxCta * 8);
+  ok = ok && dalloc((void **)&h->partial, (size_t)3 * (kMaxM + 2) * kMaxCta * 8);   // three pass regions
   ok = ok && dalloc((void **)&h->st, sizeof(DevState));
   ok = ok && dalloc((void **)&h->api_st, sizeof(DevState));
   ok = ok && dalloc((void **)&h->moments, (size_t)n * (4 * b + 4) * 8);
@@ -405,6 +407,16 @@ psp_status psp_create(const psp_grid *grid, int order, const psp_term *terms, in
     cudaGetLastError();
     psp_destroy(h);
     return fail(PSP_ERR_OOM, "device or pinned allocation failed");
+  }
+  {
+    const bool enc = h->mixed ? encode_arnoldi_maps<float>(h->maps, (const float *)h->V, vcols, (const float *)h->Py,
+                                                           h->mmax, h->ld)
+                              : encode_arnoldi_maps<double>(h->maps, (const double *)h->V, vcols,
+                                                            (const double *)h->Py, h->mmax, h->ld);
+    if (!enc) {
+      psp_destroy(h);
+      return fail(PSP_ERR_CUDA, "tensor map encoding failed");
+    }
   }
   std::memset(h->st_host, 0, sizeof(DevState));
   h->st_host->mmax = h->mmax;
@@ -466,6 +478,8 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
     launches += h->graph_kernels[which];
     if (h->profiling) accumulate_profile(h, which, sm.k_end);
     bnorm = sm.bnorm;
+    if (sm.error) return fail(PSP_ERR_DEVICE, "device error flag " + std::to_string(sm.error) +
+                                                  " (a bounded wait expired or a launch was misconfigured)");
     if (sm.status & kStNumeric) { numeric = true; break; }
     if (sm.status & kStBreakdown) flags |= PSP_FLAG_BREAKDOWN;
     // residual at the end of the cycle: the FP64 true residual of a converged restart

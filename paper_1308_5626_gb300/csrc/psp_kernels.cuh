@@ -63,12 +63,22 @@ void launch_restart(const Geometry &g, const double *X, const double *B, TH *Px,
                     TV *V1, DevState *st, double *partial, int mixed, cudaStream_t s);
 
 // arnoldi.cu
-int arnoldi_grid();   // CTAs of the Gram-Schmidt passes (one per SM); call once outside capture
+int arnoldi_grid();   // CTAs of the Gram-Schmidt passes (one per SM)
+void arnoldi_setup(); // grid size and shared-memory attributes; call once outside capture
+// Opaque storage of the TMA tensor maps (CUtensorMap, 128 bytes each) of the passes:
+// V with boxes of 16, 4 and 1 columns, and the P_y ring.
+struct alignas(64) ArnoldiMaps {
+  unsigned char V[3 * 128];
+  unsigned char Py[128];
+};
+template <typename T>
+bool encode_arnoldi_maps(ArnoldiMaps &maps, const T *V, int ncols, const T *Py, int mmax, int64_t ld);
+
 // Three Gram-Schmidt passes of iteration k; if ev != nullptr, ev[0..2] are recorded after
 // passes 1..3 (profiling).
 template <typename T>
-void launch_arnoldi(int k, int64_t n, const T *V, int64_t ldv, const T *Py, int64_t ldh, DevState *st,
-                    double *partial, int mixed, cudaStream_t s, cudaEvent_t *ev = nullptr);
+void launch_arnoldi(int k, int64_t n, const ArnoldiMaps &maps, T *V, int64_t ldv, DevState *st, double *partial,
+                    int mixed, cudaStream_t s, cudaEvent_t *ev = nullptr);
 template <typename T>
 void launch_scale_copy(int k, int64_t n, const T *V, int64_t ldv, OutRef<T> y, const DevState *st,
                        cudaStream_t s);

@@ -270,6 +270,7 @@ __global__ void __launch_bounds__(kThreads) k_restart(const double *__restrict__
       st->active = 1;
     }
     st->sum.beta = beta;
+    st->sum.error = st->error;
     st->sum.bnorm = st->bnorm;
     st->sum.k_end = 0;
     st->sum.status = st->status;
