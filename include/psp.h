@@ -175,6 +175,24 @@ psp_status psp_fit_band(psp_handle h, const double *Px, const double *Py, int64_
 psp_status psp_fit_band_f32(psp_handle h, const float *Px, const float *Py, int64_t ld, int M,
                             double *N_band, int *singular_rows);
 
+/*
+ * Allocation-free band fit (the paper has no counterpart: this is a deployment variant of
+ * psp_fit_band above).  For callers that cannot allocate device memory -- e.g. code in an
+ * allocation-free real-time or graph-driven loop, or a plugin given a fixed memory budget --
+ * and so cannot create a handle (psp_create allocates the solver workspace).  Same result
+ * as psp_fit_band for a handle with half-width b and the given intercept flag: Px, Py are
+ * n x M column-major FP64 device arrays (leading dimension ld >= n), N_band the device
+ * output (n x (2b+1) band storage), *singular_rows (host, may be NULL) the count of
+ * degenerate rows.  Work is enqueued on cuda_stream (a cudaStream_t, NULL = legacy default)
+ * and the call returns after it finished if singular_rows is not NULL.
+ * Scratch: a static device array for at most 65536 rows (10 MiB per GPU that loads the
+ * library, kept until exit); larger n returns PSP_ERR_ARG.  The first call on a device
+ * looks up that array's device address (do it before any stream capture).  All calls share
+ * the array: calls that overlap on the GPU race and must be serialised by the caller.
+ */
+psp_status psp_fit_band_static(const double *Px, const double *Py, int64_t ld, int M, int64_t n, int b,
+                               int intercept, double *N_band, int *singular_rows, void *cuda_stream);
+
 /* Factor the device band N_band (half-width b) and adopt it as the preconditioner.
  * Returns PSP_ERR_NUMERIC (and keeps the previous N) if a pivot of the partitioned
  * factorisation is zero or not finite. */

@@ -78,6 +78,11 @@ int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
 }  // namespace
 
+namespace psp {
+// Lets other translation units of the library report through psp_last_error().
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+}  // namespace psp
+
 using namespace psp;
 
 constexpr int kProfileEvery = 4;   // profiling samples iterations 1, 5, 9, ...

@@ -77,6 +77,8 @@ _SIGS = {
     "psp_set_profiling": [_VP, ctypes.c_int],
     "psp_get_profile": [_VP, ctypes.POINTER(psp_profile), ctypes.c_int],
     "psp_last_cycle_residuals": [_VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+    "psp_fit_band_static": [_VP, _VP, ctypes.c_int64, ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _VP,
+                            ctypes.POINTER(ctypes.c_int), _VP],
 }
 
 _lib = None
@@ -177,6 +179,19 @@ def psp_fit_band(h, Px, Py, N_band, ld: Optional[int] = None, M: Optional[int] =
     sing = ctypes.c_int(0)
     fn = lib().psp_fit_band_f32 if str(Px.dtype) == "torch.float32" else lib().psp_fit_band
     _check(fn(h, _ptr(Px), _ptr(Py), ld, M, _ptr(N_band), ctypes.byref(sing)), "psp_fit_band")
+    return sing.value
+
+
+def psp_fit_band_static(Px, Py, N_band, b: int, intercept: int = 1, ld: Optional[int] = None,
+                        M: Optional[int] = None, n: Optional[int] = None, stream: int = 0) -> int:
+    """Allocation-free band fit (no handle): Px, Py FP64 tensors shaped (M, ld); returns the
+    number of degenerate rows."""
+    M = int(Px.shape[0]) if M is None else int(M)
+    ld = int(Px.shape[1]) if ld is None else int(ld)
+    n = ld if n is None else int(n)
+    sing = ctypes.c_int(0)
+    _check(lib().psp_fit_band_static(_ptr(Px), _ptr(Py), ld, M, n, int(b), int(intercept), _ptr(N_band),
+                                     ctypes.byref(sing), ctypes.c_void_p(stream)), "psp_fit_band_static")
     return sing.value
 
 
