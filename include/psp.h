@@ -105,9 +105,9 @@ typedef struct {
 enum {
   PSP_K_PRECOND = 0, /* preconditioner solve Y_k = N^{-1} V(:,k) (all its kernels) */
   PSP_K_STENCIL = 1, /* matvec U_k = A Y_k */
-  PSP_K_CGS1 = 2,    /* Gram-Schmidt pass 1: h1 = V^T U */
-  PSP_K_CGS2 = 3,    /* pass 2: h2 = V^T (U - V h1) */
-  PSP_K_CGS3 = 4,    /* pass 3: V(:,k+1), Givens, finish test */
+  PSP_K_CGS1 = 2,    /* orthogonalisation pass A: block dot products [V, v_j]^T [v_j, w_j] */
+  PSP_K_CGS2 = 3,    /* (unused: the orthogonalisation needs two passes) */
+  PSP_K_CGS3 = 4,    /* pass B: q_j, v_{j+1}, completed Hessenberg column, Givens, finish test */
   PSP_K_COUNT = 5
 };
 

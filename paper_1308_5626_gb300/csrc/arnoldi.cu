@@ -1,18 +1,30 @@
-// Arnoldi step of Algorithm 1 (Gram-Schmidt, H(:,k), V(:,k+1)), the Givens update of the
+// Arnoldi step of Algorithm 1 (orthogonalisation, H(:,k), V(:,k+1)), the Givens update of the
 // Hessenberg least-squares problem with the residual R(k) = |G(k+1)| and the finish test,
 // and the cycle update Z = sum_j Q(j) V(:,j) with Q = H^{-1} G.
 //
-// Gram-Schmidt is classical Gram-Schmidt applied twice (CGS2), equal in exact arithmetic
-// to the modified Gram-Schmidt loop of the paper and as stable in practice, in three
-// streaming passes over the basis:
-//   pass 1: h1 = V^T U                                   (and ||U||^2 for the breakdown test)
-//   pass 2: U' = U - V h1 formed on the fly, h2 = V^T U'
-//   pass 3: V~(:,k+1) = U - V (h1 + h2), nu = ||V~(:,k+1)||^2
-// The basis is stored unnormalised: V(:,j) = sigma_j V~(:,j) with sigma_j = 1/H(j+1,j)
-// kept in FP64, so normalising costs no extra pass.  Each pass reduces per-CTA partial
-// sums in a fixed order in the last CTA to finish (deterministic, no waiting).  The last
-// CTA of pass 3 also runs the FP64 Givens step, the finish test and, when the cycle ends,
-// the triangular solve for Q.
+// The paper orthogonalises with modified Gram-Schmidt, one global reduction per basis
+// vector.  Here the orthogonalisation is classical Gram-Schmidt with re-orthogonalisation
+// delayed by one iteration (DCGS2; Bielich, Langou, Thomas, Swirydowicz, Yamazaki, Boman,
+// "Low-synch Gram-Schmidt with delayed reorthogonalization for Krylov solvers", Parallel
+// Computing 2022): the same Arnoldi relation in exact arithmetic, the stability of CGS2,
+// and only two streaming passes over the basis per iteration j:
+//
+//   pass A (k_dcgs_dots):   a = Q^T v_j, alpha = v_j^T v_j, b = Q^T w_j, beta = v_j^T w_j,
+//                           w_j = A N^{-1} v_j, Q = [q_0 .. q_{j-1}] (per-CTA partial sums);
+//   pass B (k_dcgs_update): every CTA reduces the partials and forms, in FP64,
+//                           nu_j = sqrt(alpha - a^T a)             (q_j = (v_j - Q a) / nu_j),
+//                           column j-1 of H completed: H(:, j-1) = h_{j-1} + a, H(j, j-1) = nu_j,
+//                           t = Hbar a, h_j = ([b; (beta - a^T b)/nu_j] - t) / nu_j,
+//                           then streams q_j and v_{j+1} = w_j/nu_j - (c_j/nu_j) v_j - Q d,
+//                           c = t/nu_j + h_j, d = c_{0..j-1} - (c_j/nu_j) a.
+//
+// CTA 0 of pass B alone owns the persistent state (Hessenberg columns, Givens rotations,
+// R(j), the finish test, the triangular solve at the end of the cycle).  The Krylov
+// vector v_j handed to the preconditioner and the matvec is the once-orthogonalised,
+// unnormalised one; (N^{-1} v_j, A N^{-1} v_j) is still an exact matvec pair for the
+// history of Algorithm 2.  Column j-1 is completed one iteration late, so a cycle runs one
+// matvec past the iteration that meets the tolerance, and a cycle that reaches m columns
+// ends with a reduction-only step.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -40,6 +52,7 @@ template <> struct Vec<float> {
   __device__ static __forceinline__ float4 axpy(float c, float4 x, float4 y) {  // y - c x
     return make_float4(y.x - c * x.x, y.y - c * x.y, y.z - c * x.z, y.w - c * x.w);
   }
+  __device__ static __forceinline__ float4 scale(float c, float4 x) { return make_float4(c * x.x, c * x.y, c * x.z, c * x.w); }
 };
 template <> struct Vec<double> {
   using type = double2;
@@ -53,6 +66,7 @@ template <> struct Vec<double> {
   __device__ static __forceinline__ double2 axpy(double c, double2 x, double2 y) {
     return make_double2(y.x - c * x.x, y.y - c * x.y);
   }
+  __device__ static __forceinline__ double2 scale(double c, double2 x) { return make_double2(c * x.x, c * x.y); }
 };
 
 // ---------------------------------------------------------------------------------------
@@ -267,17 +281,18 @@ __device__ __forceinline__ void write_col_partials(const T (&acc)[KS], int k, do
 // length kMaxCta).  Warp w takes j = w, w + 8, ...; lane l takes CTAs l, l + 32, ...;
 // every load is issued before any add.  Ends with a CTA barrier.
 __device__ __forceinline__ void grid_sums(const double *partial, int nvals, int nb, double *out) {
-  constexpr int MJ = (kMaxM + 2 + kArnWarps - 1) / kArnWarps;   // j values per warp
-  constexpr int MB = kMaxArnCta / 32;                            // CTAs per lane
-  constexpr int BATCH = 3;                                       // j values loaded together
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int kMinWarps = 8;                                      // blocks of >= 256 threads
+  constexpr int MJ = (2 * kMaxM + 2 + kMinWarps - 1) / kMinWarps;   // j values per warp (at most)
+  constexpr int MB = kMaxArnCta / 32;                               // CTAs per lane
+  constexpr int BATCH = 3;                                          // j values loaded together
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int t0 = 0; t0 < MJ; t0 += BATCH) {
-    if (wid + t0 * kArnWarps >= nvals) break;
+    if (wid + t0 * nw >= nvals) break;
     double v[BATCH][MB];
 #pragma unroll
     for (int t = 0; t < BATCH; ++t) {
-      const int j = wid + (t0 + t) * kArnWarps;
+      const int j = wid + (t0 + t) * nw;
 #pragma unroll
       for (int q = 0; q < MB; ++q) {
         const int b = lane + 32 * q;
@@ -290,187 +305,251 @@ __device__ __forceinline__ void grid_sums(const double *partial, int nvals, int 
 #pragma unroll
       for (int q = 0; q < MB; ++q) s += v[t][q];
       s = warp_sum(s);
-      const int j = wid + (t0 + t) * kArnWarps;
+      const int j = wid + (t0 + t) * nw;
       if (lane == 0 && j < nvals) out[j] = s;
     }
   }
   __syncthreads();
 }
 
-// pass 1: partial sums of V^T U (columns 0..k-1) and ||U||^2 (slot k); reduced by pass 2
+// ---------------------------------------------------------------------------------------
+// pass A: partial sums of V_i^T v_j (rows 0..j) and V_i^T w_j (rows j+1..2j+1), i <= j
+// ---------------------------------------------------------------------------------------
 template <typename T, int KS>
-__global__ void __launch_bounds__(kArnThreads) k_cgs_pass1(const __grid_constant__ VMaps mapV,
-                                                           const __grid_constant__ CUtensorMap mapU, int k,
+__global__ void __launch_bounds__(kArnThreads) k_dcgs_dots(const __grid_constant__ VMaps mapV,
+                                                           const __grid_constant__ CUtensorMap mapU, int j, int woff,
                                                            DevState *st, double *partial, int ntiles) {
   if (st->active == 0) return;
   using VT = typename Vec<T>::type;
   extern __shared__ __align__(128) char smem[];
   __shared__ uint64_t bars[kMaxStages];
+  const int k = j + 1;                      // V columns 0..j
   const int ucol = ucol_for(k);
-  TilePipe p{smem, bars, ucol + 1, ucol, ntiles, (int)blockIdx.x, (int)gridDim.x, stages_for(k), st->hist_count % st->mmax};
-  T acc[KS];
+  TilePipe p{smem, bars, ucol + 1, ucol, ntiles, (int)blockIdx.x, (int)gridDim.x, stages_for(k),
+             (st->hist_base + woff) % st->mmax};
+  T av[KS], aw[KS];
 #pragma unroll
-  for (int s = 0; s < KS; ++s) acc[s] = (T)0;
-  T uu = (T)0;
+  for (int s = 0; s < KS; ++s) { av[s] = (T)0; aw[s] = (T)0; }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   run_tiles<T>(p, mapV.m, &mapU, st, [] {}, [&](const T *tile, int) {
-    const VT *useg = reinterpret_cast<const VT *>(tile) + (int64_t)ucol * kSegVec;
-    const VT u[2] = {useg[lane], useg[lane + 32]};
-    if (wid == kArnWarps - 1) uu += Vec<T>::dot(u[0], u[0]) + Vec<T>::dot(u[1], u[1]);
-    tile_dots<T, KS>(tile, k, u, acc);
-  });
-  write_col_partials<T, KS>(acc, k, partial);
-  if (wid == kArnWarps - 1) {
-    const T v = warp_sum(uu);
-    if (lane == 0) partial[(int64_t)k * kMaxCta + blockIdx.x] = (double)v;
-  }
-}
-
-// pass 2: reduces pass 1 (h1, ||U||^2) in its prologue; U' = U - V h1 formed per tile in
-// shared memory, partial sums of h2 = V^T U' from the same tile
-template <typename T, int KS>
-__global__ void __launch_bounds__(kArnThreads) k_cgs_pass2(const __grid_constant__ VMaps mapV,
-                                                           const __grid_constant__ CUtensorMap mapU, int k,
-                                                           DevState *st, const double *partial1, double *partial,
-                                                           int ntiles, int nb1) {
-  if (st->active == 0) return;
-  using VT = typename Vec<T>::type;
-  extern __shared__ __align__(128) char smem[];
-  __shared__ uint64_t bars[kMaxStages];
-  __shared__ T s_c[kMaxM];
-  __shared__ double s_sum[kMaxM + 2];
-  __shared__ VT s_part[kArnThreads];
-  __shared__ VT s_u[kSegVec];
-  const int ucol = ucol_for(k);
-  TilePipe p{smem, bars, ucol + 1, ucol, ntiles, (int)blockIdx.x, (int)gridDim.x, stages_for(k), st->hist_count % st->mmax};
-  T acc[KS];
+    const VT *vseg = reinterpret_cast<const VT *>(tile) + (int64_t)j * kSegVec;
+    const VT *wseg = reinterpret_cast<const VT *>(tile) + (int64_t)ucol * kSegVec;
+    const VT v0 = vseg[lane], v1 = vseg[lane + 32], w0 = wseg[lane], w1 = wseg[lane + 32];
 #pragma unroll
-  for (int s = 0; s < KS; ++s) acc[s] = (T)0;
-  const int lane = threadIdx.x & 31;
-  run_tiles<T>(p, mapV.m, &mapU, st, [&] {
-    grid_sums(partial1, k + 1, nb1, s_sum);
-    for (int j = threadIdx.x; j <= k; j += blockDim.x) {
-      if (j < k) {
-        const double h = st->sigma[j] * s_sum[j];
-        s_c[j] = (T)(h * st->sigma[j]);
-        if (blockIdx.x == 0) st->h1[j] = h;
-      } else if (blockIdx.x == 0) {
-        st->unorm2 = s_sum[k];
+    for (int s = 0; s < KS; ++s) {
+      const int i = wid + kArnWarps * s;
+      if (i < k) {
+        const VT *seg = reinterpret_cast<const VT *>(tile) + (int64_t)i * kSegVec;
+        const VT x0 = seg[lane], x1 = seg[lane + 32];
+        av[s] += Vec<T>::dot(x0, v0) + Vec<T>::dot(x1, v1);
+        aw[s] += Vec<T>::dot(x0, w0) + Vec<T>::dot(x1, w1);
       }
     }
-  }, [&](const T *tile, int) {
-    tile_axpy<T>(tile, k, ucol, s_c, s_part, s_u);
-    const VT u[2] = {s_u[lane], s_u[lane + 32]};
-    tile_dots<T, KS>(tile, k, u, acc);
   });
-  write_col_partials<T, KS>(acc, k, partial);
-}
-
-// FP64 Givens step of Algorithm 1 for column k (1-based), then the finish test.
-__device__ void arnoldi_finish(DevState *st, int k, double nu, int mixed) {
-  const int kk = k - 1;
-  const int ld = kMaxM + 1;
-  double *Hc = st->H + (int64_t)kk * ld;
-  for (int j = 0; j < k; ++j) Hc[j] = st->h1[j] + st->h2[j];
-  const double hk1 = sqrt(nu);
-  Hc[k] = hk1;
-  const bool brk = !(hk1 > kBreakdownRel * sqrt(st->unorm2));
-  st->sigma[k] = hk1 > 0.0 ? 1.0 / hk1 : 0.0;
-  for (int j = 0; j < kk; ++j) {  // old rotations
-    const double d = Hc[j];
-    Hc[j] = d * st->C[j] + st->S[j] * Hc[j + 1];
-    Hc[j + 1] = -d * st->S[j] + st->C[j] * Hc[j + 1];
-  }
-  const double gamma = hypot(Hc[kk], Hc[k]);
-  if (gamma > 0.0) {
-    st->C[kk] = Hc[kk] / gamma;
-    st->S[kk] = Hc[k] / gamma;
-  } else {
-    st->C[kk] = 1.0;
-    st->S[kk] = 0.0;
-  }
-  Hc[kk] = gamma;
-  Hc[k] = 0.0;
-  st->G[k] = 0.0;
-  const double d = st->G[kk];
-  st->G[kk] = st->C[kk] * d + st->S[kk] * st->G[k];
-  st->G[k] = -st->S[kk] * d + st->C[kk] * st->G[k];
-  const double R = fabs(st->G[k]);
-  st->R[kk] = R;
-  int status = st->status;
-  if (!isfinite(R) || !isfinite(hk1)) status |= kStNumeric;
-  if (brk) status |= kStBreakdown;
-  if (!mixed && R <= st->eps_abs) status |= kStConverged;
-  const bool end = (R <= st->eps_cycle) || brk || (k >= st->m) || (status & kStNumeric);
-  st->status = status;
-  st->k_end = k;
-  st->hist_count += 1;
-  if (end) {
-    st->active = 0;
-    for (int j = k - 1; j >= 0; --j) {  // Q = H^{-1} G, back substitution
-      double s = st->G[j];
-      for (int l = j + 1; l < k; ++l) s -= st->H[(int64_t)l * ld + j] * st->Q[l];
-      const double hjj = st->H[(int64_t)j * ld + j];
-      st->Q[j] = hjj != 0.0 ? s / hjj : 0.0;
+#pragma unroll
+  for (int s = 0; s < KS; ++s) {
+    const int i = wid + kArnWarps * s;
+    const T x = warp_sum(av[s]);
+    const T y = warp_sum(aw[s]);
+    if (lane == 0 && i < k) {
+      partial[(int64_t)i * kMaxCta + blockIdx.x] = (double)x;
+      partial[(int64_t)(k + i) * kMaxCta + blockIdx.x] = (double)y;
     }
   }
+}
+
+// FP64 Givens step for the completed column kk of H (rows 0..kk+1 in hcol, shared memory),
+// R(kk+1) and the finish test; run by one thread with the rotations staged in shared
+// memory (sC, sS, sG hold C, S, G).  Returns true when the cycle ends.
+__device__ bool givens_column(DevState *st, int kk, double *hcol, double *sC, double *sS, double *sG, bool brk,
+                              bool force_end, int mixed) {
+  const int k = kk + 1;
+  for (int i = 0; i < kk; ++i) {   // old rotations
+    const double d = hcol[i];
+    hcol[i] = d * sC[i] + sS[i] * hcol[i + 1];
+    hcol[i + 1] = -d * sS[i] + sC[i] * hcol[i + 1];
+  }
+  const double gamma = hypot(hcol[kk], hcol[k]);
+  double c = 1.0, s = 0.0;
+  if (gamma > 0.0) {
+    c = hcol[kk] / gamma;
+    s = hcol[k] / gamma;
+  }
+  hcol[kk] = gamma;
+  hcol[k] = 0.0;
+  const double d = sG[kk];
+  const double gk = -s * d;
+  sG[kk] = c * d;
+  sG[k] = gk;
+  sC[kk] = c;
+  sS[kk] = s;
+  // write back: rotated column, rotation, G
+  const int ld = kMaxM + 1;
+  for (int r = 0; r <= k; ++r) st->H[(int64_t)kk * ld + r] = hcol[r];
+  st->C[kk] = c;
+  st->S[kk] = s;
+  st->G[kk] = sG[kk];
+  st->G[k] = gk;
+  const double R = fabs(gk);
+  st->R[kk] = R;
+  int status = st->status;
+  if (!isfinite(R) || !isfinite(gamma)) status |= kStNumeric;
+  if (brk) status |= kStBreakdown;
+  if (!mixed && R <= st->eps_abs) status |= kStConverged;
+  st->status = status;
+  st->k_end = k;
+  const bool end = (R <= st->eps_cycle) || brk || force_end || (status & kStNumeric);
   st->sum.k_end = k;
   st->sum.error = st->error;
   st->sum.status = status;
-  st->sum.hist_count = st->hist_count;
   st->sum.R_end = R;
+  return end;
 }
 
-// pass 3: reduces pass 2 (h2) in its prologue; V~(:,k+1) = U - V (h1 + h2),
-// nu = ||V~(:,k+1)||^2; the last CTA to finish runs the Givens step
-template <typename T, int KS>
-__global__ void __launch_bounds__(kArnThreads) k_cgs_pass3(const __grid_constant__ VMaps mapV,
-                                                           const __grid_constant__ CUtensorMap mapU, T *__restrict__ V,
-                                                           int64_t ldv, int k, DevState *st, const double *partial2,
-                                                           double *partial, int ntiles, int nb2, int mixed) {
+// ---------------------------------------------------------------------------------------
+// pass B: prologue (every CTA): reduce pass A, the DCGS2 coefficients; CTA 0: completed
+// column j-1, Givens, finish test, Hessenberg bookkeeping, and at the end of the cycle the
+// triangular solve Q = H^{-1} G.  Stream (unless final): q_j over v_j in V(:,j) and v_{j+1}
+// in V(:,j+1).  The small dense work runs out of shared memory.
+// ---------------------------------------------------------------------------------------
+constexpr int kUpdThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kUpdThreads) k_dcgs_update(T *__restrict__ V, int64_t ldv, const T *__restrict__ Pyb,
+                                                             int64_t ldh, int j, int woff, DevState *st,
+                                                             const double *partial, int nbA, int64_t nv, int final_step,
+                                                             int mixed) {
   if (st->active == 0) return;
   using VT = typename Vec<T>::type;
-  extern __shared__ __align__(128) char smem[];
-  __shared__ uint64_t bars[kMaxStages];
-  __shared__ T s_c[kMaxM];
-  __shared__ double s_sum[kMaxM + 2];
-  __shared__ VT s_part[kArnThreads];
-  __shared__ VT s_u[kSegVec];
-  VT *Vout = reinterpret_cast<VT *>(V + (int64_t)k * ldv);
-  const int ucol = ucol_for(k);
-  TilePipe p{smem, bars, ucol + 1, ucol, ntiles, (int)blockIdx.x, (int)gridDim.x, stages_for(k), st->hist_count % st->mmax};
-  T nu = (T)0;
-  run_tiles<T>(p, mapV.m, &mapU, st, [&] {
-    grid_sums(partial2, k, nb2, s_sum);
-    for (int j = threadIdx.x; j < k; j += blockDim.x) {
-      const double h2 = st->sigma[j] * s_sum[j];
-      s_c[j] = (T)((st->h1[j] + h2) * st->sigma[j]);
-      if (blockIdx.x == 0) st->h2[j] = h2;
+  constexpr int ld = kMaxM + 1;
+  __shared__ double s_sum[2 * kMaxM + 2];
+  __shared__ double sH[kMaxM * (kMaxM + 1)];   // completed columns 0..j-2 (rows 0..j), later the rotated H
+  __shared__ double s_a[kMaxM], s_t[kMaxM + 1], s_hcol[kMaxM + 2];
+  __shared__ double sC[kMaxM], sS[kMaxM], sG[kMaxM + 1];
+  __shared__ double s_sc[4];   // nu, a^T a, a^T b, breakdown
+  __shared__ T s_sa[kMaxM], s_sd[kMaxM];
+  __shared__ T s_coef[3];
+  __shared__ int s_end;
+  const int k = j + 1;
+  const bool cta0 = blockIdx.x == 0;
+  // completed columns 0..j-2 of Hbar (rows 0..j) and, in CTA 0, the rotations and G
+  for (int e = threadIdx.x; e < (j > 1 ? (j - 1) * ld : 0); e += blockDim.x) sH[e] = st->Hc[e];
+  if (cta0)
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+      if (i < j) { sC[i] = st->C[i]; sS[i] = st->S[i]; }
+      sG[i] = st->G[i];
     }
-  }, [&](const T *tile, int t) {
-    tile_axpy<T>(tile, k, ucol, s_c, s_part, s_u);
-    if (threadIdx.x < kSegVec) {
-      const VT u = s_u[threadIdx.x];
-      Vout[(int64_t)t * kSegVec + threadIdx.x] = u;
-      nu += Vec<T>::dot(u, u);
+  if (j >= 1)
+    for (int r = threadIdx.x; r < j; r += blockDim.x) s_hcol[r] = st->Hf[(int64_t)(j - 1) * ld + r];
+  grid_sums(partial, 2 * k, nbA, s_sum);   // ends with a barrier
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (wid == 0) {
+    double aa = 0.0, ab = 0.0;
+    for (int i = lane; i < j; i += 32) {
+      s_a[i] = s_sum[i];
+      aa += s_sum[i] * s_sum[i];
+      ab += s_sum[i] * s_sum[k + i];
     }
-  });
-  __shared__ double s_nu[kArnWarps];
-  {
-    const T v = warp_sum(nu);
-    if ((threadIdx.x & 31) == 0) s_nu[threadIdx.x >> 5] = (double)v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double a = 0.0;
-      for (int w = 0; w < kArnWarps; ++w) a += s_nu[w];
-      partial[blockIdx.x] = a;
+    aa = warp_sum(aa);
+    ab = warp_sum(ab);
+    if (lane == 0) {
+      const double alpha = s_sum[j];
+      const double nu2 = alpha - aa;
+      const bool brk = !(nu2 > kBreakdownRel * kBreakdownRel * alpha) || !isfinite(nu2);
+      s_sc[0] = brk ? 0.0 : sqrt(nu2);
+      s_sc[1] = aa;
+      s_sc[2] = ab;
+      s_sc[3] = brk ? 1.0 : 0.0;
     }
   }
-  if (!last_block_arrive(&st->counter[3])) return;
-  grid_sums(partial, 1, gridDim.x, s_sum);
-  if (threadIdx.x == 0) arnoldi_finish(st, k, s_sum[0], mixed);
   __syncthreads();
-  last_block_reset(&st->counter[3]);
+  const double nu = s_sc[0];
+  const bool brk = s_sc[3] != 0.0;
+  // completed column j-1: first projection + a, and nu in row j
+  if (j >= 1)
+    for (int r = threadIdx.x; r <= j; r += blockDim.x) s_hcol[r] = (r < j) ? s_hcol[r] + s_a[r] : nu;
+  __syncthreads();
+  // t = Hbar a (rows 0..j)
+  for (int r = threadIdx.x; r <= j; r += blockDim.x) {
+    double t = 0.0;
+    for (int i = (r > 0 ? r - 1 : 0); i < j; ++i) t += ((i == j - 1) ? s_hcol[r] : sH[i * ld + r]) * s_a[i];
+    s_t[r] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double beta = s_sum[k + j];
+    const double inv = (nu > 0.0) ? 1.0 / nu : 0.0;
+    for (int r = 0; r <= j; ++r) {
+      const double proj = (r < j) ? s_sum[k + r] : (beta - s_sc[2]) * inv;
+      const double h = (proj - s_t[r]) * inv;
+      if (cta0 && !final_step) st->Hf[(int64_t)j * ld + r] = h;
+      s_t[r] = s_t[r] * inv + h;   // c_r
+    }
+    const double cj = s_t[j];
+    for (int i = 0; i < j; ++i) {
+      s_sa[i] = (T)(s_a[i] * inv);
+      s_sd[i] = (T)(s_t[i] - cj * inv * s_a[i]);
+    }
+    s_coef[0] = (T)inv;
+    s_coef[1] = (T)(cj * inv);
+    s_coef[2] = (T)inv;
+    s_end = 0;
+    if (cta0) {
+      bool end = false;
+      if (j >= 1) {
+        for (int r = 0; r <= j; ++r) st->Hc[(int64_t)(j - 1) * ld + r] = s_hcol[r];
+        end = givens_column(st, j - 1, s_hcol, sC, sS, sG, brk, final_step != 0, mixed);
+      } else if (brk || final_step) {
+        end = true;   // v_0 = 0: nothing to do
+        st->k_end = 0;
+        st->sum.k_end = 0;
+      }
+      if (end) {
+        st->active = 0;
+        // matvecs of this cycle: iterations 0..j had one each, the final step none
+        st->hist_count = st->hist_base + 1 + (final_step ? j : j + 1);
+        st->sum.hist_count = st->hist_count;
+      }
+      s_end = end ? 1 : 0;
+    }
+  }
+  __syncthreads();
+  if (cta0 && s_end) {
+    // Q = H^{-1} G on the leading kend x kend triangle of the rotated H (column-oriented
+    // back substitution in shared memory); the basis scales of the update become 1
+    const int kend = st->k_end;
+    for (int e = threadIdx.x; e < kend * ld; e += blockDim.x) sH[e] = st->H[e];
+    for (int i = threadIdx.x; i <= kend; i += blockDim.x) s_t[i] = st->G[i];
+    __syncthreads();
+    for (int c = kend - 1; c >= 0; --c) {
+      const double hcc = sH[c * ld + c];
+      const double q = hcc != 0.0 ? s_t[c] / hcc : 0.0;
+      __syncthreads();
+      for (int i = threadIdx.x; i < c; i += blockDim.x) s_t[i] -= sH[c * ld + i] * q;
+      if (threadIdx.x == 0) { st->Q[c] = q; st->sigma[c] = 1.0; }
+      __syncthreads();
+    }
+  }
+  if (final_step) return;
+  // stream: q_j and v_{j+1}
+  VT *vj = reinterpret_cast<VT *>(V + (int64_t)j * ldv);
+  VT *vn = reinterpret_cast<VT *>(V + (int64_t)(j + 1) * ldv);
+  const VT *w = reinterpret_cast<const VT *>(Pyb + (int64_t)((st->hist_base + woff) % st->mmax) * ldh);
+  const T sv = s_coef[0], cv = s_coef[1], sw = s_coef[2];
+  for (int64_t iv = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; iv < nv; iv += (int64_t)gridDim.x * blockDim.x) {
+    const VT v = vj[iv];
+    const VT x = w[iv];
+    VT q = Vec<T>::scale(sv, v);
+    VT y = Vec<T>::axpy(cv, v, Vec<T>::scale(sw, x));
+#pragma unroll 8
+    for (int i = 0; i < j; ++i) {
+      const VT qi = reinterpret_cast<const VT *>(V + (int64_t)i * ldv)[iv];
+      q = Vec<T>::axpy(s_sa[i], qi, q);
+      y = Vec<T>::axpy(s_sd[i], qi, y);
+    }
+    vj[iv] = q;
+    vn[iv] = y;
+  }
 }
 
 // P_x(:,i) = Y_k = V(:,k) when N = I (unpreconditioned cycle).
@@ -517,14 +596,12 @@ int arnoldi_grid() {
 
 static size_t pass_smem(int k) { return (size_t)stages_for(k) * (ucol_for(k) + 1) * kSegBytes; }
 
-// Opt the pipelined passes in to their dynamic shared memory (once, outside capture).
+// Opt the pipelined pass in to its dynamic shared memory (once, outside capture).
 template <typename T>
 static void set_attrs_t() {
-#define PSP_ATTR(KS_)                                                                                    \
-  cudaFuncSetAttribute(k_cgs_pass1<T, KS_>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageBudget); \
-  cudaFuncSetAttribute(k_cgs_pass2<T, KS_>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageBudget); \
-  cudaFuncSetAttribute(k_cgs_pass3<T, KS_>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageBudget);
-  PSP_ATTR(1) PSP_ATTR(2) PSP_ATTR(3) PSP_ATTR(4) PSP_ATTR(5) PSP_ATTR(6) PSP_ATTR(7) PSP_ATTR(8)
+#define PSP_ATTR(KS_) \
+  cudaFuncSetAttribute(k_dcgs_dots<T, KS_>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageBudget);
+  PSP_ATTR(1) PSP_ATTR(2) PSP_ATTR(3) PSP_ATTR(4) PSP_ATTR(5)
 #undef PSP_ATTR
 }
 
@@ -535,30 +612,30 @@ void arnoldi_setup() {
 }
 
 template <typename T>
-void launch_arnoldi(int k, int64_t n, const ArnoldiMaps &maps, T *V, int64_t ldv, DevState *st, double *partial,
-                    int mixed, cudaStream_t s, cudaEvent_t *ev) {
-  // tiles cover the padded column length ldv (a multiple of the tile)
+void launch_arnoldi(int j, int final_step, int64_t n, const ArnoldiMaps &maps, T *V, int64_t ldv, const T *Py,
+                    int64_t ldh, DevState *st, double *partial, int mixed, cudaStream_t s, cudaEvent_t *ev) {
   const int ntiles = (int)((ldv * (int64_t)sizeof(T)) / kSegBytes);
   int grid = std::min(ntiles, arnoldi_grid());
   if (grid < 1) grid = 1;
+  const int k = j + 1;
   const size_t sm = pass_smem(k);
+  const int woff = 1 + j;   // ring column of w_j relative to the cycle's restart column
   const VMaps &mV = *reinterpret_cast<const VMaps *>(maps.V);
   const CUtensorMap &mU = *reinterpret_cast<const CUtensorMap *>(maps.Py);
-  double *p1 = partial, *p2 = partial + (int64_t)(kMaxM + 2) * kMaxCta, *p3 = partial + 2 * (int64_t)(kMaxM + 2) * kMaxCta;
-#define PSP_CGS(KS_)                                                                                       \
-  case KS_:                                                                                                \
-    k_cgs_pass1<T, KS_><<<grid, kArnThreads, sm, s>>>(mV, mU, k, st, p1, ntiles);                          \
-    if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);                                   \
-    k_cgs_pass2<T, KS_><<<grid, kArnThreads, sm, s>>>(mV, mU, k, st, p1, p2, ntiles, grid);                \
-    if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);                                   \
-    k_cgs_pass3<T, KS_><<<grid, kArnThreads, sm, s>>>(mV, mU, V, ldv, k, st, p2, p3, ntiles, grid, mixed); \
-    if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);                                   \
-    break;
   switch ((k + kArnWarps - 1) / kArnWarps) {
-    PSP_CGS(1) PSP_CGS(2) PSP_CGS(3) PSP_CGS(4) PSP_CGS(5) PSP_CGS(6) PSP_CGS(7) PSP_CGS(8)
+#define PSP_DOTS(KS_) \
+  case KS_: k_dcgs_dots<T, KS_><<<grid, kArnThreads, sm, s>>>(mV, mU, j, woff, st, partial, ntiles); break;
+    PSP_DOTS(1) PSP_DOTS(2) PSP_DOTS(3) PSP_DOTS(4) PSP_DOTS(5)
+#undef PSP_DOTS
     default: break;
   }
-#undef PSP_CGS
+  if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
+  if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
+  const int64_t nv = (ldv + Vec<T>::W - 1) / Vec<T>::W;
+  int ugrid = final_step ? 1 : (int)std::min<int64_t>((nv + kUpdThreads - 1) / kUpdThreads, (int64_t)arnoldi_grid() * 2);
+  if (ugrid < 1) ugrid = 1;
+  k_dcgs_update<T><<<ugrid, kUpdThreads, 0, s>>>(V, ldv, Py, ldh, j, woff, st, partial, grid, nv, final_step, mixed);
+  if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);
 }
 
 // Tensor maps of the Krylov basis (ncols x ld) and of the P_y ring (mmax x ld), element
@@ -615,10 +692,10 @@ void launch_update_z(int64_t n, const T *V, int64_t ldv, T *Z, double *X, int ad
   k_update_z<T><<<grid < 1 ? 1 : grid, kThreads, 0, s>>>(n, V, ldv, Z, X, add_to_x, st);
 }
 
-template void launch_arnoldi<float>(int, int64_t, const ArnoldiMaps &, float *, int64_t, DevState *, double *, int,
-                                    cudaStream_t, cudaEvent_t *);
-template void launch_arnoldi<double>(int, int64_t, const ArnoldiMaps &, double *, int64_t, DevState *, double *, int,
-                                     cudaStream_t, cudaEvent_t *);
+template void launch_arnoldi<float>(int, int, int64_t, const ArnoldiMaps &, float *, int64_t, const float *, int64_t,
+                                    DevState *, double *, int, cudaStream_t, cudaEvent_t *);
+template void launch_arnoldi<double>(int, int, int64_t, const ArnoldiMaps &, double *, int64_t, const double *,
+                                     int64_t, DevState *, double *, int, cudaStream_t, cudaEvent_t *);
 template void launch_scale_copy<float>(int, int64_t, const float *, int64_t, OutRef<float>, const DevState *,
                                        cudaStream_t);
 template void launch_scale_copy<double>(int, int64_t, const double *, int64_t, OutRef<double>,

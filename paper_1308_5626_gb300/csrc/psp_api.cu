@@ -158,26 +158,29 @@ void enqueue_cycle(psp_ctx *h, int slot, cudaStream_t s) {
   launch_restart<T, T>(g, h->X, h->B, Px, Py, h->ld, V, h->st, h->partial, h->mixed ? 1 : 0, s);
   const int *active = &h->st->active;
   const int which = slot + 1;
-  for (int k = 1; k <= h->m; ++k) {
+  // iteration j: Y_j = N^{-1} v_j -> P_x ring column hist_base+1+j, w_j = A Y_j -> P_y column,
+  // then the DCGS2 passes (orthogonalise, complete column j-1, Givens, finish test)
+  for (int j = 0; j < h->m; ++j) {
     // profiling samples one iteration in kProfileEvery
-    cudaEvent_t *ev = (h->profiling && (k - 1) % kProfileEvery == 0) ? h->ev[which][k - 1] : nullptr;
-    OutRef<T> pxcol = ring_out<T>(Px, h->ld, &h->st->hist_count, h->mmax);
-    OutRef<T> pycol = ring_out<T>(Py, h->ld, &h->st->hist_count, h->mmax);
+    cudaEvent_t *ev = (h->profiling && j % kProfileEvery == 0) ? h->ev[which][j] : nullptr;
+    OutRef<T> pxcol = ring_out<T>(Px, h->ld, &h->st->hist_base, h->mmax, 1 + j);
+    OutRef<T> pycol = ring_out<T>(Py, h->ld, &h->st->hist_base, h->mmax, 1 + j);
     if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
     if (slot < 0) {
-      // N = I: Y_k = V(:,k); one kernel writes P_x(:,i) = Y_k and P_y(:,i) = A Y_k
+      // N = I: one kernel writes P_x(:,i) = v_j and P_y(:,i) = A v_j
       if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
-      launch_stencil<T, T, T>(g, fixed_in<T>(V + (int64_t)(k - 1) * h->ld), pycol, h->st, active, s, pxcol,
-                              &h->st->sigma[k - 1]);
+      launch_stencil<T, T, T>(g, fixed_in<T>(V + (int64_t)j * h->ld), pycol, h->st, active, s, pxcol, nullptr);
     } else {
-      h->bs.apply<T>(slot, V + (int64_t)(k - 1) * h->ld, &h->st->sigma[k - 1], active, pxcol, nullptr, 0, s);
+      h->bs.apply<T>(slot, V + (int64_t)j * h->ld, nullptr, active, pxcol, nullptr, 0, s);
       if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
-      // U_k = A Y_k, read back from the ring column just written
-      launch_stencil<T, T, T>(g, ring_in<T>(Px, h->ld, &h->st->hist_count, h->mmax), pycol, h->st, active, s);
+      launch_stencil<T, T, T>(g, ring_in<T>(Px, h->ld, &h->st->hist_base, h->mmax, 1 + j), pycol, h->st, active, s);
     }
     if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);
-    launch_arnoldi<T>(k, g.n, h->maps, V, h->ld, h->st, h->partial, h->mixed ? 1 : 0, s, ev ? ev + 3 : nullptr);
+    launch_arnoldi<T>(j, 0, g.n, h->maps, V, h->ld, Py, h->ld, h->st, h->partial, h->mixed ? 1 : 0, s,
+                      ev ? ev + 3 : nullptr);
   }
+  // reduction-only step completing column m-1 when the cycle runs to m columns
+  launch_arnoldi<T>(h->m, 1, g.n, h->maps, V, h->ld, Py, h->ld, h->st, h->partial, h->mixed ? 1 : 0, s, nullptr);
   if (slot < 0) {
     launch_update_z<T>(g.n, V, h->ld, Z, h->X, 1, h->st, s);
   } else {
@@ -249,7 +252,7 @@ psp_status fit_into(psp_ctx *h, const TH *Px, const TH *Py, int64_t ld, int M, d
 void accumulate_profile(psp_ctx *h, int which, int k_end) {
   const double s = h->mixed ? 4.0 : 8.0;
   const double n = (double)h->geo.n;
-  for (int k = 1; k <= k_end; k += kProfileEvery) {
+  for (int k = 1; k <= k_end && k <= h->m; k += kProfileEvery) {
     cudaEvent_t *ev = h->ev[which][k - 1];
     float ms[5];
     for (int c = 0; c < 5; ++c)
@@ -259,8 +262,10 @@ void accumulate_profile(psp_ctx *h, int which, int k_end) {
       }
     // N = I: the fused stencil reads V(:,k) and writes P_x and P_y columns (class 1;
     // class 0 is then empty)
+    // DCGS2 at iteration j = k-1: pass A reads V(:,0..j) and w_j (k+1 vectors), pass B
+    // reads the same and writes q_j and v_{j+1} (class 3, the former second pass, is empty)
     const double bytes[5] = {(which == 0 ? 0.0 : (2.0 * h->b + 3.0)) * s * n, (which == 0 ? 3.0 : 2.0) * s * n,
-                             (k + 1.0) * s * n, (k + 1.0) * s * n, (k + 2.0) * s * n};
+                             (k + 1.0) * s * n, 0.0, (k + 3.0) * s * n};
     for (int c = 0; c < 5; ++c) {
       if (bytes[c] == 0.0) continue;
       h->prof.ms[c] += ms[c];

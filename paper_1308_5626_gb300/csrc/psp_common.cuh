@@ -40,6 +40,7 @@ struct DevState {
   int k_end;         // Arnoldi iterations completed in the current cycle
   int status;        // kSt* bits of the current cycle
   int hist_count;    // history columns written since the history was cleared
+  int hist_base;     // ring column of the current cycle's restart pair (X_0, A X_0)
   int mmax;          // history ring length
   int m;             // restart length
   int pad0, pad1;
@@ -53,6 +54,8 @@ struct DevState {
   // Arnoldi / Givens (FP64, Algorithm 1)
   double sigma[kMaxM + 2];            // V(:,j) = sigma[j] * Vt(:,j) (lazy normalisation)
   double H[(kMaxM + 1) * kMaxM];      // rotated Hessenberg, column-major (ld = kMaxM+1)
+  double Hf[(kMaxM + 1) * kMaxM];     // first projection of each column (DCGS2)
+  double Hc[(kMaxM + 1) * kMaxM];     // completed, unrotated columns (DCGS2)
   double G[kMaxM + 1];
   double C[kMaxM];
   double S[kMaxM];

@@ -21,13 +21,14 @@ struct OutRef {
   int64_t ld;
   const int *counter;  // nullptr: fixed output `base`
   int mmax;
+  int off;             // column = (*counter + off) % mmax
   __device__ __forceinline__ T *get() const {
-    return counter ? base + (int64_t)((*counter) % mmax) * ld : base;
+    return counter ? base + (int64_t)((*counter + off) % mmax) * ld : base;
   }
 };
 
 template <typename T>
-inline OutRef<T> fixed_out(T *p) { return OutRef<T>{p, 0, nullptr, 1}; }
+inline OutRef<T> fixed_out(T *p) { return OutRef<T>{p, 0, nullptr, 1, 0}; }
 
 // Read-only counterpart of OutRef.
 template <typename T>
@@ -36,19 +37,20 @@ struct InRef {
   int64_t ld;
   const int *counter;
   int mmax;
+  int off;
   __device__ __forceinline__ const T *get() const {
-    return counter ? base + (int64_t)((*counter) % mmax) * ld : base;
+    return counter ? base + (int64_t)((*counter + off) % mmax) * ld : base;
   }
 };
 template <typename T>
-inline InRef<T> fixed_in(const T *p) { return InRef<T>{p, 0, nullptr, 1}; }
+inline InRef<T> fixed_in(const T *p) { return InRef<T>{p, 0, nullptr, 1, 0}; }
 template <typename T>
-inline InRef<T> ring_in(const T *base, int64_t ld, const int *counter, int mmax) {
-  return InRef<T>{base, ld, counter, mmax};
+inline InRef<T> ring_in(const T *base, int64_t ld, const int *counter, int mmax, int off = 0) {
+  return InRef<T>{base, ld, counter, mmax, off};
 }
 template <typename T>
-inline OutRef<T> ring_out(T *base, int64_t ld, const int *counter, int mmax) {
-  return OutRef<T>{base, ld, counter, mmax};
+inline OutRef<T> ring_out(T *base, int64_t ld, const int *counter, int mmax, int off = 0) {
+  return OutRef<T>{base, ld, counter, mmax, off};
 }
 
 int reduce_grid(int64_t n);
@@ -56,7 +58,7 @@ int reduce_grid(int64_t n);
 // stencil.cu
 template <typename TI, typename TO, typename TC>
 void launch_stencil(const Geometry &g, InRef<TI> x, OutRef<TO> y, const DevState *st, const int *active,
-                    cudaStream_t s, OutRef<TO> xcopy = OutRef<TO>{nullptr, 0, nullptr, 1},
+                    cudaStream_t s, OutRef<TO> xcopy = OutRef<TO>{nullptr, 0, nullptr, 1, 0},
                     const double *scale = nullptr);
 template <typename TH, typename TV>
 void launch_restart(const Geometry &g, const double *X, const double *B, TH *Px, TH *Py, int64_t ldh,
@@ -74,11 +76,12 @@ struct alignas(64) ArnoldiMaps {
 template <typename T>
 bool encode_arnoldi_maps(ArnoldiMaps &maps, const T *V, int ncols, const T *Py, int mmax, int64_t ld);
 
-// Three Gram-Schmidt passes of iteration k; if ev != nullptr, ev[0..2] are recorded after
-// passes 1..3 (profiling).
+// DCGS2 step of iteration j (0-based) of a cycle: pass A (dots) and pass B (update).  With
+// final_step, pass B only completes column j-1 (no matvec was made at this j).  If
+// ev != nullptr, ev[0..2] are recorded after pass A, (nothing), pass B (profiling).
 template <typename T>
-void launch_arnoldi(int k, int64_t n, const ArnoldiMaps &maps, T *V, int64_t ldv, DevState *st, double *partial,
-                    int mixed, cudaStream_t s, cudaEvent_t *ev = nullptr);
+void launch_arnoldi(int j, int final_step, int64_t n, const ArnoldiMaps &maps, T *V, int64_t ldv, const T *Py,
+                    int64_t ldh, DevState *st, double *partial, int mixed, cudaStream_t s, cudaEvent_t *ev = nullptr);
 template <typename T>
 void launch_scale_copy(int k, int64_t n, const T *V, int64_t ldv, OutRef<T> y, const DevState *st,
                        cudaStream_t s);

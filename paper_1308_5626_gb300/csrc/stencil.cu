@@ -80,12 +80,8 @@ __global__ void __launch_bounds__(kThreads) k_stencil(InRef<TI> xref, OutRef<TO>
     const int iy = rem / nx;
     const int ix = rem - iy * nx;
     const TC v = stencil_point<TI, NDIM, R, TC>(x, c, ix, iy, iz, nx, ny, nz);
-    if (scale) {
-      y[i] = (TO)(sc * v);
-      if (xc) xc[i] = (TO)(sc * (TC)x[i]);
-    } else {
-      y[i] = (TO)v;
-    }
+    y[i] = (TO)(sc * v);
+    if (xc) xc[i] = (TO)(sc * (TC)x[i]);
   }
 }
 
@@ -259,6 +255,7 @@ __global__ void __launch_bounds__(kThreads) k_restart(const double *__restrict__
     st->eps_cycle = mixed ? fmax(st->eps_abs, st->inner_tol * beta) : st->eps_abs;
     st->k_end = 0;
     st->status = 0;
+    st->hist_base = col;
     st->hist_count = col + 1;
     if (!isfinite(beta)) {
       st->status = kStNumeric;

@@ -48,7 +48,7 @@ class psp_step_info(ctypes.Structure):
                 ("singular_rows", ctypes.c_int), ("launches", ctypes.c_int)]
 
 
-PSP_K_NAMES = ["precond", "stencil", "cgs_pass1", "cgs_pass2", "cgs_pass3"]
+PSP_K_NAMES = ["precond", "stencil", "orth_dots", "unused", "orth_update"]
 
 
 class psp_profile(ctypes.Structure):
