@@ -531,24 +531,48 @@ __global__ void __launch_bounds__(kUpdThreads) k_dcgs_update(T *__restrict__ V, 
     }
   }
   if (final_step) return;
-  // stream: q_j and v_{j+1}
+  // stream: q_j and v_{j+1}.  Columns are taken in chunks of 8 with the column index
+  // clamped to j-1 and a zero coefficient past j, so the 8 loads of a chunk (for two
+  // vectors per thread) are issued together.
+  for (int i = j + threadIdx.x; i < kMaxM; i += blockDim.x) { s_sa[i] = (T)0; s_sd[i] = (T)0; }
+  __syncthreads();
   VT *vj = reinterpret_cast<VT *>(V + (int64_t)j * ldv);
   VT *vn = reinterpret_cast<VT *>(V + (int64_t)(j + 1) * ldv);
   const VT *w = reinterpret_cast<const VT *>(Pyb + (int64_t)((st->hist_base + woff) % st->mmax) * ldh);
   const T sv = s_coef[0], cv = s_coef[1], sw = s_coef[2];
-  for (int64_t iv = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; iv < nv; iv += (int64_t)gridDim.x * blockDim.x) {
-    const VT v = vj[iv];
-    const VT x = w[iv];
-    VT q = Vec<T>::scale(sv, v);
-    VT y = Vec<T>::axpy(cv, v, Vec<T>::scale(sw, x));
-#pragma unroll 8
-    for (int i = 0; i < j; ++i) {
-      const VT qi = reinterpret_cast<const VT *>(V + (int64_t)i * ldv)[iv];
-      q = Vec<T>::axpy(s_sa[i], qi, q);
-      y = Vec<T>::axpy(s_sd[i], qi, y);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t iv = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; iv < nv; iv += 2 * stride) {
+    const int64_t iv2 = iv + stride;
+    const bool two = iv2 < nv;
+    const int64_t jv2 = two ? iv2 : iv;
+    const VT v0 = vj[iv], v1 = vj[jv2];
+    const VT x0 = w[iv], x1 = w[jv2];
+    VT q0 = Vec<T>::scale(sv, v0), q1 = Vec<T>::scale(sv, v1);
+    VT y0 = Vec<T>::axpy(cv, v0, Vec<T>::scale(sw, x0)), y1 = Vec<T>::axpy(cv, v1, Vec<T>::scale(sw, x1));
+    for (int c0 = 0; c0 < j; c0 += 8) {
+      VT a0[8], a1[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int col = min(c0 + u, j - 1);
+        const VT *qc = reinterpret_cast<const VT *>(V + (int64_t)col * ldv);
+        a0[u] = qc[iv];
+        a1[u] = qc[jv2];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const T ca = s_sa[c0 + u], cd = s_sd[c0 + u];
+        q0 = Vec<T>::axpy(ca, a0[u], q0);
+        y0 = Vec<T>::axpy(cd, a0[u], y0);
+        q1 = Vec<T>::axpy(ca, a1[u], q1);
+        y1 = Vec<T>::axpy(cd, a1[u], y1);
+      }
     }
-    vj[iv] = q;
-    vn[iv] = y;
+    vj[iv] = q0;
+    vn[iv] = y0;
+    if (two) {
+      vj[iv2] = q1;
+      vn[iv2] = y1;
+    }
   }
 }
 
@@ -632,7 +656,7 @@ void launch_arnoldi(int j, int final_step, int64_t n, const ArnoldiMaps &maps, T
   if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
   if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
   const int64_t nv = (ldv + Vec<T>::W - 1) / Vec<T>::W;
-  int ugrid = final_step ? 1 : (int)std::min<int64_t>((nv + kUpdThreads - 1) / kUpdThreads, (int64_t)arnoldi_grid() * 2);
+  int ugrid = final_step ? 1 : (int)std::min<int64_t>((nv + kUpdThreads - 1) / kUpdThreads, (int64_t)arnoldi_grid() * 4);
   if (ugrid < 1) ugrid = 1;
   k_dcgs_update<T><<<ugrid, kUpdThreads, 0, s>>>(V, ldv, Py, ldh, j, woff, st, partial, grid, nv, final_step, mixed);
   if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);

@@ -328,7 +328,7 @@ void launch_stencil(const Geometry &g, InRef<TI> x, OutRef<TO> y, const DevState
                                                         : al(xcopy.base)));
     if (g.nx % W == 0 && g.nx / W > nh && aligned) {
       const int64_t nvec = g.n / W;
-      int grid = (int)std::min<int64_t>((nvec + kThreads - 1) / kThreads, 152 * 8);
+      int grid = (int)std::min<int64_t>((nvec + kThreads - 1) / kThreads, 152 * 4);
       PSP_DISPATCH_NDIM(g.ndim, PSP_DISPATCH_R(g.R, (k_stencil_vec<TI, DD, RR><<<grid, kThreads, 0, s>>>(
                                                         x, y, xcopy, scale, st, g.nx, g.ny, g.nz, active))));
       return;
