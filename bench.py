@@ -100,9 +100,14 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
+        return self.summarise(self.lines)
+
+    @staticmethod
+    def summarise(lines):
+        """Median SM clock, max clock and the throttle reasons seen in nvidia-smi CSV lines."""
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -153,7 +158,7 @@ def _traffic_for(kernel: str, workload: str):
     if d.get("source_hash") != _kernel_source_hash():
         return None
     ent = d.get("kernels", {}).get(workload, {}).get(kernel)
-    return None if ent is None else ent.get("dram_bytes_per_launch")
+    return ent
 
 
 def _dist():
@@ -170,6 +175,8 @@ def _barrier(world):
 
 
 def _max_over_ranks(x: float, world: int, device) -> float:
+    """Max of x over the ranks (the slowest rank's time); device is the collective's device
+    (a CUDA device under NCCL, the CPU under gloo)."""
     if world == 1:
         return x
     import torch
@@ -177,6 +184,12 @@ def _max_over_ranks(x: float, world: int, device) -> float:
     t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_value(steps: int, world: int, max_ms: float) -> float:
+    """Whole-job throughput: every rank ran `steps` implicit steps; the job took the slowest
+    rank's time."""
+    return world * steps / (max_ms / 1000.0)
 
 
 # --------------------------------------------------------------------------------------
@@ -357,7 +370,7 @@ def main():
     mixed = _time_form(w, psp.PSP_MIXED, a.steps, a.warmup, device, world, not a.no_profile)
     clk = clocks.stop()
     ms_max = _max_over_ranks(mixed["ms_total"], world, device)
-    value = world * a.steps / (ms_max / 1000.0)
+    value = aggregate_value(a.steps, world, ms_max)
     infos = mixed["infos"]
     prof = mixed["prof"]
     mixed["solver"].close()
@@ -366,7 +379,7 @@ def main():
     if not a.no_fp64_form:
         r = _time_form(w, psp.PSP_FP64, a.steps, a.warmup, device, world, False)
         ms64 = _max_over_ranks(r["ms_total"], world, device)
-        fp64 = {"value": world * a.steps / (ms64 / 1000.0), "ms_per_step": ms64 / a.steps,
+        fp64 = {"value": aggregate_value(a.steps, world, ms64), "ms_per_step": ms64 / a.steps,
                 "iters_per_step": sum(i.iters for i in r["infos"]) / a.steps,
                 "cycles_per_step": sum(i.cycles for i in r["infos"]) / a.steps}
         r["solver"].close()
@@ -400,7 +413,12 @@ def main():
         if kernels:
             dom = max(kernels, key=lambda k: prof[k]["ms"])
             kd = kernels[dom]
-            traffic = _traffic_for(dom, w.name)
+            ent = _traffic_for(dom, w.name)
+            # the capture is one launch at iteration j; traffic scales with the columns
+            # streamed, so it is scaled to the mean launch by its algorithmic bytes
+            traffic = None
+            if ent and ent.get("algorithmic_bytes"):
+                traffic = ent["dram_bytes_per_launch"] / ent["algorithmic_bytes"] * kd["bytes_per_launch"]
             roofline = {"kernel": dom, "bound": "hbm", "achieved": kd["gbs"], "peak": hbm_peak,
                         "unit": "GB/s", "frac": kd["gbs"] / hbm_peak, "traffic": traffic,
                         "peak_kind": peak_kind, "bytes_per_launch": kd["bytes_per_launch"],
