@@ -280,82 +280,43 @@ __device__ __forceinline__ void write_col_partials(const T (&acc)[KS], int k, do
 // out[j] = sum over CTAs of partial[j][cta] in a fixed order, j < nvals (partial rows of
 // length kMaxCta).  Warp w takes j = w, w + 8, ...; lane l takes CTAs l, l + 32, ...;
 // every load is issued before any add.  Ends with a CTA barrier.
-__device__ __forceinline__ void grid_sums(const double *partial, int nvals, int nb, double *out) {
+// out[j] = sum over CTAs of partial[j][cta] in a fixed order, j < nvals (rows of length
+// kMaxCta, element type TP: float in the mixed form, whose dot products are FP32
+// accumulations, double otherwise).  The sums are formed in TP: on GB300 every FP64 warp
+// instruction (conversions included) occupies the narrow FP64 pipe for tens of cycles.
+template <typename TP>
+__device__ __forceinline__ void grid_sums(const TP *partial, int nvals, int nb, TP *out) {
   constexpr int kMinWarps = 8;                                      // blocks of >= 256 threads
   constexpr int MJ = (2 * kMaxM + 2 + kMinWarps - 1) / kMinWarps;   // j values per warp (at most)
   constexpr int MB = kMaxArnCta / 32;                               // CTAs per lane
   constexpr int BATCH = 3;                                          // j values loaded together
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nq = (nb + 31) / 32;
 #pragma unroll
   for (int t0 = 0; t0 < MJ; t0 += BATCH) {
     if (wid + t0 * nw >= nvals) break;
-    double v[BATCH][MB];
+    TP v[BATCH][MB];
 #pragma unroll
     for (int t = 0; t < BATCH; ++t) {
       const int j = wid + (t0 + t) * nw;
 #pragma unroll
       for (int q = 0; q < MB; ++q) {
         const int b = lane + 32 * q;
-        v[t][q] = (j < nvals && b < nb) ? __ldcg(partial + (int64_t)j * kMaxCta + b) : 0.0;
+        v[t][q] = (q < nq && j < nvals && b < nb) ? __ldcg(partial + (int64_t)j * kMaxCta + b) : (TP)0;
       }
     }
 #pragma unroll
     for (int t = 0; t < BATCH; ++t) {
-      double s = 0.0;
+      TP sl = (TP)0;
 #pragma unroll
-      for (int q = 0; q < MB; ++q) s += v[t][q];
-      s = warp_sum(s);
+      for (int q = 0; q < MB; ++q)
+        if (q < nq) sl += v[t][q];
+      sl = warp_sum(sl);
       const int j = wid + (t0 + t) * nw;
-      if (lane == 0 && j < nvals) out[j] = s;
+      if (lane == 0 && j < nvals) out[j] = sl;
     }
   }
   __syncthreads();
-}
-
-// ---------------------------------------------------------------------------------------
-// pass A: partial sums of V_i^T v_j (rows 0..j) and V_i^T w_j (rows j+1..2j+1), i <= j
-// ---------------------------------------------------------------------------------------
-template <typename T, int KS>
-__global__ void __launch_bounds__(kArnThreads) k_dcgs_dots(const __grid_constant__ VMaps mapV,
-                                                           const __grid_constant__ CUtensorMap mapU, int j, int woff,
-                                                           DevState *st, double *partial, int ntiles) {
-  if (st->active == 0) return;
-  using VT = typename Vec<T>::type;
-  extern __shared__ __align__(128) char smem[];
-  __shared__ uint64_t bars[kMaxStages];
-  const int k = j + 1;                      // V columns 0..j
-  const int ucol = ucol_for(k);
-  TilePipe p{smem, bars, ucol + 1, ucol, ntiles, (int)blockIdx.x, (int)gridDim.x, stages_for(k),
-             (st->hist_base + woff) % st->mmax};
-  T av[KS], aw[KS];
-#pragma unroll
-  for (int s = 0; s < KS; ++s) { av[s] = (T)0; aw[s] = (T)0; }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  run_tiles<T>(p, mapV.m, &mapU, st, [] {}, [&](const T *tile, int) {
-    const VT *vseg = reinterpret_cast<const VT *>(tile) + (int64_t)j * kSegVec;
-    const VT *wseg = reinterpret_cast<const VT *>(tile) + (int64_t)ucol * kSegVec;
-    const VT v0 = vseg[lane], v1 = vseg[lane + 32], w0 = wseg[lane], w1 = wseg[lane + 32];
-#pragma unroll
-    for (int s = 0; s < KS; ++s) {
-      const int i = wid + kArnWarps * s;
-      if (i < k) {
-        const VT *seg = reinterpret_cast<const VT *>(tile) + (int64_t)i * kSegVec;
-        const VT x0 = seg[lane], x1 = seg[lane + 32];
-        av[s] += Vec<T>::dot(x0, v0) + Vec<T>::dot(x1, v1);
-        aw[s] += Vec<T>::dot(x0, w0) + Vec<T>::dot(x1, w1);
-      }
-    }
-  });
-#pragma unroll
-  for (int s = 0; s < KS; ++s) {
-    const int i = wid + kArnWarps * s;
-    const T x = warp_sum(av[s]);
-    const T y = warp_sum(aw[s]);
-    if (lane == 0 && i < k) {
-      partial[(int64_t)i * kMaxCta + blockIdx.x] = (double)x;
-      partial[(int64_t)(k + i) * kMaxCta + blockIdx.x] = (double)y;
-    }
-  }
 }
 
 // FP64 Givens step for the completed column kk of H (rows 0..kk+1 in hcol, shared memory),
@@ -407,116 +368,139 @@ __device__ bool givens_column(DevState *st, int kk, double *hcol, double *sC, do
 }
 
 // ---------------------------------------------------------------------------------------
-// pass B: prologue (every CTA): reduce pass A, the DCGS2 coefficients; CTA 0: completed
-// column j-1, Givens, finish test, Hessenberg bookkeeping, and at the end of the cycle the
-// triangular solve Q = H^{-1} G.  Stream (unless final): q_j over v_j in V(:,j) and v_{j+1}
-// in V(:,j+1).  The small dense work runs out of shared memory.
+// DCGS2 scalar engine, run once per iteration by all threads of the last CTA of pass A:
+// reduce the partial sums, form nu_j, complete column j-1, t = Hbar a, h_j, the pass-B
+// coefficients, the Givens step, the finish test and, when the cycle ends, Q = H^{-1} G.
+// Small dense work in FP64 out of shared memory (`scratch`, the freed stage ring).
 // ---------------------------------------------------------------------------------------
-constexpr int kUpdThreads = 256;
+// Arrays of the scalar engine in the precision of the Krylov vectors (FP32 copies in the
+// mixed form; the FP64 Hessenberg used by the Givens step is kept alongside).
+template <typename T> __device__ __forceinline__ T *hc_copy(DevState *st);
+template <> __device__ __forceinline__ float *hc_copy<float>(DevState *st) { return st->HcF; }
+template <> __device__ __forceinline__ double *hc_copy<double>(DevState *st) { return st->Hc; }
+template <typename T> __device__ __forceinline__ T *coef_copy(DevState *st, int which);
+template <> __device__ __forceinline__ float *coef_copy<float>(DevState *st, int which) {
+  return which == 0 ? st->cAF : (which == 1 ? st->cDF : st->c3F);
+}
+template <> __device__ __forceinline__ double *coef_copy<double>(DevState *st, int which) {
+  return which == 0 ? st->cA : (which == 1 ? st->cD : st->c3);
+}
 
 template <typename T>
-__global__ void __launch_bounds__(kUpdThreads) k_dcgs_update(T *__restrict__ V, int64_t ldv, const T *__restrict__ Pyb,
-                                                             int64_t ldh, int j, int woff, DevState *st,
-                                                             const double *partial, int nbA, int64_t nv, int final_step,
-                                                             int mixed) {
-  if (st->active == 0) return;
-  using VT = typename Vec<T>::type;
+__device__ void dcgs_scalar(DevState *st, int j, int final_step, const T *partial, int nb, T *scratch) {
   constexpr int ld = kMaxM + 1;
-  __shared__ double s_sum[2 * kMaxM + 2];
-  __shared__ double sH[kMaxM * (kMaxM + 1)];   // completed columns 0..j-2 (rows 0..j), later the rotated H
-  __shared__ double s_a[kMaxM], s_t[kMaxM + 1], s_hcol[kMaxM + 2];
-  __shared__ double sC[kMaxM], sS[kMaxM], sG[kMaxM + 1];
-  __shared__ double s_sc[4];   // nu, a^T a, a^T b, breakdown
-  __shared__ T s_sa[kMaxM], s_sd[kMaxM];
-  __shared__ T s_coef[3];
-  __shared__ int s_end;
+  T *s_sum = scratch;                                             // 2 kMaxM + 2
+  T *sH = s_sum + 2 * kMaxM + 2;                                  // kMaxM * ld
+  T *s_a = sH + kMaxM * ld;                                       // kMaxM
+  T *s_t = s_a + kMaxM;                                           // kMaxM + 1
+  T *s_hcol = s_t + kMaxM + 1;                                    // kMaxM + 2
+  T *s_sc = s_hcol + kMaxM + 2;                                   // 4
+  const T *HcT = hc_copy<T>(st);
+  T *HcTw = hc_copy<T>(st);
   const int k = j + 1;
-  const bool cta0 = blockIdx.x == 0;
-  // completed columns 0..j-2 of Hbar (rows 0..j) and, in CTA 0, the rotations and G
-  for (int e = threadIdx.x; e < (j > 1 ? (j - 1) * ld : 0); e += blockDim.x) sH[e] = st->Hc[e];
-  if (cta0)
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-      if (i < j) { sC[i] = st->C[i]; sS[i] = st->S[i]; }
-      sG[i] = st->G[i];
-    }
+  for (int e = threadIdx.x; e < (j > 1 ? (j - 1) * ld : 0); e += blockDim.x) sH[e] = HcT[e];
   if (j >= 1)
-    for (int r = threadIdx.x; r < j; r += blockDim.x) s_hcol[r] = st->Hf[(int64_t)(j - 1) * ld + r];
-  grid_sums(partial, 2 * k, nbA, s_sum);   // ends with a barrier
+    for (int r = threadIdx.x; r < j; r += blockDim.x) s_hcol[r] = (T)st->Hf[(int64_t)(j - 1) * ld + r];
+  grid_sums<T>(partial, 2 * k, nb, s_sum);   // ends with a barrier
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (wid == 0) {
-    double aa = 0.0, ab = 0.0;
+    T aa = (T)0, ab = (T)0;
     for (int i = lane; i < j; i += 32) {
-      s_a[i] = s_sum[i];
-      aa += s_sum[i] * s_sum[i];
-      ab += s_sum[i] * s_sum[k + i];
+      const T ai = s_sum[i];
+      s_a[i] = ai;
+      aa += ai * ai;
+      ab += ai * s_sum[k + i];
     }
     aa = warp_sum(aa);
     ab = warp_sum(ab);
     if (lane == 0) {
-      const double alpha = s_sum[j];
-      const double nu2 = alpha - aa;
-      const bool brk = !(nu2 > kBreakdownRel * kBreakdownRel * alpha) || !isfinite(nu2);
-      s_sc[0] = brk ? 0.0 : sqrt(nu2);
-      s_sc[1] = aa;
+      const T alpha = s_sum[j];
+      const T nu2 = alpha - aa;
+      const bool brk = !(nu2 > (T)(kBreakdownRel * kBreakdownRel) * alpha) || !isfinite(nu2);
+      s_sc[0] = brk ? (T)0 : sqrt(nu2);
       s_sc[2] = ab;
-      s_sc[3] = brk ? 1.0 : 0.0;
+      st->dc_brk = brk ? 1 : 0;
     }
   }
   __syncthreads();
-  const double nu = s_sc[0];
-  const bool brk = s_sc[3] != 0.0;
-  // completed column j-1: first projection + a, and nu in row j
+  const T nu = s_sc[0];
+  // completed column j-1 (first projection + a, nu in row j): kept for the Givens step
   if (j >= 1)
-    for (int r = threadIdx.x; r <= j; r += blockDim.x) s_hcol[r] = (r < j) ? s_hcol[r] + s_a[r] : nu;
+    for (int r = threadIdx.x; r <= j; r += blockDim.x) {
+      const T v = (r < j) ? s_hcol[r] + s_a[r] : nu;
+      s_hcol[r] = v;
+      st->Hc[(int64_t)(j - 1) * ld + r] = (double)v;
+      HcTw[(int64_t)(j - 1) * ld + r] = v;
+    }
   __syncthreads();
-  // t = Hbar a (rows 0..j)
-  for (int r = threadIdx.x; r <= j; r += blockDim.x) {
-    double t = 0.0;
+  for (int r = threadIdx.x; r <= j; r += blockDim.x) {   // t = Hbar a
+    T t = (T)0;
     for (int i = (r > 0 ? r - 1 : 0); i < j; ++i) t += ((i == j - 1) ? s_hcol[r] : sH[i * ld + r]) * s_a[i];
     s_t[r] = t;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    const double beta = s_sum[k + j];
-    const double inv = (nu > 0.0) ? 1.0 / nu : 0.0;
-    for (int r = 0; r <= j; ++r) {
-      const double proj = (r < j) ? s_sum[k + r] : (beta - s_sc[2]) * inv;
-      const double h = (proj - s_t[r]) * inv;
-      if (cta0 && !final_step) st->Hf[(int64_t)j * ld + r] = h;
-      s_t[r] = s_t[r] * inv + h;   // c_r
-    }
-    const double cj = s_t[j];
-    for (int i = 0; i < j; ++i) {
-      s_sa[i] = (T)(s_a[i] * inv);
-      s_sd[i] = (T)(s_t[i] - cj * inv * s_a[i]);
-    }
-    s_coef[0] = (T)inv;
-    s_coef[1] = (T)(cj * inv);
-    s_coef[2] = (T)inv;
-    s_end = 0;
-    if (cta0) {
-      bool end = false;
-      if (j >= 1) {
-        for (int r = 0; r <= j; ++r) st->Hc[(int64_t)(j - 1) * ld + r] = s_hcol[r];
-        end = givens_column(st, j - 1, s_hcol, sC, sS, sG, brk, final_step != 0, mixed);
-      } else if (brk || final_step) {
-        end = true;   // v_0 = 0: nothing to do
-        st->k_end = 0;
-        st->sum.k_end = 0;
-      }
-      if (end) {
-        st->active = 0;
-        // matvecs of this cycle: iterations 0..j had one each, the final step none
-        st->hist_count = st->hist_base + 1 + (final_step ? j : j + 1);
-        st->sum.hist_count = st->hist_count;
-      }
-      s_end = end ? 1 : 0;
-    }
+  const T inv = (nu > (T)0) ? (T)1 / nu : (T)0;
+  const T beta = s_sum[k + j];
+  for (int r = threadIdx.x; r <= j; r += blockDim.x) {
+    const T proj = (r < j) ? s_sum[k + r] : (beta - s_sc[2]) * inv;
+    const T h = (proj - s_t[r]) * inv;
+    if (!final_step) st->Hf[(int64_t)j * ld + r] = (double)h;
+    s_t[r] = s_t[r] * inv + h;                    // c_r
   }
   __syncthreads();
-  if (cta0 && s_end) {
+  const T cj = s_t[j];
+  T *cA = coef_copy<T>(st, 0), *cD = coef_copy<T>(st, 1), *c3 = coef_copy<T>(st, 2);
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    cA[i] = s_a[i] * inv;
+    cD[i] = s_t[i] - cj * inv * s_a[i];
+  }
+  if (threadIdx.x == 0) {
+    c3[0] = inv;
+    c3[1] = cj * inv;
+    c3[2] = inv;
+  }
+}
+
+// Givens step for column j-1 (completed by the scalar engine of this iteration), the
+// finish test and, when the cycle ends, Q = H^{-1} G; one CTA of pass B, concurrently with
+// the stream of the other CTAs.
+__device__ void dcgs_givens(DevState *st, int j, int final_step, int mixed, double *scratch) {
+  constexpr int ld = kMaxM + 1;
+  double *s_hcol = scratch;                   // kMaxM + 2
+  double *sC = s_hcol + kMaxM + 2;            // kMaxM
+  double *sS = sC + kMaxM;                    // kMaxM
+  double *sG = sS + kMaxM;                    // kMaxM + 1
+  double *s_t = sG + kMaxM + 1;               // kMaxM + 1
+  double *sH = s_t + kMaxM + 1;               // kMaxM * ld
+  __shared__ int s_end;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    if (i < j) { sC[i] = st->C[i]; sS[i] = st->S[i]; }
+    sG[i] = st->G[i];
+    if (j >= 1) s_hcol[i] = st->Hc[(int64_t)(j - 1) * ld + i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const bool brk = st->dc_brk != 0;
+    bool end = false;
+    if (j >= 1) {
+      end = givens_column(st, j - 1, s_hcol, sC, sS, sG, brk, final_step != 0, mixed);
+    } else if (brk || final_step) {
+      end = true;   // v_0 = 0: nothing to do
+      st->k_end = 0;
+      st->sum.k_end = 0;
+    }
+    if (end) {
+      st->active = 0;
+      // matvecs of this cycle: iterations 0..j had one each, the final step none
+      st->hist_count = st->hist_base + 1 + (final_step ? j : j + 1);
+      st->sum.hist_count = st->hist_count;
+    }
+    s_end = end ? 1 : 0;
+  }
+  __syncthreads();
+  if (s_end) {
     // Q = H^{-1} G on the leading kend x kend triangle of the rotated H (column-oriented
-    // back substitution in shared memory); the basis scales of the update become 1
+    // back substitution); the basis scales of the update become 1
     const int kend = st->k_end;
     for (int e = threadIdx.x; e < kend * ld; e += blockDim.x) sH[e] = st->H[e];
     for (int i = threadIdx.x; i <= kend; i += blockDim.x) s_t[i] = st->G[i];
@@ -530,17 +514,94 @@ __global__ void __launch_bounds__(kUpdThreads) k_dcgs_update(T *__restrict__ V, 
       __syncthreads();
     }
   }
-  if (final_step) return;
-  // stream: q_j and v_{j+1}.  Columns are taken in chunks of 8 with the column index
-  // clamped to j-1 and a zero coefficient past j, so the 8 loads of a chunk (for two
-  // vectors per thread) are issued together.
-  for (int i = j + threadIdx.x; i < kMaxM; i += blockDim.x) { s_sa[i] = (T)0; s_sd[i] = (T)0; }
+}
+
+// Shared memory (doubles) the scalar engine needs.
+constexpr int kScalarDoubles = (2 * kMaxM + 2) + kMaxM * (kMaxM + 1) + kMaxM + (kMaxM + 1) + (kMaxM + 2) + 4;
+// ... and the Givens CTA of pass B
+constexpr int kGivensDoubles = (kMaxM + 2) + 2 * kMaxM + 2 * (kMaxM + 1) + kMaxM * (kMaxM + 1);
+
+// ---------------------------------------------------------------------------------------
+// pass A: partial sums of V_i^T v_j (rows 0..j) and V_i^T w_j (rows j+1..2j+1), i <= j
+// ---------------------------------------------------------------------------------------
+template <typename T, int KS>
+__global__ void __launch_bounds__(kArnThreads) k_dcgs_dots(const __grid_constant__ VMaps mapV,
+                                                           const __grid_constant__ CUtensorMap mapU, int j, int woff,
+                                                           DevState *st, T *partial, int ntiles, int final_step) {
+  if (st->active == 0) return;
+  using VT = typename Vec<T>::type;
+  extern __shared__ __align__(128) char smem[];
+  __shared__ uint64_t bars[kMaxStages];
+  const int k = j + 1;                      // V columns 0..j
+  const int ucol = ucol_for(k);
+  TilePipe p{smem, bars, ucol + 1, ucol, ntiles, (int)blockIdx.x, (int)gridDim.x, stages_for(k),
+             (st->hist_base + woff) % st->mmax};
+  T av[KS], aw[KS];
+#pragma unroll
+  for (int s = 0; s < KS; ++s) { av[s] = (T)0; aw[s] = (T)0; }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  run_tiles<T>(p, mapV.m, &mapU, st, [] {}, [&](const T *tile, int) {
+    const VT *vseg = reinterpret_cast<const VT *>(tile) + (int64_t)j * kSegVec;
+    const VT *wseg = reinterpret_cast<const VT *>(tile) + (int64_t)ucol * kSegVec;
+    const VT v0 = vseg[lane], v1 = vseg[lane + 32], w0 = wseg[lane], w1 = wseg[lane + 32];
+#pragma unroll
+    for (int s = 0; s < KS; ++s) {
+      const int i = wid + kArnWarps * s;
+      if (i < k) {
+        const VT *seg = reinterpret_cast<const VT *>(tile) + (int64_t)i * kSegVec;
+        const VT x0 = seg[lane], x1 = seg[lane + 32];
+        av[s] += Vec<T>::dot(x0, v0) + Vec<T>::dot(x1, v1);
+        aw[s] += Vec<T>::dot(x0, w0) + Vec<T>::dot(x1, w1);
+      }
+    }
+  });
+#pragma unroll
+  for (int s = 0; s < KS; ++s) {
+    const int i = wid + kArnWarps * s;
+    const T x = warp_sum(av[s]);
+    const T y = warp_sum(aw[s]);
+    if (lane == 0 && i < k) {
+      partial[(int64_t)i * kMaxCta + blockIdx.x] = x;
+      partial[(int64_t)(k + i) * kMaxCta + blockIdx.x] = y;
+    }
+  }
+  if (!last_block_arrive(&st->counter[1])) return;
+  dcgs_scalar<T>(st, j, final_step, partial, gridDim.x, reinterpret_cast<T *>(smem));
+  last_block_reset(&st->counter[1]);
+}
+
+
+// ---------------------------------------------------------------------------------------
+// pass B: q_j over v_j in V(:,j) and v_{j+1} in V(:,j+1), with the coefficients formed by
+// the scalar engine.  Columns are taken in chunks of 8 with the column index clamped to
+// j-1 and a zero coefficient past j, so the 8 loads of a chunk (for two vectors per
+// thread) are issued together.
+// ---------------------------------------------------------------------------------------
+constexpr int kUpdThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kUpdThreads) k_dcgs_update(T *__restrict__ V, int64_t ldv, const T *__restrict__ Pyb,
+                                                             int64_t ldh, int j, int woff, DevState *st, int64_t nv,
+                                                             int final_step, int mixed) {
+  if (st->active == 0) return;   // the cycle ended: nothing to do
+  extern __shared__ __align__(16) double dsm[];
+  if (blockIdx.x == gridDim.x - 1) {   // the Givens CTA
+    dcgs_givens(st, j, final_step, mixed, dsm);
+    return;
+  }
+  using VT = typename Vec<T>::type;
+  __shared__ T s_sa[kMaxM], s_sd[kMaxM];
+  const T *cA = coef_copy<T>(st, 0), *cD = coef_copy<T>(st, 1), *c3 = coef_copy<T>(st, 2);
+  for (int i = threadIdx.x; i < kMaxM; i += blockDim.x) {
+    s_sa[i] = (i < j) ? cA[i] : (T)0;
+    s_sd[i] = (i < j) ? cD[i] : (T)0;
+  }
+  const T sv = c3[0], cv = c3[1], sw = c3[2];
   __syncthreads();
   VT *vj = reinterpret_cast<VT *>(V + (int64_t)j * ldv);
   VT *vn = reinterpret_cast<VT *>(V + (int64_t)(j + 1) * ldv);
   const VT *w = reinterpret_cast<const VT *>(Pyb + (int64_t)((st->hist_base + woff) % st->mmax) * ldh);
-  const T sv = s_coef[0], cv = s_coef[1], sw = s_coef[2];
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t stride = (int64_t)(gridDim.x - 1) * blockDim.x;   // streaming CTAs
   for (int64_t iv = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; iv < nv; iv += 2 * stride) {
     const int64_t iv2 = iv + stride;
     const bool two = iv2 < nv;
@@ -633,6 +694,8 @@ void arnoldi_setup() {
   arnoldi_grid();
   set_attrs_t<float>();
   set_attrs_t<double>();
+  cudaFuncSetAttribute(k_dcgs_update<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kGivensDoubles * sizeof(double)));
+  cudaFuncSetAttribute(k_dcgs_update<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kGivensDoubles * sizeof(double)));
 }
 
 template <typename T>
@@ -642,23 +705,28 @@ void launch_arnoldi(int j, int final_step, int64_t n, const ArnoldiMaps &maps, T
   int grid = std::min(ntiles, arnoldi_grid());
   if (grid < 1) grid = 1;
   const int k = j + 1;
-  const size_t sm = pass_smem(k);
+  // the stage ring, later reused by the last CTA as the scalar engine's scratch
+  const size_t sm = std::max(pass_smem(k), (size_t)kScalarDoubles * sizeof(double));
   const int woff = 1 + j;   // ring column of w_j relative to the cycle's restart column
   const VMaps &mV = *reinterpret_cast<const VMaps *>(maps.V);
   const CUtensorMap &mU = *reinterpret_cast<const CUtensorMap *>(maps.Py);
   switch ((k + kArnWarps - 1) / kArnWarps) {
 #define PSP_DOTS(KS_) \
-  case KS_: k_dcgs_dots<T, KS_><<<grid, kArnThreads, sm, s>>>(mV, mU, j, woff, st, partial, ntiles); break;
+  case KS_: k_dcgs_dots<T, KS_><<<grid, kArnThreads, sm, s>>>(mV, mU, j, woff, st, reinterpret_cast<T *>(partial), ntiles, final_step); break;
     PSP_DOTS(1) PSP_DOTS(2) PSP_DOTS(3) PSP_DOTS(4) PSP_DOTS(5)
 #undef PSP_DOTS
     default: break;
   }
   if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
   if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
-  const int64_t nv = (ldv + Vec<T>::W - 1) / Vec<T>::W;
-  int ugrid = final_step ? 1 : (int)std::min<int64_t>((nv + kUpdThreads - 1) / kUpdThreads, (int64_t)arnoldi_grid() * 4);
-  if (ugrid < 1) ugrid = 1;
-  k_dcgs_update<T><<<ugrid, kUpdThreads, 0, s>>>(V, ldv, Py, ldh, j, woff, st, partial, grid, nv, final_step, mixed);
+  {
+    // streaming CTAs (none for the final step) plus one CTA for the Givens step
+    const int64_t nv = (ldv + Vec<T>::W - 1) / Vec<T>::W;
+    int ugrid = final_step ? 0 : (int)std::min<int64_t>((nv + kUpdThreads - 1) / kUpdThreads, (int64_t)arnoldi_grid() * 4);
+    if (!final_step && ugrid < 1) ugrid = 1;
+    k_dcgs_update<T><<<ugrid + 1, kUpdThreads, kGivensDoubles * sizeof(double), s>>>(V, ldv, Py, ldh, j, woff, st, nv,
+                                                                                     final_step, mixed);
+  }
   if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);
 }
 

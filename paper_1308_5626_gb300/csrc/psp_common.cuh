@@ -63,6 +63,15 @@ struct DevState {
   double h1[kMaxM + 1];               // first Gram-Schmidt projection coefficients
   double h2[kMaxM + 1];               // second (re-orthogonalisation) coefficients
   double R[kMaxM];                    // R(k) of the current cycle
+  double cA[kMaxM];                   // DCGS2 update coefficients of the current iteration
+  double cD[kMaxM];
+  double c3[4];
+  float HcF[(kMaxM + 1) * kMaxM];     // FP32 copies for the mixed form's scalar engine
+  float cAF[kMaxM];
+  float cDF[kMaxM];
+  float c3F[4];
+  int dc_brk;                         // breakdown seen by this iteration's scalar engine
+  int pad2;
   // stencil coefficients of A = I - dt L for the current dt: coef[d][j + kMaxR]
   double coef[3][2 * kMaxR + 1];
   // last-block counters of the grid reductions
@@ -87,16 +96,18 @@ __device__ __forceinline__ T warp_sum(T v) {
 // Signal that this CTA finished writing its partials; returns true in the last CTA.
 // Standard "last block" pattern: fence, count, the last arriving CTA reduces.  No
 // thread waits for another CTA.
+// The barrier makes every thread's writes visible to thread 0, whose GPU-scope fence then
+// releases them (fences are cumulative) before its arrival is counted.
 __device__ __forceinline__ bool last_block_arrive(unsigned int *counter) {
   __shared__ bool s_last;
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     unsigned int t = atomicAdd(counter, 1u);
     s_last = (t == gridDim.x - 1);
+    if (s_last) __threadfence();
   }
   __syncthreads();
-  if (s_last) __threadfence();
   return s_last;
 }
 
