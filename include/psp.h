@@ -86,6 +86,10 @@ typedef struct {
                         (default 1e-5); the step ends on the FP64 true residual */
   int accept_rule;   /* 1 (default): a fitted N is adopted only if it converges at least
                         as fast on the next step's first cycle; 0: always adopt */
+  int fuse_matvec;   /* 1 (default): the Arnoldi matvec w = A N^{-1} v runs inside the first
+                        Gram-Schmidt pass when every grid row is a whole number of 16-byte
+                        vectors wider than the stencil halo; 0: as a kernel of its own.
+                        Same arithmetic either way. */
 } psp_opts;
 
 typedef struct {

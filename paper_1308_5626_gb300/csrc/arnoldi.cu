@@ -158,9 +158,10 @@ struct VMaps {
   CUtensorMap m[3];
 };
 
+// V segments of one tile into `stage` (thread 0); the mbarrier expects the whole stage,
+// U included.
 template <typename T>
-__device__ __forceinline__ void issue_tile(const TilePipe &p, int stage, int tile, const CUtensorMap *mapV,
-                                           const CUtensorMap *mapU) {
+__device__ __forceinline__ void issue_tile_v(const TilePipe &p, int stage, int tile, const CUtensorMap *mapV) {
   constexpr int TR = kSegBytes / sizeof(T);   // rows per tile
   char *base = p.buf + (int64_t)stage * p.ncols * kSegBytes;
   mbar_expect_tx(&p.bar[stage], (uint32_t)(p.ncols * kSegBytes));
@@ -168,7 +169,19 @@ __device__ __forceinline__ void issue_tile(const TilePipe &p, int stage, int til
   for (; cb + 16 <= p.ucol; cb += 16) tma_load_2d(base + (int64_t)cb * kSegBytes, &mapV[0], tile * TR, cb, &p.bar[stage]);
   for (; cb + 4 <= p.ucol; cb += 4) tma_load_2d(base + (int64_t)cb * kSegBytes, &mapV[1], tile * TR, cb, &p.bar[stage]);
   for (; cb < p.ucol; ++cb) tma_load_2d(base + (int64_t)cb * kSegBytes, &mapV[2], tile * TR, cb, &p.bar[stage]);
+}
+// U segment of one tile (thread 0).
+template <typename T>
+__device__ __forceinline__ void issue_tile_u(const TilePipe &p, int stage, int tile, const CUtensorMap *mapU) {
+  constexpr int TR = kSegBytes / sizeof(T);
+  char *base = p.buf + (int64_t)stage * p.ncols * kSegBytes;
   tma_load_2d(base + (int64_t)p.ucol * kSegBytes, mapU, tile * TR, p.uring, &p.bar[stage]);
+}
+template <typename T>
+__device__ __forceinline__ void issue_tile(const TilePipe &p, int stage, int tile, const CUtensorMap *mapV,
+                                           const CUtensorMap *mapU) {
+  issue_tile_v<T>(p, stage, tile, mapV);
+  issue_tile_u<T>(p, stage, tile, mapU);
 }
 
 // Drives the pipeline: calls body(stage_ptr, tile) for each of this CTA's tiles.
@@ -178,9 +191,12 @@ __device__ __forceinline__ uint32_t dynamic_smem_bytes() {
   return r;
 }
 
+// With defer_u the prologue writes U itself (the matvec folded into the pass): the V
+// segments of the first stages are issued before it and their U segments after it, once
+// its global writes are ordered before the bulk copies that read them.
 template <typename T, typename Body, typename Pro>
 __device__ __forceinline__ void run_tiles(TilePipe &p, const CUtensorMap *mapV, const CUtensorMap *mapU, DevState *st,
-                                          Pro prologue, Body body) {
+                                          bool defer_u, Pro prologue, Body body) {
   const int kStages = p.nst;
   // the stage ring must fit the dynamic shared memory of this launch; otherwise no copy
   // is issued and the error flag is set
@@ -194,9 +210,15 @@ __device__ __forceinline__ void run_tiles(TilePipe &p, const CUtensorMap *mapV, 
   __syncthreads();
   const int my = (p.ntiles - p.first + p.step - 1) / p.step;   // tiles of this CTA
   if (threadIdx.x == 0)
-    for (int i = 0; i < kStages && i < my; ++i) issue_tile<T>(p, i, p.first + i * p.step, mapV, mapU);
-  prologue();          // runs while the first tiles are in flight
+    for (int i = 0; i < kStages && i < my; ++i) {
+      if (defer_u) issue_tile_v<T>(p, i, p.first + i * p.step, mapV);
+      else issue_tile<T>(p, i, p.first + i * p.step, mapV, mapU);
+    }
+  prologue(my);        // runs while the first tiles are in flight
+  if (defer_u) asm volatile("fence.proxy.async.global;" ::: "memory");
   __syncthreads();
+  if (defer_u && threadIdx.x == 0)
+    for (int i = 0; i < kStages && i < my; ++i) issue_tile_u<T>(p, i, p.first + i * p.step, mapU);
   bool ok = true;
   for (int i = 0; i < my; ++i) {
     const int s = i % kStages;
@@ -220,6 +242,128 @@ __device__ __forceinline__ void run_tiles(TilePipe &p, const CUtensorMap *mapV, 
       for (int i = (my > kStages ? my - kStages : 0); i < my; ++i) mbar_wait(&p.bar[i % kStages], (uint32_t)((i / kStages) & 1));
     __syncthreads();
   }
+}
+
+// The matvec of the iteration, w = A x (Eq. 4: A = I - dt L with the finite-difference
+// stencil of L), on the rows of this CTA's tiles: thread e of the CTA takes vector e % 64
+// of tile e / 64 (16-byte vectors of W points along x), one or two vectors per round with
+// every load of the round issued before the arithmetic.  The x terms come from a register
+// window of the row, the y and z terms from one vector per neighbour row (periodic).  With
+// xc set, x is also copied there (P_x column of an unpreconditioned cycle).  Needs
+// nx % W == 0 and more vectors per row than halo vectors.
+template <typename T, int NDIM, int R>
+__device__ __forceinline__ void tile_matvec_t(const T *__restrict__ x, T *__restrict__ w, T *__restrict__ xc,
+                                           const T (*c)[2 * kMaxR + 1], int nx, int ny, int nz, int first,
+                                           int step, int my) {
+  using VT = typename Vec<T>::type;
+  constexpr int W = Vec<T>::W;
+  constexpr int NH = (R + W - 1) / W;          // halo vectors on each side along x
+  constexpr int NY = NDIM >= 2 ? R : 0, NZ = NDIM >= 3 ? R : 0;
+  // vectors per thread and round: two while their loads fit in about 80 registers
+  constexpr int kLoads = 2 * NH + 1 + 2 * NY + 2 * NZ;
+  constexpr int U = kLoads <= 10 ? 2 : 1;
+  const int nxv = nx / W, plane = nx * ny;
+  const int nvec = nxv * ny * nz;
+  const int total = my * kSegVec;
+  for (int e0 = threadIdx.x; e0 < total; e0 += U * blockDim.x) {
+    int iv[U];
+    bool ok[U];
+    VT win[U][2 * NH + 1], ym[U][NY > 0 ? NY : 1], yp[U][NY > 0 ? NY : 1], zm[U][NZ > 0 ? NZ : 1],
+        zp[U][NZ > 0 ? NZ : 1];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * blockDim.x;
+      iv[u] = (first + (e / kSegVec) * step) * kSegVec + (e % kSegVec);
+      ok[u] = e < total && iv[u] < nvec;
+      if (!ok[u]) iv[u] = 0;   // loads of a padding lane stay in bounds; nothing is stored
+      const int row = iv[u] / nxv;
+      const int xv = iv[u] - row * nxv;
+      const int iz = row / ny;
+      const int iy = row - iz * ny;
+      const int base = row * nx;
+#pragma unroll
+      for (int h = -NH; h <= NH; ++h) {
+        int v = xv + h;
+        v += (v < 0) ? nxv : 0;
+        v -= (v >= nxv) ? nxv : 0;
+        win[u][h + NH] = *reinterpret_cast<const VT *>(x + base + v * W);
+      }
+#pragma unroll
+      for (int jj = 1; jj <= NY; ++jj) {
+        int m = iy - jj; m += (m < 0) ? ny : 0;
+        int p = iy + jj; p -= (p >= ny) ? ny : 0;
+        ym[u][jj - 1] = *reinterpret_cast<const VT *>(x + iz * plane + m * nx + xv * W);
+        yp[u][jj - 1] = *reinterpret_cast<const VT *>(x + iz * plane + p * nx + xv * W);
+      }
+#pragma unroll
+      for (int jj = 1; jj <= NZ; ++jj) {
+        int m = iz - jj; m += (m < 0) ? nz : 0;
+        int p = iz + jj; p -= (p >= nz) ? nz : 0;
+        zm[u][jj - 1] = *reinterpret_cast<const VT *>(x + m * plane + iy * nx + xv * W);
+        zp[u][jj - 1] = *reinterpret_cast<const VT *>(x + p * plane + iy * nx + xv * W);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const T *wn = reinterpret_cast<const T *>(&win[u][0]);   // (2 NH + 1) W points
+      T acc[W];
+#pragma unroll
+      for (int i = 0; i < W; ++i) {
+        T s = c[0][kMaxR] * wn[NH * W + i];
+#pragma unroll
+        for (int jj = 1; jj <= R; ++jj)
+          s += c[0][kMaxR - jj] * wn[NH * W + i - jj] + c[0][kMaxR + jj] * wn[NH * W + i + jj];
+        acc[i] = s;
+      }
+#pragma unroll
+      for (int jj = 1; jj <= NY; ++jj) {
+        const T *me = reinterpret_cast<const T *>(&ym[u][jj - 1]), *pe = reinterpret_cast<const T *>(&yp[u][jj - 1]);
+#pragma unroll
+        for (int i = 0; i < W; ++i) acc[i] += c[1][kMaxR - jj] * me[i] + c[1][kMaxR + jj] * pe[i];
+      }
+#pragma unroll
+      for (int jj = 1; jj <= NZ; ++jj) {
+        const T *me = reinterpret_cast<const T *>(&zm[u][jj - 1]), *pe = reinterpret_cast<const T *>(&zp[u][jj - 1]);
+#pragma unroll
+        for (int i = 0; i < W; ++i) acc[i] += c[2][kMaxR - jj] * me[i] + c[2][kMaxR + jj] * pe[i];
+      }
+      if (ok[u]) {
+        VT out;
+        T *oe = reinterpret_cast<T *>(&out);
+#pragma unroll
+        for (int i = 0; i < W; ++i) oe[i] = acc[i];
+        reinterpret_cast<VT *>(w)[iv[u]] = out;
+        if (xc) reinterpret_cast<VT *>(xc)[iv[u]] = win[u][NH];
+      }
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void tile_matvec(const TileMatvec<T> &mv, const T (*c)[2 * kMaxR + 1], int first, int step,
+                                            int my) {
+  const T *x = mv.x.get();
+  T *w = mv.w.get();
+  T *xc = mv.xcopy.base ? mv.xcopy.get() : nullptr;
+#define PSP_TMV(D_, R_) \
+  tile_matvec_t<T, D_, R_>(x, w, xc, c, mv.nx, mv.ny, mv.nz, first, step, my)
+#define PSP_TMV_R(D_)                  \
+  switch (mv.R) {                      \
+    case 1: PSP_TMV(D_, 1); break;     \
+    case 2: PSP_TMV(D_, 2); break;     \
+    case 3: PSP_TMV(D_, 3); break;     \
+    case 4: PSP_TMV(D_, 4); break;     \
+    case 5: PSP_TMV(D_, 5); break;     \
+    default: break;                    \
+  }
+  switch (mv.ndim) {
+    case 1: PSP_TMV_R(1); break;
+    case 2: PSP_TMV_R(2); break;
+    case 3: PSP_TMV_R(3); break;
+    default: break;
+  }
+#undef PSP_TMV_R
+#undef PSP_TMV
 }
 
 // Per-warp column ownership: warp w owns columns j = w + kArnWarps * s, s < KS.  Lane l
@@ -527,11 +671,18 @@ constexpr int kGivensDoubles = (kMaxM + 2) + 2 * kMaxM + 2 * (kMaxM + 1) + kMaxM
 template <typename T, int KS>
 __global__ void __launch_bounds__(kArnThreads) k_dcgs_dots(const __grid_constant__ VMaps mapV,
                                                            const __grid_constant__ CUtensorMap mapU, int j, int woff,
-                                                           DevState *st, T *partial, int ntiles, int final_step) {
+                                                           DevState *st, T *partial, int ntiles, int final_step,
+                                                           const TileMatvec<T> mv) {
   if (st->active == 0) return;
   using VT = typename Vec<T>::type;
   extern __shared__ __align__(128) char smem[];
   __shared__ uint64_t bars[kMaxStages];
+  __shared__ T s_c[3][2 * kMaxR + 1];
+  const bool fused = mv.x.base != nullptr;
+  if (fused && threadIdx.x < 3 * (2 * kMaxR + 1))
+    s_c[threadIdx.x / (2 * kMaxR + 1)][threadIdx.x % (2 * kMaxR + 1)] =
+        (T)st->coef[threadIdx.x / (2 * kMaxR + 1)][threadIdx.x % (2 * kMaxR + 1)];
+  // (the pipeline's first CTA barrier orders these writes before the prologue)
   const int k = j + 1;                      // V columns 0..j
   const int ucol = ucol_for(k);
   TilePipe p{smem, bars, ucol + 1, ucol, ntiles, (int)blockIdx.x, (int)gridDim.x, stages_for(k),
@@ -540,7 +691,9 @@ __global__ void __launch_bounds__(kArnThreads) k_dcgs_dots(const __grid_constant
 #pragma unroll
   for (int s = 0; s < KS; ++s) { av[s] = (T)0; aw[s] = (T)0; }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  run_tiles<T>(p, mapV.m, &mapU, st, [] {}, [&](const T *tile, int) {
+  run_tiles<T>(p, mapV.m, &mapU, st, fused, [&](int my) {
+    if (fused) tile_matvec<T>(mv, s_c, p.first, p.step, my);
+  }, [&](const T *tile, int) {
     const VT *vseg = reinterpret_cast<const VT *>(tile) + (int64_t)j * kSegVec;
     const VT *wseg = reinterpret_cast<const VT *>(tile) + (int64_t)ucol * kSegVec;
     const VT v0 = vseg[lane], v1 = vseg[lane + 32], w0 = wseg[lane], w1 = wseg[lane + 32];
@@ -566,6 +719,9 @@ __global__ void __launch_bounds__(kArnThreads) k_dcgs_dots(const __grid_constant
     }
   }
   if (!last_block_arrive(&st->counter[1])) return;
+  // pass B (a programmatic dependent) may start its CTAs now; it waits for this grid
+  // before it reads anything the scalar engine writes
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   dcgs_scalar<T>(st, j, final_step, partial, gridDim.x, reinterpret_cast<T *>(smem));
   last_block_reset(&st->counter[1]);
 }
@@ -583,6 +739,9 @@ template <typename T>
 __global__ void __launch_bounds__(kUpdThreads) k_dcgs_update(T *__restrict__ V, int64_t ldv, const T *__restrict__ Pyb,
                                                              int64_t ldh, int j, int woff, DevState *st, int64_t nv,
                                                              int final_step, int mixed) {
+  // Launched as a programmatic dependent of pass A: the CTAs may be scheduled while pass
+  // A's last CTA still forms the coefficients, and wait here for that grid to finish.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   if (st->active == 0) return;   // the cycle ended: nothing to do
   extern __shared__ __align__(16) double dsm[];
   if (blockIdx.x == gridDim.x - 1) {   // the Givens CTA
@@ -700,7 +859,9 @@ void arnoldi_setup() {
 
 template <typename T>
 void launch_arnoldi(int j, int final_step, int64_t n, const ArnoldiMaps &maps, T *V, int64_t ldv, const T *Py,
-                    int64_t ldh, DevState *st, double *partial, int mixed, cudaStream_t s, cudaEvent_t *ev) {
+                    int64_t ldh, DevState *st, double *partial, int mixed, cudaStream_t s, cudaEvent_t *ev,
+                    const TileMatvec<T> *mv) {
+  const TileMatvec<T> m = mv ? *mv : TileMatvec<T>{};
   const int ntiles = (int)((ldv * (int64_t)sizeof(T)) / kSegBytes);
   int grid = std::min(ntiles, arnoldi_grid());
   if (grid < 1) grid = 1;
@@ -712,7 +873,7 @@ void launch_arnoldi(int j, int final_step, int64_t n, const ArnoldiMaps &maps, T
   const CUtensorMap &mU = *reinterpret_cast<const CUtensorMap *>(maps.Py);
   switch ((k + kArnWarps - 1) / kArnWarps) {
 #define PSP_DOTS(KS_) \
-  case KS_: k_dcgs_dots<T, KS_><<<grid, kArnThreads, sm, s>>>(mV, mU, j, woff, st, reinterpret_cast<T *>(partial), ntiles, final_step); break;
+  case KS_: k_dcgs_dots<T, KS_><<<grid, kArnThreads, sm, s>>>(mV, mU, j, woff, st, reinterpret_cast<T *>(partial), ntiles, final_step, m); break;
     PSP_DOTS(1) PSP_DOTS(2) PSP_DOTS(3) PSP_DOTS(4) PSP_DOTS(5)
 #undef PSP_DOTS
     default: break;
@@ -724,8 +885,17 @@ void launch_arnoldi(int j, int final_step, int64_t n, const ArnoldiMaps &maps, T
     const int64_t nv = (ldv + Vec<T>::W - 1) / Vec<T>::W;
     int ugrid = final_step ? 0 : (int)std::min<int64_t>((nv + kUpdThreads - 1) / kUpdThreads, (int64_t)arnoldi_grid() * 4);
     if (!final_step && ugrid < 1) ugrid = 1;
-    k_dcgs_update<T><<<ugrid + 1, kUpdThreads, kGivensDoubles * sizeof(double), s>>>(V, ldv, Py, ldh, j, woff, st, nv,
-                                                                                     final_step, mixed);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(ugrid + 1));
+    cfg.blockDim = dim3(kUpdThreads);
+    cfg.dynamicSmemBytes = kGivensDoubles * sizeof(double);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_dcgs_update<T>, V, ldv, Py, ldh, j, woff, st, nv, final_step, mixed);
   }
   if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);
 }
@@ -785,9 +955,16 @@ void launch_update_z(int64_t n, const T *V, int64_t ldv, T *Z, double *X, int ad
 }
 
 template void launch_arnoldi<float>(int, int, int64_t, const ArnoldiMaps &, float *, int64_t, const float *, int64_t,
-                                    DevState *, double *, int, cudaStream_t, cudaEvent_t *);
+                                    DevState *, double *, int, cudaStream_t, cudaEvent_t *, const TileMatvec<float> *);
 template void launch_arnoldi<double>(int, int, int64_t, const ArnoldiMaps &, double *, int64_t, const double *,
-                                     int64_t, DevState *, double *, int, cudaStream_t, cudaEvent_t *);
+                                     int64_t, DevState *, double *, int, cudaStream_t, cudaEvent_t *,
+                                     const TileMatvec<double> *);
+
+bool fused_matvec_ok(const Geometry &g, int elem_bytes) {
+  const int W = 16 / elem_bytes;
+  const int nh = (g.R + W - 1) / W;
+  return g.R >= 1 && g.R <= kMaxR && g.ndim >= 1 && g.ndim <= 3 && g.nx % W == 0 && g.nx / W > nh;
+}
 template void launch_scale_copy<float>(int, int64_t, const float *, int64_t, OutRef<float>, const DevState *,
                                        cudaStream_t);
 template void launch_scale_copy<double>(int, int64_t, const double *, int64_t, OutRef<double>,

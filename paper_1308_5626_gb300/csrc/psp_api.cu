@@ -94,6 +94,7 @@ struct psp_ctx {
   int order = 0, b = 0, m = 0;
   psp_opts opts{};
   bool mixed = false;
+  bool fused = false;                // matvec folded into the first Gram-Schmidt pass
   cudaStream_t stream = nullptr;     // caller's stream
   cudaStream_t cap = nullptr;        // internal capture stream
   int64_t ld = 0;                    // leading dimension of every n-vector column
@@ -160,24 +161,29 @@ void enqueue_cycle(psp_ctx *h, int slot, cudaStream_t s) {
   const int which = slot + 1;
   // iteration j: Y_j = N^{-1} v_j -> P_x ring column hist_base+1+j, w_j = A Y_j -> P_y column,
   // then the DCGS2 passes (orthogonalise, complete column j-1, Givens, finish test)
+  const bool fused = h->fused;
   for (int j = 0; j < h->m; ++j) {
     // profiling samples one iteration in kProfileEvery
     cudaEvent_t *ev = (h->profiling && j % kProfileEvery == 0) ? h->ev[which][j] : nullptr;
     OutRef<T> pxcol = ring_out<T>(Px, h->ld, &h->st->hist_base, h->mmax, 1 + j);
     OutRef<T> pycol = ring_out<T>(Py, h->ld, &h->st->hist_base, h->mmax, 1 + j);
     if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
+    TileMatvec<T> mv{};
     if (slot < 0) {
-      // N = I: one kernel writes P_x(:,i) = v_j and P_y(:,i) = A v_j
+      // N = I: P_x(:,i) = v_j and P_y(:,i) = A v_j
       if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
-      launch_stencil<T, T, T>(g, fixed_in<T>(V + (int64_t)j * h->ld), pycol, h->st, active, s, pxcol, nullptr);
+      if (fused) mv = TileMatvec<T>{fixed_in<T>(V + (int64_t)j * h->ld), pycol, pxcol, g.nx, g.ny, g.nz, g.ndim, g.R};
+      else launch_stencil<T, T, T>(g, fixed_in<T>(V + (int64_t)j * h->ld), pycol, h->st, active, s, pxcol, nullptr);
     } else {
       h->bs.apply<T>(slot, V + (int64_t)j * h->ld, nullptr, active, pxcol, nullptr, 0, s);
       if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
-      launch_stencil<T, T, T>(g, ring_in<T>(Px, h->ld, &h->st->hist_base, h->mmax, 1 + j), pycol, h->st, active, s);
+      InRef<T> xin = ring_in<T>(Px, h->ld, &h->st->hist_base, h->mmax, 1 + j);
+      if (fused) mv = TileMatvec<T>{xin, pycol, OutRef<T>{nullptr, 0, nullptr, 1, 0}, g.nx, g.ny, g.nz, g.ndim, g.R};
+      else launch_stencil<T, T, T>(g, xin, pycol, h->st, active, s);
     }
     if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);
     launch_arnoldi<T>(j, 0, g.n, h->maps, V, h->ld, Py, h->ld, h->st, h->partial, h->mixed ? 1 : 0, s,
-                      ev ? ev + 3 : nullptr);
+                      ev ? ev + 3 : nullptr, fused ? &mv : nullptr);
   }
   // reduction-only step completing column m-1 when the cycle runs to m columns
   launch_arnoldi<T>(h->m, 1, g.n, h->maps, V, h->ld, Py, h->ld, h->st, h->partial, h->mixed ? 1 : 0, s, nullptr);
@@ -260,12 +266,15 @@ void accumulate_profile(psp_ctx *h, int which, int k_end) {
         ms[c] = 0.0f;
         cudaGetLastError();   // a failed query must not surface as a later launch error
       }
-    // N = I: the fused stencil reads V(:,k) and writes P_x and P_y columns (class 1;
-    // class 0 is then empty)
-    // DCGS2 at iteration j = k-1: pass A reads V(:,0..j) and w_j (k+1 vectors), pass B
-    // reads the same and writes q_j and v_{j+1} (class 3, the former second pass, is empty)
-    const double bytes[5] = {(which == 0 ? 0.0 : (2.0 * h->b + 3.0)) * s * n, (which == 0 ? 3.0 : 2.0) * s * n,
-                             (k + 1.0) * s * n, 0.0, (k + 3.0) * s * n};
+    // N = I: the stencil reads V(:,k) and writes the P_x and P_y columns (class 1; class 0
+    // is then empty).  DCGS2 at iteration j = k-1: pass A reads V(:,0..j) and w_j (k+1
+    // vectors), pass B reads the same and writes q_j and v_{j+1} (class 3 is empty).  With
+    // the matvec folded into pass A, class 1 is empty and pass A moves V(:,0..j) and the
+    // matvec's input in, w_j (and the P_x copy) out: k+2 vectors.
+    const double st_bytes = h->fused ? 0.0 : (which == 0 ? 3.0 : 2.0) * s * n;
+    const double dots_bytes = (h->fused ? k + 2.0 : k + 1.0) * s * n;
+    const double bytes[5] = {(which == 0 ? 0.0 : (2.0 * h->b + 3.0)) * s * n, st_bytes, dots_bytes, 0.0,
+                             (k + 3.0) * s * n};
     for (int c = 0; c < 5; ++c) {
       if (bytes[c] == 0.0) continue;
       h->prof.ms[c] += ms[c];
@@ -294,6 +303,7 @@ psp_status psp_default_opts(psp_opts *o) {
   o->max_hist_cols = 0;
   o->inner_tol = 1e-5;
   o->accept_rule = 1;
+  o->fuse_matvec = 1;
   return PSP_OK;
 }
 
@@ -375,6 +385,7 @@ psp_status psp_create(const psp_grid *grid, int order, const psp_term *terms, in
   h->geo.nz = (int)nn[2];
   h->geo.n = n;
   h->geo.R = R;
+  h->fused = o.fuse_matvec != 0 && fused_matvec_ok(h->geo, h->mixed ? 4 : 8);
   h->ld = round_up(n, 512);   // whole 1 KB tiles of the Gram-Schmidt pipeline (FP32 and FP64)
   h->mmax = o.max_hist_cols > 0 ? o.max_hist_cols : 2 * (m + 1);
   if (h->mmax < m + 1) h->mmax = m + 1;

@@ -55,6 +55,15 @@ inline OutRef<T> ring_out(T *base, int64_t ld, const int *counter, int mmax, int
 
 int reduce_grid(int64_t n);
 
+// Matvec folded into the first Gram-Schmidt pass (see launch_arnoldi).
+template <typename T>
+struct TileMatvec {
+  InRef<T> x;          // input; x.base == nullptr: no matvec in the pass
+  OutRef<T> w;         // w = A x (P_y ring column)
+  OutRef<T> xcopy;     // copy of x (P_x ring column of an unpreconditioned cycle) or base nullptr
+  int nx, ny, nz, ndim, R;
+};
+
 // stencil.cu
 template <typename TI, typename TO, typename TC>
 void launch_stencil(const Geometry &g, InRef<TI> x, OutRef<TO> y, const DevState *st, const int *active,
@@ -78,10 +87,17 @@ bool encode_arnoldi_maps(ArnoldiMaps &maps, const T *V, int ncols, const T *Py, 
 
 // DCGS2 step of iteration j (0-based) of a cycle: pass A (dots) and pass B (update).  With
 // final_step, pass B only completes column j-1 (no matvec was made at this j).  If
-// ev != nullptr, ev[0..2] are recorded after pass A, (nothing), pass B (profiling).
+// ev != nullptr, ev[0..2] are recorded after pass A, (nothing), pass B (profiling).  With
+// mv, pass A also makes the iteration's matvec w_j = A x into mv->w (and the copy of x
+// into mv->xcopy) on its own tiles before it reads w_j back; mv is only valid when
+// fused_matvec_ok(geometry) holds.
 template <typename T>
 void launch_arnoldi(int j, int final_step, int64_t n, const ArnoldiMaps &maps, T *V, int64_t ldv, const T *Py,
-                    int64_t ldh, DevState *st, double *partial, int mixed, cudaStream_t s, cudaEvent_t *ev = nullptr);
+                    int64_t ldh, DevState *st, double *partial, int mixed, cudaStream_t s, cudaEvent_t *ev = nullptr,
+                    const TileMatvec<T> *mv = nullptr);
+// The folded matvec handles the geometry: x rows of whole 16-byte vectors (elem bytes each)
+// with more vectors per row than stencil halo vectors.
+bool fused_matvec_ok(const Geometry &g, int elem_bytes);
 template <typename T>
 void launch_scale_copy(int k, int64_t n, const T *V, int64_t ldv, OutRef<T> y, const DevState *st,
                        cudaStream_t s);

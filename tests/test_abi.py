@@ -46,6 +46,7 @@ def test_default_opts_without_gpu(libpsp):
     o = psp.psp_default_opts()
     assert o.precision == psp.PSP_FP64 and o.intercept == 1 and o.max_restarts == 200
     assert o.accept_rule == 1 and abs(o.inner_tol - 1e-5) < 1e-20
+    assert o.fuse_matvec == 1
 
 
 def test_argument_errors_need_no_gpu(libpsp):

@@ -76,6 +76,30 @@ def test_mixed_steps_match_exact(dev, w):
     s.close()
 
 
+@pytest.mark.parametrize("fuse", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("w", [inputs.c2(48, 40), inputs.c2(45, 40), inputs.c1(998)], ids=lambda w: w.name)
+def test_matvec_placement(dev, w, precision, fuse):
+    """The Arnoldi matvec made inside the first Gram-Schmidt pass (fuse_matvec = 1, rows of
+    whole 16-byte vectors) or by its own kernel (fuse_matvec = 0, and always for rows that
+    are not: nx = 45, and nx = 998 in FP32): the steps match the exact solve either way."""
+    op = Operator(w.shape, w.order, w.terms)
+    dt = _dt(w, op)
+    tol = 1e-12 if precision == 0 else 1e-10
+    bound = exact.condition_number(op, dt) * 2 * tol if precision == 0 else 1e-8
+    s = _solver(w, precision=precision, fuse_matvec=fuse)
+    u = t64(w.u0, dev)
+    un = w.u0
+    for step in range(3):
+        u, info = s.step(u, dt, tol)
+        ref = exact.solve_fourier(op, un, dt)
+        got = u.cpu().numpy()
+        assert info.status == 0
+        assert rel(got, ref) <= bound, (step, rel(got, ref), info.iters)
+        un = got
+    s.close()
+
+
 @pytest.mark.parametrize("w", [inputs.c1(1000), inputs.c3(12, kmax=3)], ids=lambda w: w.name)
 def test_iterations_follow_the_oracle(dev, w):
     from paper_1308_5626_gb300 import psp
