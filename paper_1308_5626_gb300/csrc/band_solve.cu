@@ -322,24 +322,43 @@ __global__ void k_assemble(LevelInput in, int q, int G, LevelF64 f, double *nLo,
 // apply
 // ---------------------------------------------------------------------------------------
 
-template <typename T, int B>
+// Factor blocks are read-only during an apply: in global memory (RO) they are read
+// through the read-only path, so the loads may be issued ahead of the recurrence that
+// consumes them; in the shared-memory tail they are plain loads.
+template <bool RO, typename T>
+__device__ __forceinline__ T ldf(const T *p) {
+  if constexpr (RO) return __ldg(p);
+  else return *p;
+}
+
+template <typename T, int B, bool RO>
 __device__ __forceinline__ void mv_sub(T (&y)[B], const T *M, int i, int G, int g, const T (&x)[B]) {
+  T m[B][B];
+#pragma unroll
+  for (int r = 0; r < B; ++r)
+#pragma unroll
+    for (int c = 0; c < B; ++c) m[r][c] = ldf<RO>(M + gi(i, r * B + c, G, g, B * B));
 #pragma unroll
   for (int r = 0; r < B; ++r) {
     T s = y[r];
 #pragma unroll
-    for (int c = 0; c < B; ++c) s -= M[gi(i, r * B + c, G, g, B * B)] * x[c];
+    for (int c = 0; c < B; ++c) s -= m[r][c] * x[c];
     y[r] = s;
   }
 }
 
-template <typename T, int B>
+template <typename T, int B, bool RO>
 __device__ __forceinline__ void mv(T (&y)[B], const T *M, int i, int G, int g, const T (&x)[B]) {
+  T m[B][B];
+#pragma unroll
+  for (int r = 0; r < B; ++r)
+#pragma unroll
+    for (int c = 0; c < B; ++c) m[r][c] = ldf<RO>(M + gi(i, r * B + c, G, g, B * B));
 #pragma unroll
   for (int r = 0; r < B; ++r) {
     T s = (T)0;
 #pragma unroll
-    for (int c = 0; c < B; ++c) s += M[gi(i, r * B + c, G, g, B * B)] * x[c];
+    for (int c = 0; c < B; ++c) s += m[r][c] * x[c];
     y[r] = s;
   }
 }
@@ -347,14 +366,14 @@ __device__ __forceinline__ void mv(T (&y)[B], const T *M, int i, int G, int g, c
 // Down sweep of group g.  `rhs(i, r)` is a reference to the right-hand side of interior
 // block i (i < q) or of the separator block (i == q); the forward sweep overwrites it with
 // y.  The back substitution writes p to L.p (group-interleaved).
-template <typename T, int B, typename Acc>
+template <typename T, int B, bool RO, typename Acc>
 __device__ __forceinline__ void down_group(const LevelApply<T> &L, int g, Acc rhs) {
   const int q = L.q, G = L.G;
   T y[B], yp[B];
   for (int i = 0; i < q; ++i) {
 #pragma unroll
     for (int r = 0; r < B; ++r) y[r] = rhs(i, r);
-    if (i > 0) mv_sub<T, B>(y, L.Mul, i, G, g, yp);
+    if (i > 0) mv_sub<T, B, RO>(y, L.Mul, i, G, g, yp);
 #pragma unroll
     for (int r = 0; r < B; ++r) { rhs(i, r) = y[r]; yp[r] = y[r]; }
   }
@@ -362,8 +381,8 @@ __device__ __forceinline__ void down_group(const LevelApply<T> &L, int g, Acc rh
   for (int i = q - 1; i >= 0; --i) {
 #pragma unroll
     for (int r = 0; r < B; ++r) y[r] = rhs(i, r);
-    if (i < q - 1) mv_sub<T, B>(y, L.Up, i, G, g, xn);
-    mv<T, B>(x, L.Minv, i, G, g, y);
+    if (i < q - 1) mv_sub<T, B, RO>(y, L.Up, i, G, g, xn);
+    mv<T, B, RO>(x, L.Minv, i, G, g, y);
 #pragma unroll
     for (int r = 0; r < B; ++r) {
       L.p[gi(i, r, G, g, B)] = x[r];
@@ -375,13 +394,13 @@ __device__ __forceinline__ void down_group(const LevelApply<T> &L, int g, Acc rh
   if (G > 1) {
     if (g < G - 1) {
       T c[B];
-      mv<T, B>(c, L.LoSep, 0, G, g, xl);
+      mv<T, B, RO>(c, L.LoSep, 0, G, g, xl);
 #pragma unroll
       for (int r = 0; r < B; ++r) { L.cR[g * B + r] = -c[r]; L.seprhs[g * B + r] = rhs(q, r); }
     }
     if (g > 0) {
       T c[B];
-      mv<T, B>(c, L.UpSepPrev, 0, G, g, x0);
+      mv<T, B, RO>(c, L.UpSepPrev, 0, G, g, x0);
 #pragma unroll
       for (int r = 0; r < B; ++r) L.cL[g * B + r] = -c[r];
     }
@@ -390,7 +409,7 @@ __device__ __forceinline__ void down_group(const LevelApply<T> &L, int g, Acc rh
 
 // Up sweep of group g: x_i = p_i - W_i sl - V_i sr; out(i, r) receives interior block i
 // (i < q) and the separator block (i == q, only for g < G-1).
-template <typename T, int B, typename Out>
+template <typename T, int B, bool RO, typename Out>
 __device__ __forceinline__ void up_group(const LevelApply<T> &L, int g, const T *solnext, Out out) {
   const int q = L.q, G = L.G;
   T sl[B], sr[B];
@@ -404,8 +423,8 @@ __device__ __forceinline__ void up_group(const LevelApply<T> &L, int g, const T 
 #pragma unroll
     for (int r = 0; r < B; ++r) x[r] = L.p[gi(i, r, G, g, B)];
     if (G > 1) {
-      mv_sub<T, B>(x, L.W, i, G, g, sl);
-      mv_sub<T, B>(x, L.Vs, i, G, g, sr);
+      mv_sub<T, B, RO>(x, L.W, i, G, g, sl);
+      mv_sub<T, B, RO>(x, L.Vs, i, G, g, sr);
     }
 #pragma unroll
     for (int r = 0; r < B; ++r) out(i, r, x[r]);
@@ -418,7 +437,7 @@ __device__ __forceinline__ void up_group(const LevelApply<T> &L, int g, const T 
 
 // Level >= 1 down: right-hand side of block j = prev.seprhs[j] + prev.cR[j] + prev.cL[j+1],
 // staged in L.p and swept in place.
-template <typename T, int B>
+template <typename T, int B, bool RO>
 __device__ __forceinline__ void down_level_group(const LevelApply<T> &L, const LevelApply<T> &P, int g) {
   const int q = L.q, G = L.G;
   // stage: p slots 0..q-1 hold the interior rhs; the separator rhs is computed on demand
@@ -437,10 +456,10 @@ __device__ __forceinline__ void down_level_group(const LevelApply<T> &L, const L
   }
   T *p = L.p;
   auto acc = [&](int i, int r) -> T & { return i < q ? p[gi(i, r, G, g, B)] : sep[r]; };
-  down_group<T, B>(L, g, acc);
+  down_group<T, B, RO>(L, g, acc);
 }
 
-template <typename T, int B>
+template <typename T, int B, bool RO>
 __device__ __forceinline__ void up_level_group(const LevelApply<T> &L, const T *solnext, int g) {
   const int q = L.q;
   T *sol = L.sol;
@@ -449,11 +468,14 @@ __device__ __forceinline__ void up_level_group(const LevelApply<T> &L, const T *
     const int j = g * (q + 1) + i;
     if (j < nb) sol[j * B + r] = v;
   };
-  up_group<T, B>(L, g, solnext, out);
+  up_group<T, B, RO>(L, g, solnext, out);
 }
 
-constexpr int kQ0 = 16;          // interior blocks per group on level 0
+constexpr int kQ0 = 8;           // interior blocks per group on level 0
+constexpr int kQ = 4;            // ... on the levels above
 constexpr int kGroupsPerCta = 64;
+constexpr int kMaxLevels = 24;
+constexpr int kTailSmem = 200 * 1024;   // shared memory of the single-CTA top levels
 
 // Level 0 down: stage the CTA's rows of v (times *scale) in shared memory, one group per thread.
 template <typename T, int B>
@@ -475,7 +497,7 @@ __global__ void __launch_bounds__(kGroupsPerCta) k_down0(const T *__restrict__ v
   if (g < L.G) {
     T *mine = tile + threadIdx.x * PITCH;
     auto acc = [&](int i, int r) -> T & { return mine[i * B + r]; };
-    down_group<T, B>(L, g, acc);
+    down_group<T, B, true>(L, g, acc);
   }
 }
 
@@ -493,7 +515,7 @@ __global__ void __launch_bounds__(kGroupsPerCta) k_up0(const int *active, LevelA
   if (g < L.G) {
     T *mine = tile + threadIdx.x * PITCH;
     auto out = [&](int i, int r, T v) { mine[i * B + r] = v; };
-    up_group<T, B>(L, g, solnext, out);
+    up_group<T, B, true>(L, g, solnext, out);
   }
   __syncthreads();
   const int64_t row0 = (int64_t)g0 * SPAN;
@@ -512,32 +534,70 @@ template <typename T, int B>
 __global__ void k_down_level(const int *active, LevelApply<T> L, LevelApply<T> P) {
   if (active && *active == 0) return;
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g < L.G) down_level_group<T, B>(L, P, g);
+  if (g < L.G) down_level_group<T, B, true>(L, P, g);
 }
 
 template <typename T, int B>
 __global__ void k_up_level(const int *active, LevelApply<T> L, const T *solnext) {
   if (active && *active == 0) return;
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g < L.G) up_level_group<T, B>(L, solnext, g);
+  if (g < L.G) up_level_group<T, B, true>(L, solnext, g);
 }
 
-// Levels first..last (last = top, one group) in one CTA: down sweeps, then up sweeps.
+// Levels first..last (last = top, one group) in one CTA: their factors and vectors are
+// copied to shared memory, then the down sweeps and the up sweeps run there.  Level
+// first reads the separator vectors of level first-1 and writes its solution to global
+// memory (the up sweep of level first-1 reads it).
+template <typename T>
+__device__ __forceinline__ void stage(T *&cursor, const T *&dst_ptr, size_t count) {
+  T *d = cursor;
+  for (size_t e = threadIdx.x; e < count; e += blockDim.x) d[e] = dst_ptr[e];
+  dst_ptr = d;
+  cursor += (count + 1) & ~size_t(1);
+}
+template <typename T>
+__device__ __forceinline__ T *carve_s(T *&cursor, size_t count) {
+  T *d = cursor;
+  cursor += (count + 1) & ~size_t(1);
+  return d;
+}
+
 template <typename T, int B>
 __global__ void __launch_bounds__(512) k_tail(const int *active, const LevelApply<T> *lv, int first, int last) {
   if (active && *active == 0) return;
+  extern __shared__ __align__(16) unsigned char tail_smem[];
+  __shared__ LevelApply<T> S[kMaxLevels];
+  if (last - first + 1 > kMaxLevels) return;
+  constexpr int BB = B * B;
+  T *cur = reinterpret_cast<T *>(tail_smem);
   for (int l = first; l <= last; ++l) {
-    const LevelApply<T> L = lv[l];
-    const LevelApply<T> P = lv[l - 1];
-    for (int g = threadIdx.x; g < L.G; g += blockDim.x) down_level_group<T, B>(L, P, g);
-    __threadfence_block();
+    LevelApply<T> L = lv[l];
+    const size_t gq = (size_t)L.G * L.q * BB, gs = (size_t)L.G * BB;
+    stage(cur, L.Mul, gq);
+    stage(cur, L.Minv, gq);
+    stage(cur, L.Up, gq);
+    stage(cur, L.W, gq);
+    stage(cur, L.Vs, gq);
+    stage(cur, L.LoSep, gs);
+    stage(cur, L.UpSepPrev, gs);
+    L.p = carve_s(cur, (size_t)L.G * L.q * B);
+    L.cR = carve_s(cur, (size_t)L.G * B + 64);
+    L.cL = carve_s(cur, (size_t)L.G * B + 64);
+    L.seprhs = carve_s(cur, (size_t)L.G * B + 64);
+    if (l > first) L.sol = carve_s(cur, (size_t)(L.nb + 1) * B);
+    if (threadIdx.x == 0) S[l - first] = L;
+  }
+  __syncthreads();
+  for (int l = first; l <= last; ++l) {
+    const LevelApply<T> L = S[l - first];
+    const LevelApply<T> P = (l == first) ? lv[l - 1] : S[l - 1 - first];
+    for (int g = threadIdx.x; g < L.G; g += blockDim.x) down_level_group<T, B, false>(L, P, g);
     __syncthreads();
   }
   for (int l = last; l >= first; --l) {
-    const LevelApply<T> L = lv[l];
-    const T *solnext = (l < last) ? lv[l + 1].sol : nullptr;
-    for (int g = threadIdx.x; g < L.G; g += blockDim.x) up_level_group<T, B>(L, solnext, g);
-    __threadfence_block();
+    const LevelApply<T> L = S[l - first];
+    const T *solnext = (l < last) ? S[l + 1 - first].sol : nullptr;
+    for (int g = threadIdx.x; g < L.G; g += blockDim.x) up_level_group<T, B, false>(L, solnext, g);
     __syncthreads();
   }
 }
@@ -560,12 +620,30 @@ void BandSolver::plan(int64_t n_, int b_) {
     levels.push_back(s);
     if (s.G == 1) break;
     nb = s.G - 1;
-    q = 32;
+    q = kQ;
   }
-  // levels whose block count is small run in the single-CTA tail
+  // the top levels run in one CTA with their factors and vectors in shared memory: as
+  // many levels (at least the top one, never level 0) as fit in kTailSmem in FP64
   tail_first = (int)levels.size() - 1;
-  while (tail_first > 1 && levels[tail_first - 1].nb <= 2048) --tail_first;
+  while (tail_first > 1 && tail_smem_bytes(tail_first - 1, (int)levels.size() - 1, 8) <= kTailSmem) --tail_first;
   if (levels.size() == 1) tail_first = 1;  // no tail: level 0 is the top
+}
+
+// Shared memory of the tail kernel for levels first..last in elements of `es` bytes: the
+// factor blocks, p, the separator vectors and (above `first`) the solution of each level,
+// every array rounded up to an even element count exactly as k_tail carves them.
+size_t BandSolver::tail_smem_bytes(int first, int last, int es) const {
+  auto ev = [](size_t c) { return (c + 1) & ~size_t(1); };
+  size_t e = 0;
+  const int BB = b * b;
+  for (int l = first; l <= last; ++l) {
+    const LevelShape &s = levels[l];
+    const size_t gq = (size_t)s.G * s.q * BB, gs = (size_t)s.G * BB;
+    e += 5 * ev(gq) + 2 * ev(gs);                           // Mul Minv Up W Vs, LoSep UpSepPrev
+    e += ev((size_t)s.G * s.q * b) + 3 * ev((size_t)s.G * b + 64);   // p, cR cL seprhs
+    if (l > first) e += ev((size_t)(s.nb + 1) * b);         // sol
+  }
+  return e * es;
 }
 
 template <typename T>
@@ -661,6 +739,15 @@ void BandSolver::bind_apply(void *mem) {
   const std::vector<LevelF32> f32[2] = {slots[0].h, slots[1].h};
   bind_apply_t<double>(levels, b, p, f64, app64, dev_app64);
   bind_apply_t<float>(levels, b, p, f32, app32, dev_app32);
+  static bool attrs = false;
+  if (!attrs) {
+    attrs = true;
+#define PSP_TAIL_ATTR(T_, B_) \
+  cudaFuncSetAttribute(k_tail<T_, B_>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTailSmem + 1024);
+    PSP_TAIL_ATTR(float, 1) PSP_TAIL_ATTR(float, 2) PSP_TAIL_ATTR(float, 3) PSP_TAIL_ATTR(float, 4)
+    PSP_TAIL_ATTR(double, 1) PSP_TAIL_ATTR(double, 2) PSP_TAIL_ATTR(double, 3) PSP_TAIL_ATTR(double, 4)
+#undef PSP_TAIL_ATTR
+  }
 }
 
 template <int B>
@@ -703,7 +790,7 @@ static void apply_b(const BandSolver &bs, const std::vector<LevelApply<T>> &a, c
   const int tf = bs.tail_first;
   for (int l = 1; l < tf && l < L; ++l)
     k_down_level<T, B><<<(a[l].G + 63) / 64, 64, 0, s>>>(active, a[l], a[l - 1]);
-  if (L > 1) k_tail<T, B><<<1, 512, 0, s>>>(active, dev, tf, L - 1);
+  if (L > 1) k_tail<T, B><<<1, 512, bs.tail_smem_bytes(tf, L - 1, sizeof(T)), s>>>(active, dev, tf, L - 1);
   for (int l = std::min(tf, L) - 1; l >= 1; --l)
     k_up_level<T, B><<<(a[l].G + 63) / 64, 64, 0, s>>>(active, a[l], a[l + 1].sol);
   k_up0<T, B><<<g0, kGroupsPerCta, 0, s>>>(active, a[0], L > 1 ? a[1].sol : nullptr, y, X, mode, bs.n);

@@ -47,6 +47,8 @@ struct BandSolver {
   LevelApply<float> *dev_app32[2] = {nullptr, nullptr};
 
   void plan(int64_t n, int b);
+  // shared memory of the single-CTA kernel for levels first..last, elements of es bytes
+  size_t tail_smem_bytes(int first, int last, int es) const;
   size_t slot_bytes() const;     // factor storage of one slot
   size_t apply_bytes() const;    // shared apply scratch + per-slot descriptors
   void bind(void *slot_mem, int slot);
