@@ -363,62 +363,57 @@ __device__ __forceinline__ void mv(T (&y)[B], const T *M, int i, int G, int g, c
   }
 }
 
-// Down sweep of group g.  `rhs(i, r)` is a reference to the right-hand side of interior
-// block i (i < q) or of the separator block (i == q); the forward sweep overwrites it with
-// y.  The back substitution writes p to L.p (group-interleaved).
-template <typename T, int B, bool RO, typename Acc>
-__device__ __forceinline__ void down_group(const LevelApply<T> &L, int g, Acc rhs) {
-  const int q = L.q, G = L.G;
-  T y[B], yp[B];
-  for (int i = 0; i < q; ++i) {
+// Down sweep of group g (Q interior blocks, the level's q), all in registers: f holds the
+// right-hand sides of the interior blocks and sep that of the separator block.  Forward
+// elimination y_i = f_i - Mul_i y_{i-1}, back substitution x_i = Minv_i (y_i - Up_i x_{i+1})
+// (both in place in f); p = x goes to L.p (group-interleaved), and the separator terms of
+// the next level to cR, cL and seprhs.
+template <typename T, int B, int Q, bool RO>
+__device__ __forceinline__ void down_group(const LevelApply<T> &L, int g, T (&f)[Q][B], const T (&sep)[B]) {
+  const int G = L.G;
 #pragma unroll
-    for (int r = 0; r < B; ++r) y[r] = rhs(i, r);
-    if (i > 0) mv_sub<T, B, RO>(y, L.Mul, i, G, g, yp);
+  for (int i = 1; i < Q; ++i) mv_sub<T, B, RO>(f[i], L.Mul, i, G, g, f[i - 1]);
 #pragma unroll
-    for (int r = 0; r < B; ++r) { rhs(i, r) = y[r]; yp[r] = y[r]; }
+  for (int i = Q - 1; i >= 0; --i) {
+    if (i < Q - 1) mv_sub<T, B, RO>(f[i], L.Up, i, G, g, f[i + 1]);
+    T x[B];
+    mv<T, B, RO>(x, L.Minv, i, G, g, f[i]);
+#pragma unroll
+    for (int r = 0; r < B; ++r) f[i][r] = x[r];
   }
-  T x[B], xn[B], x0[B], xl[B];
-  for (int i = q - 1; i >= 0; --i) {
 #pragma unroll
-    for (int r = 0; r < B; ++r) y[r] = rhs(i, r);
-    if (i < q - 1) mv_sub<T, B, RO>(y, L.Up, i, G, g, xn);
-    mv<T, B, RO>(x, L.Minv, i, G, g, y);
+  for (int i = 0; i < Q; ++i)
 #pragma unroll
-    for (int r = 0; r < B; ++r) {
-      L.p[gi(i, r, G, g, B)] = x[r];
-      xn[r] = x[r];
-      if (i == q - 1) xl[r] = x[r];
-      if (i == 0) x0[r] = x[r];
-    }
-  }
+    for (int r = 0; r < B; ++r) L.p[gi(i, r, G, g, B)] = f[i][r];
   if (G > 1) {
     if (g < G - 1) {
       T c[B];
-      mv<T, B, RO>(c, L.LoSep, 0, G, g, xl);
+      mv<T, B, RO>(c, L.LoSep, 0, G, g, f[Q - 1]);
 #pragma unroll
-      for (int r = 0; r < B; ++r) { L.cR[g * B + r] = -c[r]; L.seprhs[g * B + r] = rhs(q, r); }
+      for (int r = 0; r < B; ++r) { L.cR[g * B + r] = -c[r]; L.seprhs[g * B + r] = sep[r]; }
     }
     if (g > 0) {
       T c[B];
-      mv<T, B, RO>(c, L.UpSepPrev, 0, G, g, x0);
+      mv<T, B, RO>(c, L.UpSepPrev, 0, G, g, f[0]);
 #pragma unroll
       for (int r = 0; r < B; ++r) L.cL[g * B + r] = -c[r];
     }
   }
 }
 
-// Up sweep of group g: x_i = p_i - W_i sl - V_i sr; out(i, r) receives interior block i
-// (i < q) and the separator block (i == q, only for g < G-1).
-template <typename T, int B, bool RO, typename Out>
+// Up sweep of group g: x_i = p_i - W_i sl - V_i sr (independent blocks); out(i, r)
+// receives interior block i (i < Q) and the separator block (i == Q, only for g < G-1).
+template <typename T, int B, int Q, bool RO, typename Out>
 __device__ __forceinline__ void up_group(const LevelApply<T> &L, int g, const T *solnext, Out out) {
-  const int q = L.q, G = L.G;
+  const int G = L.G;
   T sl[B], sr[B];
 #pragma unroll
   for (int r = 0; r < B; ++r) {
     sl[r] = (g > 0) ? solnext[(g - 1) * B + r] : (T)0;
     sr[r] = (g < G - 1) ? solnext[g * B + r] : (T)0;
   }
-  for (int i = 0; i < q; ++i) {
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
     T x[B];
 #pragma unroll
     for (int r = 0; r < B; ++r) x[r] = L.p[gi(i, r, G, g, B)];
@@ -431,48 +426,43 @@ __device__ __forceinline__ void up_group(const LevelApply<T> &L, int g, const T 
   }
   if (g < G - 1) {
 #pragma unroll
-    for (int r = 0; r < B; ++r) out(q, r, sr[r]);
+    for (int r = 0; r < B; ++r) out(Q, r, sr[r]);
   }
-}
-
-// Level >= 1 down: right-hand side of block j = prev.seprhs[j] + prev.cR[j] + prev.cL[j+1],
-// staged in L.p and swept in place.
-template <typename T, int B, bool RO>
-__device__ __forceinline__ void down_level_group(const LevelApply<T> &L, const LevelApply<T> &P, int g) {
-  const int q = L.q, G = L.G;
-  // stage: p slots 0..q-1 hold the interior rhs; the separator rhs is computed on demand
-  for (int i = 0; i < q; ++i) {
-    const int j = g * (q + 1) + i;
-#pragma unroll
-    for (int r = 0; r < B; ++r)
-      L.p[gi(i, r, G, g, B)] = (j < L.nb) ? P.seprhs[j * B + r] + P.cR[j * B + r] + P.cL[(j + 1) * B + r] : (T)0;
-  }
-  T sep[B];
-  {
-    const int j = g * (q + 1) + q;
-#pragma unroll
-    for (int r = 0; r < B; ++r)
-      sep[r] = (g < G - 1) ? P.seprhs[j * B + r] + P.cR[j * B + r] + P.cL[(j + 1) * B + r] : (T)0;
-  }
-  T *p = L.p;
-  auto acc = [&](int i, int r) -> T & { return i < q ? p[gi(i, r, G, g, B)] : sep[r]; };
-  down_group<T, B, RO>(L, g, acc);
-}
-
-template <typename T, int B, bool RO>
-__device__ __forceinline__ void up_level_group(const LevelApply<T> &L, const T *solnext, int g) {
-  const int q = L.q;
-  T *sol = L.sol;
-  const int nb = L.nb;
-  auto out = [&](int i, int r, T v) {
-    const int j = g * (q + 1) + i;
-    if (j < nb) sol[j * B + r] = v;
-  };
-  up_group<T, B, RO>(L, g, solnext, out);
 }
 
 constexpr int kQ0 = 8;           // interior blocks per group on level 0
 constexpr int kQ = 4;            // ... on the levels above
+
+// Level >= 1 down: right-hand side of block j = prev.seprhs[j] + prev.cR[j] + prev.cL[j+1].
+template <typename T, int B, bool RO>
+__device__ __forceinline__ void down_level_group(const LevelApply<T> &L, const LevelApply<T> &P, int g) {
+  const int G = L.G;
+  T f[kQ][B], sep[B];
+#pragma unroll
+  for (int i = 0; i <= kQ; ++i) {
+    const int j = g * (kQ + 1) + i;
+    const bool real = (i < kQ) ? (j < L.nb) : (g < G - 1);
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+      const T v = real ? P.seprhs[j * B + r] + P.cR[j * B + r] + P.cL[(j + 1) * B + r] : (T)0;
+      if (i < kQ) f[i][r] = v;
+      else sep[r] = v;
+    }
+  }
+  down_group<T, B, kQ, RO>(L, g, f, sep);
+}
+
+template <typename T, int B, bool RO>
+__device__ __forceinline__ void up_level_group(const LevelApply<T> &L, const T *solnext, int g) {
+  T *sol = L.sol;
+  const int nb = L.nb;
+  auto out = [&](int i, int r, T v) {
+    const int j = g * (kQ + 1) + i;
+    if (j < nb) sol[j * B + r] = v;
+  };
+  up_group<T, B, kQ, RO>(L, g, solnext, out);
+}
+
 constexpr int kGroupsPerCta = 64;
 constexpr int kMaxLevels = 24;
 constexpr int kTailSmem = 200 * 1024;   // shared memory of the single-CTA top levels
@@ -495,9 +485,15 @@ __global__ void __launch_bounds__(kGroupsPerCta) k_down0(const T *__restrict__ v
   __syncthreads();
   const int g = g0 + threadIdx.x;
   if (g < L.G) {
-    T *mine = tile + threadIdx.x * PITCH;
-    auto acc = [&](int i, int r) -> T & { return mine[i * B + r]; };
-    down_group<T, B, true>(L, g, acc);
+    const T *mine = tile + threadIdx.x * PITCH;
+    T f[kQ0][B], sep[B];
+#pragma unroll
+    for (int i = 0; i < kQ0; ++i)
+#pragma unroll
+      for (int r = 0; r < B; ++r) f[i][r] = mine[i * B + r];
+#pragma unroll
+    for (int r = 0; r < B; ++r) sep[r] = mine[kQ0 * B + r];
+    down_group<T, B, kQ0, true>(L, g, f, sep);
   }
 }
 
@@ -515,7 +511,7 @@ __global__ void __launch_bounds__(kGroupsPerCta) k_up0(const int *active, LevelA
   if (g < L.G) {
     T *mine = tile + threadIdx.x * PITCH;
     auto out = [&](int i, int r, T v) { mine[i * B + r] = v; };
-    up_group<T, B, true>(L, g, solnext, out);
+    up_group<T, B, kQ0, true>(L, g, solnext, out);
   }
   __syncthreads();
   const int64_t row0 = (int64_t)g0 * SPAN;
@@ -548,17 +544,36 @@ __global__ void k_up_level(const int *active, LevelApply<T> L, const T *solnext)
 // copied to shared memory, then the down sweeps and the up sweeps run there.  Level
 // first reads the separator vectors of level first-1 and writes its solution to global
 // memory (the up sweep of level first-1 reads it).
+// Shared-memory arrays of the tail start on 16-byte boundaries; a staged array is copied
+// in 16-byte chunks, four per thread in flight (global arrays are 256-byte aligned and
+// padded, so the last chunk stays inside the array's allocation).
+__device__ __forceinline__ size_t tail_bytes(size_t count, size_t es) { return (count * es + 15) & ~size_t(15); }
+
 template <typename T>
-__device__ __forceinline__ void stage(T *&cursor, const T *&dst_ptr, size_t count) {
-  T *d = cursor;
-  for (size_t e = threadIdx.x; e < count; e += blockDim.x) d[e] = dst_ptr[e];
-  dst_ptr = d;
-  cursor += (count + 1) & ~size_t(1);
+__device__ __forceinline__ void stage(unsigned char *&cur, const T *&ptr, size_t count) {
+  const size_t n16 = tail_bytes(count, sizeof(T)) / 16;
+  const uint4 *__restrict__ src = reinterpret_cast<const uint4 *>(ptr);
+  uint4 *dst = reinterpret_cast<uint4 *>(cur);
+  for (size_t e = threadIdx.x; e < n16; e += 4 * (size_t)blockDim.x) {
+    uint4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const size_t k = e + (size_t)u * blockDim.x;
+      if (k < n16) v[u] = __ldg(src + k);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const size_t k = e + (size_t)u * blockDim.x;
+      if (k < n16) dst[k] = v[u];
+    }
+  }
+  ptr = reinterpret_cast<const T *>(cur);
+  cur += n16 * 16;
 }
 template <typename T>
-__device__ __forceinline__ T *carve_s(T *&cursor, size_t count) {
-  T *d = cursor;
-  cursor += (count + 1) & ~size_t(1);
+__device__ __forceinline__ T *carve_s(unsigned char *&cur, size_t count) {
+  T *d = reinterpret_cast<T *>(cur);
+  cur += tail_bytes(count, sizeof(T));
   return d;
 }
 
@@ -569,7 +584,7 @@ __global__ void __launch_bounds__(512) k_tail(const int *active, const LevelAppl
   __shared__ LevelApply<T> S[kMaxLevels];
   if (last - first + 1 > kMaxLevels) return;
   constexpr int BB = B * B;
-  T *cur = reinterpret_cast<T *>(tail_smem);
+  unsigned char *cur = tail_smem;
   for (int l = first; l <= last; ++l) {
     LevelApply<T> L = lv[l];
     const size_t gq = (size_t)L.G * L.q * BB, gs = (size_t)L.G * BB;
@@ -580,11 +595,11 @@ __global__ void __launch_bounds__(512) k_tail(const int *active, const LevelAppl
     stage(cur, L.Vs, gq);
     stage(cur, L.LoSep, gs);
     stage(cur, L.UpSepPrev, gs);
-    L.p = carve_s(cur, (size_t)L.G * L.q * B);
-    L.cR = carve_s(cur, (size_t)L.G * B + 64);
-    L.cL = carve_s(cur, (size_t)L.G * B + 64);
-    L.seprhs = carve_s(cur, (size_t)L.G * B + 64);
-    if (l > first) L.sol = carve_s(cur, (size_t)(L.nb + 1) * B);
+    L.p = carve_s<T>(cur, (size_t)L.G * L.q * B);
+    L.cR = carve_s<T>(cur, (size_t)L.G * B + 64);
+    L.cL = carve_s<T>(cur, (size_t)L.G * B + 64);
+    L.seprhs = carve_s<T>(cur, (size_t)L.G * B + 64);
+    if (l > first) L.sol = carve_s<T>(cur, (size_t)(L.nb + 1) * B);
     if (threadIdx.x == 0) S[l - first] = L;
   }
   __syncthreads();
@@ -631,9 +646,9 @@ void BandSolver::plan(int64_t n_, int b_) {
 
 // Shared memory of the tail kernel for levels first..last in elements of `es` bytes: the
 // factor blocks, p, the separator vectors and (above `first`) the solution of each level,
-// every array rounded up to an even element count exactly as k_tail carves them.
+// every array rounded up to 16 bytes exactly as k_tail carves them.
 size_t BandSolver::tail_smem_bytes(int first, int last, int es) const {
-  auto ev = [](size_t c) { return (c + 1) & ~size_t(1); };
+  auto ev = [es](size_t c) { return ((c * es + 15) & ~size_t(15)) / es; };
   size_t e = 0;
   const int BB = b * b;
   for (int l = first; l <= last; ++l) {

@@ -131,7 +131,6 @@ struct psp_ctx {
   bool profiling = false;
   cudaEvent_t ev[3][kMaxM][6] = {};                          // profiling events per graph
   psp_profile prof{};
-  ArnoldiMaps maps{};
   double *hostbuf = nullptr;   // pinned staging for psp_step_host
   double *dev_un = nullptr, *dev_unp1 = nullptr;
 };
@@ -182,11 +181,11 @@ void enqueue_cycle(psp_ctx *h, int slot, cudaStream_t s) {
       else launch_stencil<T, T, T>(g, xin, pycol, h->st, active, s);
     }
     if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);
-    launch_arnoldi<T>(j, 0, g.n, h->maps, V, h->ld, Py, h->ld, h->st, h->partial, h->mixed ? 1 : 0, s,
+    launch_arnoldi<T>(j, 0, g.n, V, h->ld, Py, h->ld, h->st, h->partial, h->mixed ? 1 : 0, s,
                       ev ? ev + 3 : nullptr, fused ? &mv : nullptr);
   }
   // reduction-only step completing column m-1 when the cycle runs to m columns
-  launch_arnoldi<T>(h->m, 1, g.n, h->maps, V, h->ld, Py, h->ld, h->st, h->partial, h->mixed ? 1 : 0, s, nullptr);
+  launch_arnoldi<T>(h->m, 1, g.n, V, h->ld, Py, h->ld, h->st, h->partial, h->mixed ? 1 : 0, s, nullptr);
   if (slot < 0) {
     launch_update_z<T>(g.n, V, h->ld, Z, h->X, 1, h->st, s);
   } else {
@@ -386,7 +385,7 @@ psp_status psp_create(const psp_grid *grid, int order, const psp_term *terms, in
   h->geo.n = n;
   h->geo.R = R;
   h->fused = o.fuse_matvec != 0 && fused_matvec_ok(h->geo, h->mixed ? 4 : 8);
-  h->ld = round_up(n, 512);   // whole 1 KB tiles of the Gram-Schmidt pipeline (FP32 and FP64)
+  h->ld = round_up(n, 512);   // every column starts on a 2 KB boundary (16-byte vector loads)
   h->mmax = o.max_hist_cols > 0 ? o.max_hist_cols : 2 * (m + 1);
   if (h->mmax < m + 1) h->mmax = m + 1;
   const size_t es = h->mixed ? sizeof(float) : sizeof(double);
@@ -398,7 +397,6 @@ psp_status psp_create(const psp_grid *grid, int order, const psp_term *terms, in
   };
   bool ok = true;
   ok = ok && dalloc(&h->V, (size_t)h->ld * (m + 1) * es);
-  const int vcols = m + 1;
   ok = ok && dalloc(&h->Px, (size_t)h->ld * h->mmax * es);
   ok = ok && dalloc(&h->Py, (size_t)h->ld * h->mmax * es);
   ok = ok && dalloc(&h->Z, (size_t)h->ld * es);
@@ -428,16 +426,6 @@ psp_status psp_create(const psp_grid *grid, int order, const psp_term *terms, in
     cudaGetLastError();
     psp_destroy(h);
     return fail(PSP_ERR_OOM, "device or pinned allocation failed");
-  }
-  {
-    const bool enc = h->mixed ? encode_arnoldi_maps<float>(h->maps, (const float *)h->V, vcols, (const float *)h->Py,
-                                                           h->mmax, h->ld)
-                              : encode_arnoldi_maps<double>(h->maps, (const double *)h->V, vcols,
-                                                            (const double *)h->Py, h->mmax, h->ld);
-    if (!enc) {
-      psp_destroy(h);
-      return fail(PSP_ERR_CUDA, "tensor map encoding failed");
-    }
   }
   std::memset(h->st_host, 0, sizeof(DevState));
   h->st_host->mmax = h->mmax;

@@ -76,24 +76,15 @@ void launch_restart(const Geometry &g, const double *X, const double *B, TH *Px,
 // arnoldi.cu
 int arnoldi_grid();   // CTAs of the Gram-Schmidt passes (one per SM)
 void arnoldi_setup(); // grid size and shared-memory attributes; call once outside capture
-// Opaque storage of the TMA tensor maps (CUtensorMap, 128 bytes each) of the passes:
-// V with boxes of 16, 4 and 1 columns, and the P_y ring.
-struct alignas(64) ArnoldiMaps {
-  unsigned char V[3 * 128];
-  unsigned char Py[128];
-};
-template <typename T>
-bool encode_arnoldi_maps(ArnoldiMaps &maps, const T *V, int ncols, const T *Py, int mmax, int64_t ld);
-
 // DCGS2 step of iteration j (0-based) of a cycle: pass A (dots) and pass B (update).  With
 // final_step, pass B only completes column j-1 (no matvec was made at this j).  If
 // ev != nullptr, ev[0..2] are recorded after pass A, (nothing), pass B (profiling).  With
 // mv, pass A also makes the iteration's matvec w_j = A x into mv->w (and the copy of x
-// into mv->xcopy) on its own tiles before it reads w_j back; mv is only valid when
-// fused_matvec_ok(geometry) holds.
+// into mv->xcopy) for the vectors each thread streams, and uses w_j from registers; mv is
+// only valid when fused_matvec_ok(geometry) holds.
 template <typename T>
-void launch_arnoldi(int j, int final_step, int64_t n, const ArnoldiMaps &maps, T *V, int64_t ldv, const T *Py,
-                    int64_t ldh, DevState *st, double *partial, int mixed, cudaStream_t s, cudaEvent_t *ev = nullptr,
+void launch_arnoldi(int j, int final_step, int64_t n, T *V, int64_t ldv, const T *Py, int64_t ldh, DevState *st,
+                    double *partial, int mixed, cudaStream_t s, cudaEvent_t *ev = nullptr,
                     const TileMatvec<T> *mv = nullptr);
 // The folded matvec handles the geometry: x rows of whole 16-byte vectors (elem bytes each)
 // with more vectors per row than stencil halo vectors.
