@@ -18,7 +18,7 @@
 //                           t = Hbar a, h_j = ([b; (beta - a^T b)/nu_j] - t) / nu_j,
 //                           c = t/nu_j + h_j, d = c_{0..j-1} - (c_j/nu_j) a;
 //   pass B (k_dcgs_update): streams q_j and v_{j+1} = w_j/nu_j - (c_j/nu_j) v_j - Q d; its
-//                           extra last CTA runs the FP64 Givens step of column j-1.
+//                           extra first CTA (block 0) runs the FP64 Givens step of column j-1.
 //
 // That Givens CTA alone owns the persistent state (Givens rotations, R(j), the finish test,
 // the triangular solve at the end of the cycle).  The Krylov vector v_j handed to the
@@ -500,7 +500,9 @@ __global__ void __launch_bounds__(kUpdThreads) k_dcgs_update(T *__restrict__ V, 
   asm volatile("griddepcontrol.wait;" ::: "memory");
   if (st->active == 0) return;   // the cycle ended: nothing to do
   extern __shared__ __align__(16) double dsm[];
-  if (blockIdx.x == gridDim.x - 1) {   // the Givens CTA
+  // block 0 is the Givens CTA: the first block is scheduled first, so it runs alongside the
+  // streaming CTAs instead of waiting for a free slot after them
+  if (blockIdx.x == 0) {
     dcgs_givens(st, j, final_step, mixed, dsm);
     return;
   }
@@ -517,7 +519,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_dcgs_update(T *__restrict__ V, 
   VT *vn = reinterpret_cast<VT *>(V + (int64_t)(j + 1) * ldv);
   const VT *w = reinterpret_cast<const VT *>(Pyb + (int64_t)((st->hist_base + woff) % st->mmax) * ldh);
   const int64_t stride = (int64_t)(gridDim.x - 1) * blockDim.x;   // streaming CTAs
-  for (int64_t iv = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; iv < nv; iv += 2 * stride) {
+  for (int64_t iv = (blockIdx.x - 1) * (int64_t)blockDim.x + threadIdx.x; iv < nv; iv += 2 * stride) {
     const int64_t iv2 = iv + stride;
     const bool two = iv2 < nv;
     const int64_t jv2 = two ? iv2 : iv;
@@ -637,9 +639,9 @@ void launch_arnoldi(int j, int final_step, int64_t n, T *V, int64_t ldv, const T
   if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
   if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
   {
-    // streaming CTAs (none for the final step) plus one CTA for the Givens step, launched as
-    // a programmatic dependent of pass A
-    int ugrid = final_step ? 0 : (int)std::min<int64_t>((nv + kUpdThreads - 1) / kUpdThreads, (int64_t)arnoldi_grid() * 4);
+    // one CTA for the Givens step plus the streaming CTAs (none for the final step), all in
+    // one wave of four CTAs per SM, launched as a programmatic dependent of pass A
+    int ugrid = final_step ? 0 : (int)std::min<int64_t>((nv + kUpdThreads - 1) / kUpdThreads, (int64_t)arnoldi_grid() * 4 - 1);
     if (!final_step && ugrid < 1) ugrid = 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(ugrid + 1));
