@@ -100,7 +100,9 @@ typedef struct {
   double rel_res;    /* PSP_FP64: Givens estimate R(k)/||u^n|| at exit;
                         PSP_MIXED: FP64 true residual ||u^n - A u^{n+1}|| / ||u^n|| */
   int hist_cols;     /* valid history columns after the step */
-  int singular_rows; /* degenerate rows in the fit made after the step */
+  int singular_rows; /* degenerate rows in the fit made after the step (0 if no fit was
+                        made: none is made while the acceptance rule's back-off keeps
+                        the next step from trying a candidate) */
   int launches;      /* CUDA kernels this step launched (every kernel node of every
                         replayed cycle graph, plus the fit and factorisation kernels) */
 } psp_step_info;
@@ -146,7 +148,8 @@ const char *psp_last_error(void);
  * One implicit-Euler step (Eq. 4): u_np1 = A^{-1} u_n to the relative tolerance tol
  * (||u_n - A u_np1|| <= tol ||u_n||), by Algorithm 1 with X_0 = u_n, B = u_n and the
  * adopted preconditioner N (identity until a fit was adopted), followed by the
- * Algorithm 2 fit of a candidate N for the next step.  u_n and u_np1 are device arrays
+ * Algorithm 2 fit of a candidate N for the next step (not made while the acceptance
+ * rule's back-off keeps the next step from trying a candidate).  u_n and u_np1 are device arrays
  * of n doubles and must not overlap.  `info` (host) may be NULL.  The history persists
  * across steps while dt is unchanged and is cleared when dt changes.
  * Returns PSP_ERR_NOCONV after max_restarts cycles (u_np1 = last iterate).

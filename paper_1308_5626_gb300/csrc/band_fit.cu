@@ -13,6 +13,12 @@
 // first and last b rows take the slope of the simple linear fit on P_x(i,:) (diagonal
 // of N only), as the paper prescribes.  A row whose relative Cholesky pivot is <= 1e-12
 // (regressors collinear in the sample) gets the identity row and is counted.
+//
+// Moments of an FP32 history are accumulated in double-float (an FP32 pair): every product
+// of two FP32 values is split exactly into p + e with one FMA and added by an error-free
+// two-sum, so a moment carries about 48 significant bits -- FP64-grade for sums of a few
+// hundred terms -- at FP32 instruction rates (GB300 runs FP64 at 1/64 of the FP32 rate).
+// An FP64 history is accumulated in FP64.
 #include "psp_kernels.cuh"
 
 namespace psp {
@@ -21,19 +27,48 @@ constexpr double kRelPivot = 1e-12;
 constexpr int kFitRows = 256;   // rows per CTA
 constexpr int kFitCols = 8;     // history columns staged per round
 
+// Accumulators of the moments: FP64, or double-float for FP32 data (see above).
+struct AccD {
+  double v = 0.0;
+  __device__ __forceinline__ void fma(double a, double b) { v = ::fma(a, b, v); }
+  __device__ __forceinline__ void add(double a) { v += a; }
+  __device__ __forceinline__ double get() const { return v; }
+};
+struct AccF2 {
+  float hi = 0.0f, lo = 0.0f;
+  // hi + lo += a b: two-product a b = p + e (FMA), two-sum hi + p = s + err (Knuth); the
+  // _rn intrinsics keep the compiler from contracting or reassociating these steps
+  __device__ __forceinline__ void fma(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = fmaf(a, b, -p);
+    add2(p, e);
+  }
+  __device__ __forceinline__ void add(float a) { add2(a, 0.0f); }
+  __device__ __forceinline__ void add2(float p, float e) {
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+  }
+  __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
+};
+template <typename TH> struct FitAcc;
+template <> struct FitAcc<double> { using type = AccD; };
+template <> struct FitAcc<float> { using type = AccF2; };
+
 template <typename TH, int B>
 __global__ void __launch_bounds__(kFitRows) k_fit_moments(int64_t n, int M, const TH *__restrict__ Px,
                                                           const TH *__restrict__ Py, int64_t ld,
                                                           double *__restrict__ mom) {
   constexpr int TW = kFitRows + 3 * B;   // P_x rows r0-B .. r0+kFitRows+2B-1
   constexpr int NM = 4 * B + 4;
-  __shared__ double sx[kFitCols][TW];
-  __shared__ double sy[kFitCols][kFitRows];
+  using Acc = typename FitAcc<TH>::type;
+  __shared__ TH sx[kFitCols][TW];
+  __shared__ TH sy[kFitCols][kFitRows];
   const int64_t r0 = (int64_t)blockIdx.x * kFitRows;
   const int tid = threadIdx.x;
-  double S[2 * B + 1], Rp[2 * B + 1], sx_sum = 0.0, sy_sum = 0.0;
-#pragma unroll
-  for (int l = 0; l <= 2 * B; ++l) { S[l] = 0.0; Rp[l] = 0.0; }
+  Acc S[2 * B + 1], Rp[2 * B + 1], sx_sum, sy_sum;
   for (int c0 = 0; c0 < M; c0 += kFitCols) {
     const int nc = min(kFitCols, M - c0);
     __syncthreads();
@@ -42,38 +77,54 @@ __global__ void __launch_bounds__(kFitRows) k_fit_moments(int64_t n, int M, cons
       const TH *py = Py + (int64_t)(c0 + cc) * ld;
       for (int t = tid; t < TW; t += kFitRows) {
         const int64_t row = r0 - B + t;
-        sx[cc][t] = (cc < nc && row >= 0 && row < n) ? (double)px[row] : 0.0;
+        sx[cc][t] = (cc < nc && row >= 0 && row < n) ? px[row] : (TH)0;
       }
       const int64_t row = r0 + tid;
-      sy[cc][tid] = (cc < nc && row < n) ? (double)py[row] : 0.0;
+      sy[cc][tid] = (cc < nc && row < n) ? py[row] : (TH)0;
     }
     __syncthreads();
 #pragma unroll 2
     for (int cc = 0; cc < kFitCols; ++cc) {
-      const double *x = &sx[cc][tid + B];   // x[0] = P_x(row, c)
-      const double y = sy[cc][tid];
+      const TH *x = &sx[cc][tid + B];   // x[0] = P_x(row, c)
+      const TH y = sy[cc][tid];
 #pragma unroll
-      for (int l = 0; l <= 2 * B; ++l) S[l] = fma(x[0], x[l], S[l]);
+      for (int l = 0; l <= 2 * B; ++l) S[l].fma(x[0], x[l]);
 #pragma unroll
-      for (int p = 0; p <= 2 * B; ++p) Rp[p] = fma(x[p - B], y, Rp[p]);
-      sx_sum += x[0];
-      sy_sum += y;
+      for (int p = 0; p <= 2 * B; ++p) Rp[p].fma(x[p - B], y);
+      sx_sum.add(x[0]);
+      sy_sum.add(y);
     }
   }
   const int64_t row = r0 + tid;
   if (row < n) {
     double *o = mom + row * NM;
 #pragma unroll
-    for (int l = 0; l <= 2 * B; ++l) { o[l] = S[l]; o[2 * B + 1 + l] = Rp[l]; }
-    o[4 * B + 2] = sx_sum;
-    o[4 * B + 3] = sy_sum;
+    for (int l = 0; l <= 2 * B; ++l) { o[l] = S[l].get(); o[2 * B + 1 + l] = Rp[l].get(); }
+    o[4 * B + 2] = sx_sum.get();
+    o[4 * B + 3] = sy_sum.get();
   }
 }
 
-// Cholesky solve of a Q x Q SPD system in registers.  Returns false if degenerate.
+// 1/sqrt(d), d > 0: an FP32 seed refined by two steps of Newton's iteration for the
+// reciprocal square root, y <- y (3 - d y^2) / 2 (quadratic convergence: the seed's
+// ~2^-22 relative error falls to ~1e-13, then to FP64 rounding).  FP64 square roots and
+// divisions are long instruction sequences on GB300's narrow FP64 pipe; this is 8 FP64
+// operations.  Outside the FP32 exponent range it falls back to 1 / sqrt(d).
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  if (d > 1e-30 && d < 1e30) {
+    double y = (double)rsqrtf((float)d);
+    y = y * (1.5 - 0.5 * d * y * y);
+    y = y * (1.5 - 0.5 * d * y * y);
+    return y;
+  }
+  return 1.0 / sqrt(d);
+}
+
+// Cholesky solve of a Q x Q SPD system in registers (one reciprocal square root per
+// pivot; the substitutions multiply by it).  Returns false if degenerate.
 template <int Q>
 __device__ __forceinline__ bool chol_solve(double (&G)[Q][Q], double (&rhs)[Q], int q) {
-  double L[Q][Q];
+  double L[Q][Q], rd[Q];
 #pragma unroll
   for (int j = 0; j < Q; ++j) {
     if (j >= q) break;
@@ -81,15 +132,17 @@ __device__ __forceinline__ bool chol_solve(double (&G)[Q][Q], double (&rhs)[Q], 
 #pragma unroll
     for (int l = 0; l < Q; ++l) if (l < j) d -= L[j][l] * L[j][l];
     if (!(G[j][j] > 0.0) || !(d > kRelPivot * G[j][j])) return false;
-    const double ljj = sqrt(d);
+    const double r = rsqrt_newton(d);
+    const double ljj = d * r;
     L[j][j] = ljj;
+    rd[j] = r;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       if (i > j && i < q) {
         double s = G[i][j];
 #pragma unroll
         for (int l = 0; l < Q; ++l) if (l < j) s -= L[i][l] * L[j][l];
-        L[i][j] = s / ljj;
+        L[i][j] = s * r;
       }
     }
   }
@@ -100,7 +153,7 @@ __device__ __forceinline__ bool chol_solve(double (&G)[Q][Q], double (&rhs)[Q], 
       double s = rhs[i];
 #pragma unroll
       for (int l = 0; l < Q; ++l) if (l < i) s -= L[i][l] * z[l];
-      z[i] = s / L[i][i];
+      z[i] = s * rd[i];
     }
   }
 #pragma unroll
@@ -109,7 +162,7 @@ __device__ __forceinline__ bool chol_solve(double (&G)[Q][Q], double (&rhs)[Q], 
       double s = z[i];
 #pragma unroll
       for (int l = 0; l < Q; ++l) if (l > i && l < q) s -= L[l][i] * rhs[l];
-      rhs[i] = s / L[i][i];
+      rhs[i] = s * rd[i];
     }
   }
   return true;

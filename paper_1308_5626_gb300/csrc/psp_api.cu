@@ -539,7 +539,10 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
   }
   const int need = 2 * h->b + (h->opts.intercept ? 2 : 1);
   int singular = 0;
-  if (!numeric && hist >= need) {
+  // a fit is only worth making when the next step tries it: while the acceptance rule's
+  // back-off still runs (wait > 0) the next step keeps the adopted N, and the step after
+  // it fits afresh from the longer history, so the skipped fit could never be used
+  if (!numeric && hist >= need && h->wait == 0) {
     psp_status fs = h->mixed ? fit_into<float>(h, (const float *)h->Px, (const float *)h->Py, h->ld, hist,
                                                h->band_cand, &singular)
                              : fit_into<double>(h, (const double *)h->Px, (const double *)h->Py, h->ld, hist,
