@@ -400,6 +400,12 @@ __global__ void __launch_bounds__(kDotThreads, 1) k_dcgs_dots(const T *__restric
                                                                 const T *__restrict__ Pyb, int64_t ldh, int j,
                                                                 int woff, DevState *st, T *partial, int64_t nv,
                                                                 int final_step, const TileMatvec<T> mv) {
+  // launch self-check: the engine's cross-CTA sums cover at most kMaxArnCta CTAs and the
+  // partial rows kMaxCta; a larger grid records a device error instead of reading past them
+  if (gridDim.x > kMaxArnCta || gridDim.x > kMaxCta || blockDim.x != kDotThreads) {
+    if (threadIdx.x == 0) atomicExch(&st->error, 3);
+    return;
+  }
   if (st->active == 0) return;
   using VT = typename Vec<T>::type;
   constexpr int W = Vec<T>::W;
