@@ -54,6 +54,7 @@ def _args():
     ap.add_argument("--no-fp64-form", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--no-standalone", action="store_true")
     ap.add_argument("--nx", type=int, default=1024, help="grid points per direction (default: the full workload)")
     return ap.parse_args()
 
@@ -128,6 +129,11 @@ class ClockSampler:
 # --------------------------------------------------------------------------------------
 # helpers
 # --------------------------------------------------------------------------------------
+
+# FP64 FMA throughput of this GPU type, measured with an FMA-chain kernel (2 FP64 FMA per
+# clock per SM x 152 SMs at the ~1.99 GHz seen under that load); 1.26 at the 2.07 GHz maximum
+FP64_PEAK_TFLOPS = 1.20
+
 
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -231,6 +237,98 @@ def _time_form(w, precision, steps, warmup, device, world, profile):
     res = {"ms_total": ms, "host_s": t_host, "infos": infos, "prof": prof, "solver": solver, "u": u,
            "stream": stream}
     return res
+
+
+def _standalone(w, device, hbm_peak, fp64_peak_tflops):
+    """Stencil (S1) and band fit (S6) on their own, through the C ABI, in both forms.
+
+    Each call is bracketed by CUDA events on the solver's stream; the minimum of several calls
+    is kept.  psp_matvec uploads the coefficients only when dt changes, so the timed stencil
+    calls are the kernel and its launch; the fit interval is the whole psp_fit_band call
+    (moments, row solves, the singular-row count).  Algorithmic bytes: stencil 2 s n, fit
+    2 s n M + 8 n (4b+4) (history once, moments once); fit arithmetic 4(2b+1)+4 flops per
+    history element (the lagged and cross products and sums, FP64-grade)."""
+    import torch
+    from paper_1308_5626_gb300 import psp
+    out = {}
+    n, b = w.n, w.b
+    M = 2 * (w.m + 1)
+    g = torch.Generator(device=device)
+    g.manual_seed(7)
+    for name, prec, dt in (("mixed", psp.PSP_MIXED, torch.float32), ("fp64", psp.PSP_FP64, torch.float64)):
+        stream = torch.cuda.Stream(device=device)
+        with torch.cuda.stream(stream):
+            s = psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=prec, stream=stream)
+            es = 4 if dt == torch.float32 else 8
+            x = torch.randn(n, dtype=dt, device=device, generator=g)
+            y = torch.empty_like(x)
+            Px = torch.randn(M, n, dtype=dt, device=device, generator=g)
+            Py = torch.randn(M, n, dtype=dt, device=device, generator=g)
+            band = torch.empty(n * (2 * b + 1), dtype=torch.float64, device=device)
+
+            def timed(call, reps):
+                best = None
+                for _ in range(reps):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    call()
+                    e1.record(stream)
+                    e1.synchronize()
+                    t = e0.elapsed_time(e1)
+                    best = t if best is None else min(best, t)
+                return best
+
+            timed(lambda: psp.psp_matvec(s.handle, x, y, w.dt), 3)
+            ms_st = timed(lambda: psp.psp_matvec(s.handle, x, y, w.dt), 20)
+            timed(lambda: psp.psp_fit_band(s.handle, Px, Py, band), 1)
+            ms_fit = timed(lambda: psp.psp_fit_band(s.handle, Px, Py, band), 3)
+            s.close()
+        st_bytes = 2.0 * es * n
+        fit_bytes = 2.0 * es * n * M + 8.0 * n * (4 * b + 4)
+        fit_flops = (4.0 * (2 * b + 1) + 4.0) * n * M
+        out[name] = {
+            "stencil": {"us": ms_st * 1e3, "bytes": st_bytes, "gbs": st_bytes / (ms_st * 1e-3) / 1e9,
+                        "frac_hbm": st_bytes / (ms_st * 1e-3) / 1e9 / hbm_peak},
+            "band_fit": {"ms": ms_fit, "history_cols": M, "bytes": fit_bytes,
+                         "gbs": fit_bytes / (ms_fit * 1e-3) / 1e9,
+                         "frac_hbm": fit_bytes / (ms_fit * 1e-3) / 1e9 / hbm_peak,
+                         "tflops_fp64_grade": fit_flops / (ms_fit * 1e-3) / 1e12,
+                         "frac_fp64_peak": fit_flops / (ms_fit * 1e-3) / 1e12 / fp64_peak_tflops},
+        }
+    # the stencil alone on the 256^3 grid of the 3D workload (8th order, radius 5, 31-point
+    # cross): at 1024^2 the kernel's ~1.5 us of data time is small against its launch
+    from paper_1308_5626_gb300 import inputs
+    w3 = inputs.c3(256, with_u0=False)
+    n3 = w3.n
+    for name, prec, dt in (("mixed", psp.PSP_MIXED, torch.float32), ("fp64", psp.PSP_FP64, torch.float64)):
+        stream = torch.cuda.Stream(device=device)
+        with torch.cuda.stream(stream):
+            s = psp.Solver(w3.shape, w3.order, w3.terms, w3.b, 2, precision=prec, max_hist_cols=4, stream=stream)
+            x = torch.randn(n3, dtype=dt, device=device, generator=g)
+            y = torch.empty_like(x)
+            best = None
+            for r in range(12):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                psp.psp_matvec(s.handle, x, y, 1e-3)
+                e1.record(stream)
+                e1.synchronize()
+                if r >= 2:
+                    t = e0.elapsed_time(e1)
+                    best = t if best is None else min(best, t)
+            s.close()
+            del x, y
+        es = 4 if dt == torch.float32 else 8
+        by = 2.0 * es * n3
+        out[name]["stencil_256cubed"] = {"us": best * 1e3, "bytes": by, "gbs": by / (best * 1e-3) / 1e9,
+                                         "frac_hbm": by / (best * 1e-3) / 1e9 / hbm_peak}
+    out["note"] = ("psp_matvec / psp_fit_band through the C ABI on the %s grid (stencil also on 256^3), CUDA events around each "
+                   "call, minimum of 20 / 3 calls (coefficients uploaded once per dt, outside the timed calls); "
+                   "the fit uses M = 2(m+1) random history columns; FP64 peak %.2f TFLOP/s measured"
+                   % ("x".join(str(v) for v in w.shape), fp64_peak_tflops))
+    return out
 
 
 def _e2e(w, precision, steps, device):
@@ -400,12 +498,16 @@ def main():
         e2e = {"value": world * a.steps / secs}
         e2e.update(e)
 
+    hbm_peak, peak_kind = _peaks()
+    standalone = None
+    if not a.no_standalone and rank == 0:
+        standalone = _standalone(w, device, hbm_peak, FP64_PEAK_TFLOPS)
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return
 
-    hbm_peak, peak_kind = _peaks()
     roofline = None
     kernels = {}
     if prof:
@@ -465,6 +567,7 @@ def main():
         {"source": "CUDA events recorded by the library around every kernel class of every 4th Arnoldi "
                    "iteration, in a separate timed region of the same %d steps" % a.steps,
          "ms_per_step_with_events": prof_ms},
+        "standalone": standalone,
         "cpu_baseline": cpu, "clocks": clk,
     }
     if fp64:

@@ -686,6 +686,9 @@ template void launch_arnoldi<double>(int, int, int64_t, double *, int64_t, const
 bool fused_matvec_ok(const Geometry &g, int elem_bytes) {
   const int W = 16 / elem_bytes;
   const int nh = (g.R + W - 1) / W;
+  // a 3D grid that the z-marching tiled stencil takes keeps its own matvec kernel: folded,
+  // each vector would gather its 4R+2NH+1 neighbour vectors from L2 one by one
+  if (g.ndim == 3 && stencil_3d_tiled(g, elem_bytes)) return false;
   return g.R >= 1 && g.R <= kMaxR && g.ndim >= 1 && g.ndim <= 3 && g.nx % W == 0 && g.nx / W > nh;
 }
 template void launch_scale_copy<float>(int, int64_t, const float *, int64_t, OutRef<float>, const DevState *,

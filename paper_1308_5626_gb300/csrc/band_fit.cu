@@ -105,23 +105,8 @@ __global__ void __launch_bounds__(kFitRows) k_fit_moments(int64_t n, int M, cons
   }
 }
 
-// 1/sqrt(d), d > 0: an FP32 seed refined by two steps of Newton's iteration for the
-// reciprocal square root, y <- y (3 - d y^2) / 2 (quadratic convergence: the seed's
-// ~2^-22 relative error falls to ~1e-13, then to FP64 rounding).  FP64 square roots and
-// divisions are long instruction sequences on GB300's narrow FP64 pipe; this is 8 FP64
-// operations.  Outside the FP32 exponent range it falls back to 1 / sqrt(d).
-__device__ __forceinline__ double rsqrt_newton(double d) {
-  if (d > 1e-30 && d < 1e30) {
-    double y = (double)rsqrtf((float)d);
-    y = y * (1.5 - 0.5 * d * y * y);
-    y = y * (1.5 - 0.5 * d * y * y);
-    return y;
-  }
-  return 1.0 / sqrt(d);
-}
-
-// Cholesky solve of a Q x Q SPD system in registers (one reciprocal square root per
-// pivot; the substitutions multiply by it).  Returns false if degenerate.
+// Cholesky solve of a Q x Q SPD system in registers (one square root and one division per
+// pivot; the substitutions multiply by the pivot's reciprocal).  Returns false if degenerate.
 template <int Q>
 __device__ __forceinline__ bool chol_solve(double (&G)[Q][Q], double (&rhs)[Q], int q) {
   double L[Q][Q], rd[Q];
@@ -132,8 +117,8 @@ __device__ __forceinline__ bool chol_solve(double (&G)[Q][Q], double (&rhs)[Q], 
 #pragma unroll
     for (int l = 0; l < Q; ++l) if (l < j) d -= L[j][l] * L[j][l];
     if (!(G[j][j] > 0.0) || !(d > kRelPivot * G[j][j])) return false;
-    const double r = rsqrt_newton(d);
-    const double ljj = d * r;
+    const double ljj = sqrt(d);
+    const double r = 1.0 / ljj;
     L[j][j] = ljj;
     rd[j] = r;
 #pragma unroll

@@ -124,6 +124,7 @@ struct psp_ctx {
   double rate_ref = -1;  // reference per-iteration residual reduction
   int wait = 0, wait_len = 1;
   double hist_dt = NAN;
+  double api_dt = NAN;   // dt of the coefficients in api_st (psp_matvec)
   int last_singular = 0;
 
   cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};   // [0] N = I, [1] slot 0, [2] slot 1
@@ -286,6 +287,17 @@ void accumulate_profile(psp_ctx *h, int which, int k_end) {
 double rate_of(double R_end, double beta, int k) {
   if (k <= 0 || !(beta > 0.0)) return 1.0;
   return std::pow(std::max(R_end, 1e-300) / beta, 1.0 / k);
+}
+
+// Coefficients of A for psp_matvec, uploaded only when dt differs from the last call's.
+psp_status upload_api_coef(psp_ctx *h, double dt) {
+  if (h->api_dt == dt) return PSP_OK;
+  set_coef(h, dt, h->st_host->coef);
+  PSP_CUDA(cudaMemcpyAsync(h->api_st->coef, h->st_host->coef, sizeof(h->st_host->coef), cudaMemcpyHostToDevice,
+                           h->stream));
+  PSP_CUDA(cudaStreamSynchronize(h->stream));   // the pinned staging is reused by psp_step
+  h->api_dt = dt;
+  return PSP_OK;
 }
 
 }  // namespace
@@ -588,9 +600,8 @@ psp_status psp_step_host(psp_handle h, const double *u_n_host, double *u_np1_hos
 
 psp_status psp_matvec(psp_handle h, const double *x, double *y, double dt) {
   if (!h || !x || !y) return fail(PSP_ERR_ARG, "NULL argument");
-  set_coef(h, dt, h->st_host->coef);
-  PSP_CUDA(cudaMemcpyAsync(h->api_st->coef, h->st_host->coef, sizeof(h->st_host->coef), cudaMemcpyHostToDevice,
-                           h->stream));
+  psp_status cs = upload_api_coef(h, dt);
+  if (cs != PSP_OK) return cs;
   launch_stencil<double, double, double>(h->geo, fixed_in<double>(x), fixed_out<double>(y), h->api_st, nullptr, h->stream);
   PSP_CUDA(cudaGetLastError());
   PSP_CUDA(cudaStreamSynchronize(h->stream));
@@ -599,9 +610,8 @@ psp_status psp_matvec(psp_handle h, const double *x, double *y, double dt) {
 
 psp_status psp_matvec_f32(psp_handle h, const float *x, float *y, double dt) {
   if (!h || !x || !y) return fail(PSP_ERR_ARG, "NULL argument");
-  set_coef(h, dt, h->st_host->coef);
-  PSP_CUDA(cudaMemcpyAsync(h->api_st->coef, h->st_host->coef, sizeof(h->st_host->coef), cudaMemcpyHostToDevice,
-                           h->stream));
+  psp_status cs = upload_api_coef(h, dt);
+  if (cs != PSP_OK) return cs;
   launch_stencil<float, float, float>(h->geo, fixed_in<float>(x), fixed_out<float>(y), h->api_st, nullptr, h->stream);
   PSP_CUDA(cudaGetLastError());
   PSP_CUDA(cudaStreamSynchronize(h->stream));

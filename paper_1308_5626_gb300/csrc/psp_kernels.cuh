@@ -54,6 +54,9 @@ inline OutRef<T> ring_out(T *base, int64_t ld, const int *counter, int mmax, int
 }
 
 int reduce_grid(int64_t n);
+// The 3D geometry is taken by the z-marching tiled stencil (x a whole number of tiles of
+// 32 16-byte vectors, y of 8 rows).
+bool stencil_3d_tiled(const Geometry &g, int elem_bytes);
 
 // Matvec folded into the first Gram-Schmidt pass (see launch_arnoldi).
 template <typename T>

@@ -8,6 +8,7 @@
 // coef[0][R].  One thread computes one grid point; neighbour loads go through the
 // read-only cache, and the y/z neighbours of a warp's 32 consecutive x points are reused
 // from L1/L2 by the warps of the neighbouring rows.
+#include <algorithm>
 #include <type_traits>
 
 #include "psp_kernels.cuh"
@@ -312,6 +313,191 @@ static int stencil_grid(int64_t n) {
     default: break;                               \
   }
 
+// 3D vectorised stencil with z-marching (2.5D blocking): a CTA owns a tile of kTileXV
+// x-vectors by kTileY rows and walks a range of planes.  Each thread keeps the 2R+1 planes
+// of its own vector in a register queue (the z terms), loaded R planes ahead.  The tile of
+// each plane, with an x halo of whole vectors and a y halo of R rows on each side (no
+// corners), is staged in a ring of kStage3 shared-memory slots by 16-byte asynchronous
+// copies (cp.async) issued kAhead3 planes ahead, so the halo latency overlaps the work of
+// the planes before it.  A point is read from HBM about once; the halos come from L2.
+// Needs nx / W and ny to be multiples of the tile (the periodic wrap is then tile-exact).
+constexpr int kTileXV = 32;
+constexpr int kTileY = 8;
+constexpr int kAhead3 = 4;
+constexpr int kStage3 = kAhead3 + 1;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <typename T, int R>
+__host__ __device__ constexpr int tile3d_slot_vecs() {
+  return (kTileY + 2 * R) * (kTileXV + 2 * ((R + SVec<T>::W - 1) / SVec<T>::W));
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(kTileXV * kTileY, 2) k_stencil_3d(InRef<T> xref, OutRef<T> yref, OutRef<T> xcopy,
+                                                                   const double *scale, const DevState *__restrict__ st,
+                                                                   int nx, int ny, int nz, int tz, const int *active) {
+  using VT = typename SVec<T>::type;
+  constexpr int W = SVec<T>::W;
+  constexpr int NH = (R + W - 1) / W;
+  constexpr int SX = kTileXV + 2 * NH;
+  constexpr int SLOT = tile3d_slot_vecs<T, R>();
+  if (active && *active == 0) return;
+  extern __shared__ __align__(16) unsigned char smem3[];
+  VT *ring = reinterpret_cast<VT *>(smem3);
+  __shared__ T s_c[3][2 * R + 1];
+  if (threadIdx.x < 3 * (2 * R + 1)) {
+    const int d = threadIdx.x / (2 * R + 1), j = threadIdx.x % (2 * R + 1);
+    s_c[d][j] = (T)st->coef[d][kMaxR - R + j];
+  }
+  const T *__restrict__ x = xref.get();
+  T *y = yref.get();
+  T *xc = xcopy.base ? xcopy.get() : nullptr;
+  const T sc = scale ? (T)(*scale) : (T)1;
+  const int nxv = nx / W;
+  const int64_t plane = (int64_t)nx * ny;
+  const int tx = threadIdx.x % kTileXV, ty = threadIdx.x / kTileXV;
+  const int xv0 = blockIdx.x * kTileXV, y0 = blockIdx.y * kTileY;
+  const int xv = xv0 + tx, iy = y0 + ty;
+  const int z0 = blockIdx.z * tz;
+  const int z1 = min(z0 + tz, nz);
+  auto wrapz = [&](int z) { return z < 0 ? z + nz : (z >= nz ? z - nz : z); };
+  auto gptr = [&](int vx, int vy, int vz) -> const VT * {
+    return reinterpret_cast<const VT *>(x + (int64_t)vz * plane + (int64_t)vy * nx + (int64_t)vx * W);
+  };
+  // the copies of one plane's tile into ring slot `slot`: centre rows (own vector), x halo
+  // of the centre rows, y halo rows (centre columns only)
+  auto stage = [&](int z, int slot) {
+    VT *t = ring + slot * SLOT;
+    cp_async16(t + (ty + R) * SX + tx + NH, gptr(xv, iy, z));
+    if (tx < NH) {
+      int v = xv0 - NH + tx;
+      v += (v < 0) ? nxv : 0;
+      cp_async16(t + (ty + R) * SX + tx, gptr(v, iy, z));
+    } else if (tx >= kTileXV - NH) {
+      const int u = tx - (kTileXV - NH);
+      int v = xv0 + kTileXV + u;
+      v -= (v >= nxv) ? nxv : 0;
+      cp_async16(t + (ty + R) * SX + kTileXV + NH + u, gptr(v, iy, z));
+    }
+    for (int e = threadIdx.x; e < 2 * R * kTileXV; e += blockDim.x) {
+      const int hr = e / kTileXV, hx = e % kTileXV;
+      int row = (hr < R) ? y0 - R + hr : y0 + kTileY + (hr - R);
+      row += (row < 0) ? ny : 0;
+      row -= (row >= ny) ? ny : 0;
+      cp_async16(t + ((hr < R) ? hr : kTileY + hr) * SX + hx + NH, gptr(xv0 + hx, row, z));
+    }
+  };
+  VT q[2 * R + 1];
+#pragma unroll
+  for (int k = 0; k < 2 * R; ++k) q[k] = *gptr(xv, iy, wrapz(z0 - R + k));
+#pragma unroll
+  for (int a = 0; a < kAhead3; ++a) {
+    if (z0 + a < z1) stage(z0 + a, a);
+    cp_async_commit();   // one group per plane slot, empty past the range
+  }
+  for (int z = z0; z < z1; ++z) {
+    q[2 * R] = *gptr(xv, iy, wrapz(z + R));
+    {
+      const int za = z + kAhead3;
+      if (za < z1) stage(za, (za - z0) % kStage3);
+      cp_async_commit();
+    }
+    cp_async_wait<kAhead3>();   // this thread's copies of plane z have landed
+    __syncthreads();            // ... and every other thread's
+    const VT *t = ring + ((z - z0) % kStage3) * SLOT;
+    T win[(2 * NH + 1) * W];
+#pragma unroll
+    for (int h = 0; h <= 2 * NH; ++h) {
+      const VT v = t[(ty + R) * SX + tx + h];
+      const T *ve = reinterpret_cast<const T *>(&v);
+#pragma unroll
+      for (int i = 0; i < W; ++i) win[h * W + i] = ve[i];
+    }
+    T acc[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      T a = s_c[0][R] * win[NH * W + i];
+#pragma unroll
+      for (int j = 1; j <= R; ++j) a += s_c[0][R - j] * win[NH * W + i - j] + s_c[0][R + j] * win[NH * W + i + j];
+      acc[i] = a;
+    }
+#pragma unroll
+    for (int j = 1; j <= R; ++j) {
+      const VT tm = t[(ty + R - j) * SX + tx + NH], tp = t[(ty + R + j) * SX + tx + NH];
+      const T *me = reinterpret_cast<const T *>(&tm), *pe = reinterpret_cast<const T *>(&tp);
+#pragma unroll
+      for (int i = 0; i < W; ++i) acc[i] += s_c[1][R - j] * me[i] + s_c[1][R + j] * pe[i];
+    }
+#pragma unroll
+    for (int j = 1; j <= R; ++j) {
+      const T *me = reinterpret_cast<const T *>(&q[R - j]), *pe = reinterpret_cast<const T *>(&q[R + j]);
+#pragma unroll
+      for (int i = 0; i < W; ++i) acc[i] += s_c[2][R - j] * me[i] + s_c[2][R + j] * pe[i];
+    }
+    VT out;
+    T *oe = reinterpret_cast<T *>(&out);
+#pragma unroll
+    for (int i = 0; i < W; ++i) oe[i] = sc * acc[i];
+    const int64_t o = (int64_t)z * plane + (int64_t)iy * nx + (int64_t)xv * W;
+    *reinterpret_cast<VT *>(y + o) = out;
+    if (xc) {
+      const T *ce = reinterpret_cast<const T *>(&q[R]);
+#pragma unroll
+      for (int i = 0; i < W; ++i) oe[i] = sc * ce[i];
+      *reinterpret_cast<VT *>(xc + o) = out;
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * R; ++k) q[k] = q[k + 1];
+    __syncthreads();   // the slot of plane z is refilled by the next step's copies
+  }
+  cp_async_wait<0>();
+}
+
+// Planes per CTA of k_stencil_3d: the fewest chunks of z that fill the resident slots.
+template <typename T, int R>
+static int tile3d_tz(int gx, int gy, int nz) {
+  static int resident = 0;
+  if (resident == 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int bytes = kStage3 * tile3d_slot_vecs<T, R>() * 16;
+    cudaFuncSetAttribute(k_stencil_3d<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_stencil_3d<T, R>, kTileXV * kTileY, bytes);
+    resident = std::max(1, sms) * std::max(1, per);
+  }
+  const int chunks = std::max(1, std::min(nz, resident / std::max(1, gx * gy)));
+  return (nz + chunks - 1) / chunks;
+}
+
+bool stencil_3d_tiled(const Geometry &g, int elem_bytes) {
+  const int W = 16 / elem_bytes;
+  return g.ndim == 3 && g.nx % W == 0 && (g.nx / W) % kTileXV == 0 && g.ny % kTileY == 0 && g.nz >= g.R;
+}
+
+// Grid of the vectorised stencil: one vector per thread when that many CTAs are resident
+// at once, else every resident slot (a grid-stride loop covers the rest).
+template <typename T, int NDIM, int R>
+static int vec_grid(int64_t nvec) {
+  static int resident = 0;
+  if (resident == 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_stencil_vec<T, NDIM, R>, kThreads, 0);
+    resident = std::max(1, sms) * std::max(1, per);
+  }
+  return (int)std::max<int64_t>(1, std::min<int64_t>((nvec + kThreads - 1) / kThreads, resident));
+}
+
 template <typename TI, typename TO, typename TC>
 void launch_stencil(const Geometry &g, InRef<TI> x, OutRef<TO> y, const DevState *st, const int *active,
                     cudaStream_t s, OutRef<TO> xcopy, const double *scale) {
@@ -326,10 +512,19 @@ void launch_stencil(const Geometry &g, InRef<TI> x, OutRef<TO> y, const DevState
                          (y.counter ? (al(y.base) && (y.ld * sizeof(TO)) % 16 == 0) : al(y.base)) &&
                          (!xcopy.base || (xcopy.counter ? (al(xcopy.base) && (xcopy.ld * sizeof(TO)) % 16 == 0)
                                                         : al(xcopy.base)));
+    if (stencil_3d_tiled(g, sizeof(TI)) && aligned) {
+      const int gx = g.nx / W / kTileXV, gy = g.ny / kTileY;
+      PSP_DISPATCH_R(g.R, {
+        const int tz = tile3d_tz<TI, RR>(gx, gy, g.nz);
+        const dim3 grid3(gx, gy, (g.nz + tz - 1) / tz);
+        const int bytes = kStage3 * tile3d_slot_vecs<TI, RR>() * 16;
+        k_stencil_3d<TI, RR><<<grid3, kTileXV * kTileY, bytes, s>>>(x, y, xcopy, scale, st, g.nx, g.ny, g.nz, tz, active);
+      });
+      return;
+    }
     if (g.nx % W == 0 && g.nx / W > nh && aligned) {
       const int64_t nvec = g.n / W;
-      int grid = (int)std::min<int64_t>((nvec + kThreads - 1) / kThreads, 152 * 4);
-      PSP_DISPATCH_NDIM(g.ndim, PSP_DISPATCH_R(g.R, (k_stencil_vec<TI, DD, RR><<<grid, kThreads, 0, s>>>(
+      PSP_DISPATCH_NDIM(g.ndim, PSP_DISPATCH_R(g.R, (k_stencil_vec<TI, DD, RR><<<vec_grid<TI, DD, RR>(nvec), kThreads, 0, s>>>(
                                                         x, y, xcopy, scale, st, g.nx, g.ny, g.nz, active))));
       return;
     }

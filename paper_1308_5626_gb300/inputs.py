@@ -165,13 +165,14 @@ def c2(nx: int = 1024, ny: Optional[int] = None) -> Workload:
                     rho_dt=None, u0=u0, seed=2)
 
 
-def c3(n: int = 256, kmax: float = 32.0) -> Workload:
-    """3D periodic diffusion + hyperdiffusion, 8th order, rho(L) dt = 100 (seed 3)."""
+def c3(n: int = 256, kmax: float = 32.0, with_u0: bool = True) -> Workload:
+    """3D periodic diffusion + hyperdiffusion, 8th order, rho(L) dt = 100 (seed 3).
+    with_u0=False skips the initial field (u0 = None) for uses that need only the operator."""
     rng = np.random.default_rng(3)
     alpha = rng.uniform(0.5, 2.0, 3)
     h = TWO_PI / n
     beta = float(alpha.mean()) * (h / math.pi) ** 2
-    u0 = lowpass_noise((n, n, n), rng, min(kmax, n / 2.0))
+    u0 = lowpass_noise((n, n, n), rng, min(kmax, n / 2.0)) if with_u0 else None
     terms = [Term(2, d, float(alpha[d])) for d in range(3)] + \
             [Term(4, d, -beta) for d in range(3)]
     return Workload("c3_3d_diff_hyperdiff_%d^3" % n, (n, n, n), 8, terms,

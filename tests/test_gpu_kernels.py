@@ -24,6 +24,12 @@ STENCIL_CASES = [
     ((24, 20, 18), 8, [(2, 0, 1.0), (2, 1, 0.6), (2, 2, 1.7), (4, 0, -1e-4), (4, 1, -2e-4), (4, 2, -3e-4)]),
     ((33, 17, 12), 2, [(3, 0, 0.3), (1, 2, -0.5), (4, 1, 0.01)]),
     ((1024, 1024), 6, [(1, 0, 0.8), (1, 1, 1.3), (2, 0, 1e-3), (2, 1, 2e-3)]),
+    # 3D grids that take the z-marching tiled kernel (x a whole number of 32-vector tiles in
+    # FP32 and FP64, y a multiple of 8 rows): one tile, several tiles and z chunks, and the
+    # smallest z extent (2R + 1 planes)
+    ((128, 16, 12), 8, [(2, 0, 1.0), (2, 1, 0.6), (2, 2, 1.7), (4, 0, -1e-4), (4, 1, -2e-4), (4, 2, -3e-4)]),
+    ((256, 24, 20), 6, [(2, 0, 0.9), (1, 1, 0.4), (2, 2, 1.1), (1, 2, -0.7)]),
+    ((128, 16, 11), 8, [(4, 0, -2e-4), (2, 1, 0.8), (4, 2, -1e-4)]),
 ]
 
 
@@ -49,6 +55,28 @@ def test_matvec(dev, shape, order, terms):
     y = torch.empty(op.n, dtype=torch.float64, device=dev)
     psp.psp_matvec(s.handle, t64(x, dev), y, dt)
     scale = (1 + dt * sum(abs(a) * op.h[d] ** -k * sum(abs(w) for w in op.weights[(k, order)])
+                          for k, d, a in op.terms)) * np.abs(x).max()
+    assert np.abs(y.cpu().numpy() - ref).max() <= 1e-13 * scale
+    y32 = torch.empty(op.n, dtype=torch.float32, device=dev)
+    psp.psp_matvec(s.handle, t32(x, dev), y32, dt)
+    assert np.abs(y32.cpu().numpy().astype(np.float64) - ref).max() <= 2e-6 * scale
+    s.close()
+
+
+def test_matvec_3d_full_size(dev):
+    """The 256^3 grid of the 3D workload (8th order, radius 5): the whole product against
+    the oracle's matrix-free stencil, FP64 and FP32, at the same rounding-scale bounds."""
+    import torch
+    from paper_1308_5626_gb300 import psp
+    w = inputs.c3(256, with_u0=False)
+    op = Operator(w.shape, w.order, w.terms)
+    dt = 1e-3
+    x = np.random.default_rng(11).standard_normal(op.n)
+    ref = op.apply_A(x, dt)
+    s = psp.Solver(w.shape, w.order, w.terms, w.b, 2, max_hist_cols=4)
+    y = torch.empty(op.n, dtype=torch.float64, device=dev)
+    psp.psp_matvec(s.handle, t64(x, dev), y, dt)
+    scale = (1 + dt * sum(abs(a) * op.h[d] ** -k * sum(abs(v) for v in op.weights[(k, w.order)])
                           for k, d, a in op.terms)) * np.abs(x).max()
     assert np.abs(y.cpu().numpy() - ref).max() <= 1e-13 * scale
     y32 = torch.empty(op.n, dtype=torch.float32, device=dev)

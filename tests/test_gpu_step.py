@@ -100,6 +100,38 @@ def test_matvec_placement(dev, w, precision, fuse):
     s.close()
 
 
+def _box3d():
+    """The 3D workload's operator (8th order, diffusion + hyperdiffusion, rho(L) dt = 100)
+    on a 128 x 16 x 12 box: x is whole tiles of 32 16-byte vectors and y whole tiles of 8
+    rows, so the cycle uses the z-marching tiled stencil instead of the folded matvec."""
+    import dataclasses
+    import numpy as np
+    base = inputs.c3(16, with_u0=False)
+    shape = (128, 16, 12)
+    u0 = inputs.lowpass_noise(shape, np.random.default_rng(31), 4.0)
+    return dataclasses.replace(base, name="c3_box_128x16x12", shape=shape, u0=u0, m=30)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_3d_tiled_stencil_steps(dev, precision):
+    w = _box3d()
+    op = Operator(w.shape, w.order, w.terms)
+    dt = _dt(w, op)
+    tol = 1e-12 if precision == 0 else 1e-10
+    bound = exact.condition_number(op, dt) * 2 * tol if precision == 0 else 1e-8
+    s = _solver(w, precision=precision)
+    u = t64(w.u0, dev)
+    un = w.u0
+    for step in range(2):
+        u, info = s.step(u, dt, tol)
+        ref = exact.solve_fourier(op, un, dt)
+        got = u.cpu().numpy()
+        assert info.status == 0
+        assert rel(got, ref) <= bound, (step, rel(got, ref), info.iters)
+        un = got
+    s.close()
+
+
 @pytest.mark.parametrize("w", [inputs.c1(1000), inputs.c3(12, kmax=3)], ids=lambda w: w.name)
 def test_iterations_follow_the_oracle(dev, w):
     from paper_1308_5626_gb300 import psp
