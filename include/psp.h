@@ -90,6 +90,9 @@ typedef struct {
                         Gram-Schmidt pass when every grid row is a whole number of 16-byte
                         vectors wider than the stencil halo; 0: as a kernel of its own.
                         Same arithmetic either way. */
+  int adjoint;       /* 0 (default): the handle solves with A = I - dt L.  1: with
+                        A^T = I - dt L^T (every stencil mirrored, w_j -> w_-j, exact on the
+                        periodic grid): the adjoint system of a step, for gradients. */
 } psp_opts;
 
 typedef struct {
@@ -208,10 +211,21 @@ psp_status psp_set_band(psp_handle h, const double *N_band);
 /* Copy the adopted N to the device array N_band (identity band if none is adopted). */
 psp_status psp_get_band(psp_handle h, double *N_band);
 
-/* y = N^{-1} v with the adopted N (the preconditioner solve of Algorithm 1), device
- * arrays of n elements; v and y may be the same array.  transpose must be 0. */
+/* y = N^{-1} v with the adopted N (the preconditioner solve of Algorithm 1), or
+ * y = N^{-T} v with transpose = 1 (the preconditioner of the adjoint system); device
+ * arrays of n elements; v and y may be the same array.  The first transposed solve after
+ * the adopted N changed factors N^T (synchronous); PSP_ERR_NUMERIC if that fails.  With
+ * no adopted N both are copies (N = I). */
 psp_status psp_apply_precond(psp_handle h, const double *v, double *y, int transpose);
 psp_status psp_apply_precond_f32(psp_handle h, const float *v, float *y, int transpose);
+
+/* y = L x (term < 0) or y = D_t x (0 <= term < nterms: term t of psp_create with unit
+ * alpha, i.e. h^-k times the central difference of order k along its direction), FP64
+ * device arrays of n elements that must not overlap.  On an adjoint handle L^T and D_t^T.
+ * With u^{n+1} = A^{-1} u^n, A = I - dt L, L = sum_t alpha_t D_t and an adjoint state
+ * lambda = A^{-T} g, the gradients of a loss with dL/du^{n+1} = g are lambda (u^n),
+ * lambda . L u^{n+1} (dt) and dt lambda . D_t u^{n+1} (alpha_t).  Synchronous. */
+psp_status psp_apply_L(psp_handle h, int term, const double *x, double *y);
 
 /* Stencil of L without dt: w_host[d*(2R+1) + (j+R)] is the weight of u(x + j h e_d) in
  * (L u)(x) for d < ndim and j in -R..R, R = *radius (host).  w_host holds 3*(2R+1)

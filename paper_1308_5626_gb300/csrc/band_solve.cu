@@ -617,6 +617,22 @@ __global__ void __launch_bounds__(512) k_tail(const int *active, const LevelAppl
   }
 }
 
+// N^T in band storage: bandT[i][p] = N^T(i, i+p-b) = N(i+p-b, i) = band[i+p-b][2b-p]
+// (zero where row i+p-b is outside [0, n)).
+__global__ void k_transpose_band(const double *__restrict__ band, double *__restrict__ bandT, int64_t n, int b) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int w = 2 * b + 1;
+  for (int p = 0; p < w; ++p) {
+    const int64_t r = i + p - b;
+    bandT[i * w + p] = (r >= 0 && r < n) ? band[r * w + (2 * b - p)] : 0.0;
+  }
+}
+
+void launch_transpose_band(const double *band, double *bandT, int64_t n, int b, cudaStream_t s) {
+  k_transpose_band<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(band, bandT, n, b);
+}
+
 // ---------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------
@@ -723,8 +739,9 @@ void BandSolver::bind(void *slot_mem, int slot) {
 }
 
 template <typename T, typename FS>
-static void bind_apply_t(const std::vector<LevelShape> &lv, int b, char *&p, const FS (&fac)[2],
-                         std::vector<LevelApply<T>> (&out)[2], LevelApply<T> *(&dev)[2]) {
+static void bind_apply_t(const std::vector<LevelShape> &lv, int b, char *&p, const FS (&fac)[BandSolver::kSlots],
+                         std::vector<LevelApply<T>> (&out)[BandSolver::kSlots],
+                         LevelApply<T> *(&dev)[BandSolver::kSlots]) {
   std::vector<LevelApply<T>> scratch(lv.size(), LevelApply<T>{});
   for (size_t l = 0; l < lv.size(); ++l) {
     LevelApply<T> &a = scratch[l];
@@ -735,7 +752,7 @@ static void bind_apply_t(const std::vector<LevelShape> &lv, int b, char *&p, con
     a.seprhs = carve<T>(p, (size_t)lv[l].G * b + 64);
     a.sol = carve<T>(p, (size_t)(lv[l].nb + 1) * b);
   }
-  for (int s = 0; s < 2; ++s) {
+  for (int s = 0; s < BandSolver::kSlots; ++s) {
     out[s] = scratch;
     for (size_t l = 0; l < lv.size(); ++l) {
       const auto &f = fac[s][l];
@@ -750,8 +767,8 @@ static void bind_apply_t(const std::vector<LevelShape> &lv, int b, char *&p, con
 
 void BandSolver::bind_apply(void *mem) {
   char *p = reinterpret_cast<char *>(mem);
-  const std::vector<LevelF64> f64[2] = {slots[0].f, slots[1].f};
-  const std::vector<LevelF32> f32[2] = {slots[0].h, slots[1].h};
+  const std::vector<LevelF64> f64[kSlots] = {slots[0].f, slots[1].f, slots[2].f};
+  const std::vector<LevelF32> f32[kSlots] = {slots[0].h, slots[1].h, slots[2].h};
   bind_apply_t<double>(levels, b, p, f64, app64, dev_app64);
   bind_apply_t<float>(levels, b, p, f32, app32, dev_app32);
   static bool attrs = false;

@@ -40,11 +40,13 @@ struct BandSolver {
     std::vector<LevelF32> h;
     std::vector<double *> nLo, nDi, nUp;   // separator systems (input of the next level)
   };
-  Slot slots[2];
-  std::vector<LevelApply<double>> app64[2];
-  std::vector<LevelApply<float>> app32[2];
-  LevelApply<double> *dev_app64[2] = {nullptr, nullptr};
-  LevelApply<float> *dev_app32[2] = {nullptr, nullptr};
+  // slots 0 and 1: the adopted and the candidate N; slot 2: N^T for the transposed solve
+  static constexpr int kSlots = 3;
+  Slot slots[kSlots];
+  std::vector<LevelApply<double>> app64[kSlots];
+  std::vector<LevelApply<float>> app32[kSlots];
+  LevelApply<double> *dev_app64[kSlots] = {nullptr, nullptr, nullptr};
+  LevelApply<float> *dev_app32[kSlots] = {nullptr, nullptr, nullptr};
 
   void plan(int64_t n, int b);
   // shared memory of the single-CTA kernel for levels first..last, elements of es bytes
@@ -61,5 +63,8 @@ struct BandSolver {
   void apply(int slot, const T *v, const double *scale, const int *active, OutRef<T> y, double *X, int mode,
              cudaStream_t s) const;
 };
+
+// bandT = N^T in the same band storage (n x (2b+1) FP64).
+void launch_transpose_band(const double *band, double *bandT, int64_t n, int b, cudaStream_t s);
 
 }  // namespace psp

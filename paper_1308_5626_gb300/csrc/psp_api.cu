@@ -109,7 +109,12 @@ struct psp_ctx {
   double *moments = nullptr;
   double *band_adopted = nullptr, *band_cand = nullptr;
   int *dev_int = nullptr;            // [0] factor failure, [1] singular rows
-  void *slot_mem[2] = {nullptr, nullptr};
+  void *slot_mem[BandSolver::kSlots] = {nullptr, nullptr, nullptr};
+  double *band_T = nullptr;          // N^T of the adopted N (transposed solve)
+  int adopted_version = 0;           // bumped whenever the adopted N changes
+  int t_version = -1;                // adopted_version that slot 2 (N^T) was factored for
+  // per-term stencils of L (unit alpha, h^-k folded in), for psp_apply_L
+  std::vector<std::pair<int, std::vector<double>>> term_w;
   void *apply_mem = nullptr;
   BandSolver bs;
 
@@ -289,6 +294,37 @@ double rate_of(double R_end, double beta, int k) {
   return std::pow(std::max(R_end, 1e-300) / beta, 1.0 / k);
 }
 
+// Slot 2 holds the factors of N^T for the adopted N (made on first use after a change).
+psp_status ensure_transposed(psp_ctx *h) {
+  if (h->t_version == h->adopted_version) return PSP_OK;
+  launch_transpose_band(h->band_adopted, h->band_T, h->geo.n, h->b, h->stream);
+  PSP_CUDA(cudaGetLastError());
+  psp_status s = factor_into(h, 2, h->band_T);
+  if (s != PSP_OK) return s;
+  h->t_version = h->adopted_version;
+  return PSP_OK;
+}
+
+// Coefficients of L (term < 0) or of one term's derivative with unit alpha (term >= 0), in
+// the stencil kernels' layout (centres folded into direction 0), without dt or identity.
+void set_L_coef(const psp_ctx *h, int term, double (*coef)[2 * kMaxR + 1]) {
+  for (int d = 0; d < 3; ++d)
+    for (int j = 0; j < 2 * kMaxR + 1; ++j) coef[d][j] = 0.0;
+  if (term < 0) {
+    for (int d = 0; d < h->geo.ndim; ++d)
+      for (int j = 0; j < 2 * kMaxR + 1; ++j) coef[d][j] = h->wdir[d][j];
+  } else {
+    const auto &tw = h->term_w[term];
+    for (int j = 0; j < 2 * kMaxR + 1; ++j) coef[tw.first][j] = tw.second[j];
+  }
+  double centre = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    centre += coef[d][kMaxR];
+    coef[d][kMaxR] = 0.0;
+  }
+  coef[0][kMaxR] = centre;
+}
+
 // Coefficients of A for psp_matvec, uploaded only when dt differs from the last call's.
 psp_status upload_api_coef(psp_ctx *h, double dt) {
   if (h->api_dt == dt) return PSP_OK;
@@ -315,6 +351,7 @@ psp_status psp_default_opts(psp_opts *o) {
   o->inner_tol = 1e-5;
   o->accept_rule = 1;
   o->fuse_matvec = 1;
+  o->adjoint = 0;
   return PSP_OK;
 }
 
@@ -327,7 +364,8 @@ psp_status psp_destroy(psp_handle h) {
       for (auto &e : b)
         if (e) cudaEventDestroy(e);
   void *dev[] = {h->V, h->Px, h->Py, h->Z, h->X, h->B, h->partial, h->st, h->api_st, h->moments,
-                 h->band_adopted, h->band_cand, h->dev_int, h->slot_mem[0], h->slot_mem[1], h->apply_mem,
+                 h->band_adopted, h->band_cand, h->dev_int, h->slot_mem[0], h->slot_mem[1], h->slot_mem[2],
+                 h->band_T, h->apply_mem,
                  h->dev_un, h->dev_unp1};
   for (void *p : dev)
     if (p) cudaFree(p);
@@ -384,9 +422,22 @@ psp_status psp_create(const psp_grid *grid, int order, const psp_term *terms, in
     }
     const int r = (tm.k - 1) / 2 + order / 2;
     const std::vector<double> w = central_weights(tm.k, order);
-    const double sc = tm.alpha * std::pow(h->h[tm.dir], -(double)tm.k);
-    for (int j = -r; j <= r; ++j) h->wdir[tm.dir][kMaxR + j] += sc * w[j + r];
+    const double hk = std::pow(h->h[tm.dir], -(double)tm.k);
+    const double sc = tm.alpha * hk;
+    std::vector<double> tw(2 * kMaxR + 1, 0.0);
+    for (int j = -r; j <= r; ++j) {
+      h->wdir[tm.dir][kMaxR + j] += sc * w[j + r];
+      tw[kMaxR + j] = hk * w[j + r];
+    }
+    h->term_w.emplace_back(tm.dir, std::move(tw));
     R = std::max(R, r);
+  }
+  if (o.adjoint) {
+    // A^T = I - dt L^T: on a periodic grid L^T applies every stencil mirrored, w_j -> w_-j
+    for (int d = 0; d < 3; ++d)
+      for (int j = 1; j <= kMaxR; ++j) std::swap(h->wdir[d][kMaxR + j], h->wdir[d][kMaxR - j]);
+    for (auto &tw : h->term_w)
+      for (int j = 1; j <= kMaxR; ++j) std::swap(tw.second[kMaxR + j], tw.second[kMaxR - j]);
   }
   for (int d = 0; d < grid->ndim; ++d)
     if (2 * R + 1 > nn[d]) { delete h; return fail(PSP_ERR_ARG, "every direction needs n >= 2R+1 (R: widest stencil radius)"); }
@@ -420,10 +471,11 @@ psp_status psp_create(const psp_grid *grid, int order, const psp_term *terms, in
   ok = ok && dalloc((void **)&h->moments, (size_t)n * (4 * b + 4) * 8);
   ok = ok && dalloc((void **)&h->band_adopted, (size_t)n * (2 * b + 1) * 8);
   ok = ok && dalloc((void **)&h->band_cand, (size_t)n * (2 * b + 1) * 8);
+  ok = ok && dalloc((void **)&h->band_T, (size_t)n * (2 * b + 1) * 8);
   ok = ok && dalloc((void **)&h->dev_int, 64);
   if (ok) {
     h->bs.plan(n, b);
-    for (int s = 0; s < 2 && ok; ++s) {
+    for (int s = 0; s < BandSolver::kSlots && ok; ++s) {
       ok = dalloc(&h->slot_mem[s], h->bs.slot_bytes());
       if (ok) h->bs.bind(h->slot_mem[s], s);
     }
@@ -517,6 +569,7 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
       const bool cycle_done = converged || (sm.R_end <= tol * sm.bnorm);
       if (!h->opts.accept_rule || cycle_done || h->rate_ref < 0.0 || r1 <= h->rate_ref) {
         h->adopted = h->cand;
+        h->adopted_version += 1;
         h->wait_len = 1;
         flags |= PSP_FLAG_CANDIDATE_ACCEPTED;
         PSP_CUDA(cudaMemcpyAsync(h->band_adopted, h->band_cand, (size_t)n * (2 * h->b + 1) * 8,
@@ -618,6 +671,19 @@ psp_status psp_matvec_f32(psp_handle h, const float *x, float *y, double dt) {
   return PSP_OK;
 }
 
+psp_status psp_apply_L(psp_handle h, int term, const double *x, double *y) {
+  if (!h || !x || !y) return fail(PSP_ERR_ARG, "NULL argument");
+  if (term >= (int)h->term_w.size()) return fail(PSP_ERR_ARG, "term index out of range");
+  set_L_coef(h, term, h->st_host->coef);
+  PSP_CUDA(cudaMemcpyAsync(h->api_st->coef, h->st_host->coef, sizeof(h->st_host->coef), cudaMemcpyHostToDevice,
+                           h->stream));
+  h->api_dt = NAN;   // api_st no longer holds A's coefficients
+  launch_stencil<double, double, double>(h->geo, fixed_in<double>(x), fixed_out<double>(y), h->api_st, nullptr, h->stream);
+  PSP_CUDA(cudaGetLastError());
+  PSP_CUDA(cudaStreamSynchronize(h->stream));
+  return PSP_OK;
+}
+
 psp_status psp_fit_band(psp_handle h, const double *Px, const double *Py, int64_t ld, int M, double *N_band,
                         int *singular_rows) {
   if (!h || !Px || !Py || !N_band) return fail(PSP_ERR_ARG, "NULL argument");
@@ -641,6 +707,7 @@ psp_status psp_set_band(psp_handle h, const double *N_band) {
   PSP_CUDA(cudaMemcpyAsync(h->band_adopted, N_band, bytes, cudaMemcpyDeviceToDevice, h->stream));
   PSP_CUDA(cudaStreamSynchronize(h->stream));
   h->adopted = slot;
+  h->adopted_version += 1;
   if (h->cand == slot) h->cand = -1;
   return PSP_OK;
 }
@@ -662,24 +729,34 @@ psp_status psp_get_band(psp_handle h, double *N_band) {
 
 psp_status psp_apply_precond(psp_handle h, const double *v, double *y, int transpose) {
   if (!h || !v || !y) return fail(PSP_ERR_ARG, "NULL argument");
-  if (transpose) return fail(PSP_ERR_ARG, "transposed solve is not available");
   if (h->adopted < 0) {
     if (v != y) PSP_CUDA(cudaMemcpyAsync(y, v, h->geo.n * 8, cudaMemcpyDeviceToDevice, h->stream));
     return PSP_OK;
   }
-  h->bs.apply<double>(h->adopted, v, nullptr, nullptr, fixed_out<double>(y), nullptr, 0, h->stream);
+  int slot = h->adopted;
+  if (transpose) {
+    psp_status ts = ensure_transposed(h);
+    if (ts != PSP_OK) return ts;
+    slot = 2;
+  }
+  h->bs.apply<double>(slot, v, nullptr, nullptr, fixed_out<double>(y), nullptr, 0, h->stream);
   PSP_CUDA(cudaGetLastError());
   return PSP_OK;
 }
 
 psp_status psp_apply_precond_f32(psp_handle h, const float *v, float *y, int transpose) {
   if (!h || !v || !y) return fail(PSP_ERR_ARG, "NULL argument");
-  if (transpose) return fail(PSP_ERR_ARG, "transposed solve is not available");
   if (h->adopted < 0) {
     if (v != y) PSP_CUDA(cudaMemcpyAsync(y, v, h->geo.n * 4, cudaMemcpyDeviceToDevice, h->stream));
     return PSP_OK;
   }
-  h->bs.apply<float>(h->adopted, v, nullptr, nullptr, fixed_out<float>(y), nullptr, 0, h->stream);
+  int slot = h->adopted;
+  if (transpose) {
+    psp_status ts = ensure_transposed(h);
+    if (ts != PSP_OK) return ts;
+    slot = 2;
+  }
+  h->bs.apply<float>(slot, v, nullptr, nullptr, fixed_out<float>(y), nullptr, 0, h->stream);
   PSP_CUDA(cudaGetLastError());
   return PSP_OK;
 }
@@ -732,6 +809,7 @@ psp_status psp_get_profile(psp_handle h, psp_profile *out, int reset) {
 psp_status psp_reset(psp_handle h) {
   if (!h) return fail(PSP_ERR_ARG, "NULL argument");
   h->adopted = -1;
+  h->adopted_version += 1;
   h->cand = -1;
   h->rate_ref = -1.0;
   h->wait = 0;

@@ -179,6 +179,21 @@ def c3(n: int = 256, kmax: float = 32.0, with_u0: bool = True) -> Workload:
                     b=3, m=50, steps=5, tol=1e-10, dt=None, rho_dt=100.0, u0=u0, seed=3)
 
 
+def c5(n: int = 512) -> Tuple[Workload, np.ndarray]:
+    """2D periodic anisotropic diffusion u_t = a_x u_xx + a_y u_yy, 6th order, rho(L) dt = 10,
+    10 steps (seed 5): the true coefficients a ~ U[0.5, 2] 1e-3 define the workload; the
+    returned perturbation factors (1 + 0.1 U[-1, 1]) give the coefficients at which a loss
+    against a target made with the true ones is differentiated."""
+    rng = np.random.default_rng(5)
+    a = rng.uniform(0.5, 2.0, 2) * 1e-3
+    u0 = gaussian_random_field((n, n), rng, power=-2.0)
+    factors = 1.0 + 0.1 * rng.uniform(-1.0, 1.0, 2)
+    terms = [Term(2, 0, float(a[0])), Term(2, 1, float(a[1]))]
+    w = Workload("c5_2d_aniso_diff_%dx%d" % (n, n), (n, n), 6, terms, b=4, m=30, steps=10, tol=1e-12,
+                 dt=None, rho_dt=10.0, u0=u0, seed=5)
+    return w, factors
+
+
 WORKLOADS = {"c1": c1, "c2": c2, "c3": c3}
 
 

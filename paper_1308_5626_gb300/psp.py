@@ -40,7 +40,7 @@ class psp_term(ctypes.Structure):
 class psp_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("intercept", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("max_hist_cols", ctypes.c_int), ("inner_tol", ctypes.c_double), ("accept_rule", ctypes.c_int),
-                ("fuse_matvec", ctypes.c_int)]
+                ("fuse_matvec", ctypes.c_int), ("adjoint", ctypes.c_int)]
 
 
 class psp_step_info(ctypes.Structure):
@@ -67,6 +67,7 @@ _SIGS = {
     "psp_step_host": [_VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(psp_step_info)],
     "psp_matvec": [_VP, _VP, _VP, ctypes.c_double],
     "psp_matvec_f32": [_VP, _VP, _VP, ctypes.c_double],
+    "psp_apply_L": [_VP, ctypes.c_int, _VP, _VP],
     "psp_fit_band": [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_int)],
     "psp_fit_band_f32": [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_int)],
     "psp_set_band": [_VP, _VP],
@@ -173,6 +174,11 @@ def psp_matvec(h, x, y, dt: float) -> None:
     _check(fn(h, _ptr(x), _ptr(y), float(dt)), "psp_matvec")
 
 
+def psp_apply_L(h, term: int, x, y) -> None:
+    """y = L x (term < 0) or the unit-alpha derivative of term `term` (FP64 tensors)."""
+    _check(lib().psp_apply_L(h, int(term), _ptr(x), _ptr(y)), "psp_apply_L")
+
+
 def psp_fit_band(h, Px, Py, N_band, ld: Optional[int] = None, M: Optional[int] = None) -> int:
     """Px, Py: torch tensors shaped (M, ld) (row c = history column c); returns singular rows."""
     M = int(Px.shape[0]) if M is None else int(M)
@@ -248,12 +254,13 @@ class Solver:
     """Owns one psp handle for a workload; vectors are torch CUDA float64 tensors."""
 
     def __init__(self, shape, order, terms, b, m, precision=PSP_FP64, intercept=1, max_restarts=200,
-                 max_hist_cols=0, inner_tol=1e-5, accept_rule=1, fuse_matvec=1, stream=None):
+                 max_hist_cols=0, inner_tol=1e-5, accept_rule=1, fuse_matvec=1, adjoint=0, stream=None):
         import torch
         o = psp_default_opts()
         o.precision, o.intercept, o.max_restarts = int(precision), int(intercept), int(max_restarts)
         o.max_hist_cols, o.inner_tol, o.accept_rule = int(max_hist_cols), float(inner_tol), int(accept_rule)
         o.fuse_matvec = int(fuse_matvec)
+        o.adjoint = int(adjoint)
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s
         self.shape = tuple(int(v) for v in shape)
