@@ -55,6 +55,7 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-standalone", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--nx", type=int, default=1024, help="grid points per direction (default: the full workload)")
     return ap.parse_args()
 
@@ -331,6 +332,63 @@ def _standalone(w, device, hbm_peak, fp64_peak_tflops):
     return out
 
 
+def _adjoint_line(device):
+    """The differentiable step on the 512 x 512 2D diffusion workload (10 steps): time of the
+    forward rollout and of forward + backward (adjoint solves and gradient stencils) in the
+    FP64 and the mixed form, and the mixed gradient's relative difference from the FP64 one."""
+    import torch
+    from paper_1308_5626_gb300 import autograd, inputs, psp
+    w, factors = inputs.c5(512)
+    # dt from rho(L) dt = 10, rho(L) the largest |eigenvalue| of the library's own stencil of L
+    # (psp_get_stencil) over the grid's Fourier modes
+    import numpy as np
+    s = psp.Solver(w.shape, w.order, w.terms, w.b, 2, max_hist_cols=4)
+    wst, R = psp.psp_get_stencil(s.handle)
+    s.close()
+    lam = 0.0
+    for d, nd in enumerate(w.shape):
+        th = 2.0 * np.pi * np.arange(nd) / nd
+        ld = sum(wst[d][j + R] * np.exp(1j * j * th) for j in range(-R, R + 1))
+        shp = [1] * len(w.shape)
+        shp[len(w.shape) - 1 - d] = nd
+        lam = lam + ld.reshape(shp)
+    dt = w.rho_dt / float(np.abs(lam).max())
+    alphas = [t.alpha * f for t, f in zip(w.terms, factors)]
+    target = torch.zeros(w.n, dtype=torch.float64, device=device)
+    out = {"workload": w.name, "steps": w.steps}
+    grads = {}
+    for name, prec, tol in (("fp64", psp.PSP_FP64, 1e-12), ("mixed", psp.PSP_MIXED, 1e-10)):
+        prob = autograd.Problem(w.shape, w.order, [(t.k, t.dir) for t in w.terms], w.b, w.m, precision=prec, tol=tol)
+        u0 = torch.tensor(w.u0, dtype=torch.float64, device=device)
+        for _ in range(2):   # warm-up: handles, graphs, the first fits
+            u = torch.tensor(w.u0, dtype=torch.float64, device=device, requires_grad=True)
+            dtt = torch.tensor(dt, dtype=torch.float64, device=device, requires_grad=True)
+            al = torch.tensor(alphas, dtype=torch.float64, device=device, requires_grad=True)
+            ((autograd.rollout(u, dtt, al, prob, w.steps) - target) ** 2).sum().backward()
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        with torch.no_grad():
+            autograd.rollout(u0, torch.tensor(dt, dtype=torch.float64, device=device),
+                             torch.tensor(alphas, dtype=torch.float64, device=device), prob, w.steps)
+        torch.cuda.synchronize(device)
+        t_fwd = time.perf_counter() - t0
+        u = torch.tensor(w.u0, dtype=torch.float64, device=device, requires_grad=True)
+        dtt = torch.tensor(dt, dtype=torch.float64, device=device, requires_grad=True)
+        al = torch.tensor(alphas, dtype=torch.float64, device=device, requires_grad=True)
+        t0 = time.perf_counter()
+        ((autograd.rollout(u, dtt, al, prob, w.steps) - target) ** 2).sum().backward()
+        torch.cuda.synchronize(device)
+        t_both = time.perf_counter() - t0
+        grads[name] = torch.cat([al.grad, dtt.grad.reshape(1)]).cpu()
+        out[name] = {"forward_ms": t_fwd * 1e3, "forward_backward_ms": t_both * 1e3}
+        prob.close()
+    g64, g32 = grads["fp64"], grads["mixed"]
+    out["mixed_grad_rel_diff"] = float((g32 - g64).abs().max() / g64.abs().max())
+    out["note"] = ("host wall clock around a 10-step rollout (no_grad) and around rollout + backward of "
+                   "||u^10||^2; gradients w.r.t. the two coefficients and dt")
+    return out
+
+
 def _e2e(w, precision, steps, device):
     """Same metric through the C ABI with host buffers: psp_step_host copies u^n from pinned
     host memory to the device and u^{n+1} back every step."""
@@ -502,6 +560,9 @@ def main():
     standalone = None
     if not a.no_standalone and rank == 0:
         standalone = _standalone(w, device, hbm_peak, FP64_PEAK_TFLOPS)
+    adj = None
+    if not a.no_adjoint and rank == 0:
+        adj = _adjoint_line(device)
 
     if rank != 0:
         if world > 1:
@@ -568,6 +629,7 @@ def main():
                    "iteration, in a separate timed region of the same %d steps" % a.steps,
          "ms_per_step_with_events": prof_ms},
         "standalone": standalone,
+        "adjoint": adj,
         "cpu_baseline": cpu, "clocks": clk,
     }
     if fp64:
