@@ -141,6 +141,18 @@ psp_status psp_default_opts(psp_opts *opts);
 psp_status psp_create(const psp_grid *grid, int order, const psp_term *terms, int nterms,
                       int b, int m, const psp_opts *opts, void *cuda_stream, psp_handle *out);
 
+/*
+ * A handle whose operator is an explicit banded matrix instead of the stencil: the paper's
+ * mock test (Results section: a random seven-diagonal A, diagonally dominant, u^n = 1..n).
+ * A_band is a device array of n x (2w+1) doubles, row-major band storage
+ * A(i, i+p-w) = A_band[i (2w+1) + p] (entries outside the matrix ignored), copied into the
+ * handle (FP64 and FP32).  psp_step then solves A u_np1 = u_n (dt is ignored) with the same
+ * restarted PSP-GMRES, history and band fit of half-width b; psp_matvec applies A, and with
+ * opts->adjoint A^T.  psp_apply_L returns PSP_ERR_ARG (there is no L).  w in 1..64.
+ */
+psp_status psp_create_banded(int64_t n, const double *A_band, int w, int b, int m, const psp_opts *opts,
+                             void *cuda_stream, psp_handle *out);
+
 /* Release every resource of the handle.  NULL is accepted. */
 psp_status psp_destroy(psp_handle h);
 

@@ -633,6 +633,16 @@ void launch_transpose_band(const double *band, double *bandT, int64_t n, int b, 
   k_transpose_band<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(band, bandT, n, b);
 }
 
+__global__ void k_to_f32(const double *__restrict__ in, float *__restrict__ out, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+void launch_to_f32(const double *in, float *out, int64_t count, cudaStream_t s) {
+  const int64_t g = std::min<int64_t>((count + 255) / 256, 4096);
+  k_to_f32<<<(unsigned)std::max<int64_t>(g, 1), 256, 0, s>>>(in, out, count);
+}
+
 // ---------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------

@@ -66,5 +66,7 @@ struct BandSolver {
 
 // bandT = N^T in the same band storage (n x (2b+1) FP64).
 void launch_transpose_band(const double *band, double *bandT, int64_t n, int b, cudaStream_t s);
+// out = (float) in, count elements.
+void launch_to_f32(const double *in, float *out, int64_t count, cudaStream_t s);
 
 }  // namespace psp

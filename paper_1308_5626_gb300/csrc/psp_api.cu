@@ -111,6 +111,8 @@ struct psp_ctx {
   int *dev_int = nullptr;            // [0] factor failure, [1] singular rows
   void *slot_mem[BandSolver::kSlots] = {nullptr, nullptr, nullptr};
   double *band_T = nullptr;          // N^T of the adopted N (transposed solve)
+  double *Ab = nullptr;              // explicit banded operator (psp_create_banded), FP64
+  float *Ab32 = nullptr;             // ... and its FP32 copy
   int adopted_version = 0;           // bumped whenever the adopted N changes
   int t_version = -1;                // adopted_version that slot 2 (N^T) was factored for
   // per-term stencils of L (unit alpha, h^-k folded in), for psp_apply_L
@@ -355,6 +357,50 @@ psp_status psp_default_opts(psp_opts *o) {
   return PSP_OK;
 }
 
+psp_status psp_create_banded(int64_t n, const double *A_band, int w, int b, int m, const psp_opts *opts,
+                             void *cuda_stream, psp_handle *out) {
+  if (!A_band || !out) return fail(PSP_ERR_ARG, "NULL argument");
+  if (w < 1 || w > 64) return fail(PSP_ERR_ARG, "band half-width w must be in 1..64");
+  if (n < 3 || n < 2 * (int64_t)w + 1) return fail(PSP_ERR_ARG, "need n >= max(3, 2w+1)");
+  psp_opts o;
+  psp_default_opts(&o);
+  if (opts) o = *opts;
+  const int adjoint = o.adjoint;
+  o.adjoint = 0;
+  o.fuse_matvec = 0;
+  // a 1D handle whose placeholder stencil (a zero-coefficient second difference) the banded
+  // operator replaces: the solver, history, fit and preconditioner are the same
+  psp_grid g{};
+  g.ndim = 1;
+  g.n[0] = n;
+  g.n[1] = g.n[2] = 1;
+  g.length[0] = g.length[1] = g.length[2] = 1.0;
+  psp_term t{2, 0, 0.0};
+  psp_handle h = nullptr;
+  psp_status s = psp_create(&g, 2, &t, 1, b, m, &o, cuda_stream, &h);
+  if (s != PSP_OK) return s;
+  h->opts.adjoint = adjoint;
+  const int64_t cnt = n * (2 * w + 1);
+  if (cudaMalloc((void **)&h->Ab, cnt * 8) != cudaSuccess || cudaMalloc((void **)&h->Ab32, cnt * 4) != cudaSuccess) {
+    cudaGetLastError();
+    psp_destroy(h);
+    return fail(PSP_ERR_OOM, "banded operator storage");
+  }
+  if (adjoint) launch_transpose_band(A_band, h->Ab, n, w, h->stream);
+  else cudaMemcpyAsync(h->Ab, A_band, cnt * 8, cudaMemcpyDeviceToDevice, h->stream);
+  launch_to_f32(h->Ab, h->Ab32, cnt, h->stream);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    psp_destroy(h);
+    return fail(PSP_ERR_CUDA, "banded operator upload");
+  }
+  h->geo.band_w = w;
+  h->geo.Ab = h->Ab;
+  h->geo.Ab32 = h->Ab32;
+  h->fused = false;
+  *out = h;
+  return PSP_OK;
+}
+
 psp_status psp_destroy(psp_handle h) {
   if (!h) return PSP_OK;
   for (auto &g : h->graph)
@@ -365,7 +411,7 @@ psp_status psp_destroy(psp_handle h) {
         if (e) cudaEventDestroy(e);
   void *dev[] = {h->V, h->Px, h->Py, h->Z, h->X, h->B, h->partial, h->st, h->api_st, h->moments,
                  h->band_adopted, h->band_cand, h->dev_int, h->slot_mem[0], h->slot_mem[1], h->slot_mem[2],
-                 h->band_T, h->apply_mem,
+                 h->band_T, h->Ab, h->Ab32, h->apply_mem,
                  h->dev_un, h->dev_unp1};
   for (void *p : dev)
     if (p) cudaFree(p);
@@ -673,6 +719,7 @@ psp_status psp_matvec_f32(psp_handle h, const float *x, float *y, double dt) {
 
 psp_status psp_apply_L(psp_handle h, int term, const double *x, double *y) {
   if (!h || !x || !y) return fail(PSP_ERR_ARG, "NULL argument");
+  if (h->geo.band_w > 0) return fail(PSP_ERR_ARG, "an explicit banded operator has no L");
   if (term >= (int)h->term_w.size()) return fail(PSP_ERR_ARG, "term index out of range");
   set_L_coef(h, term, h->st_host->coef);
   PSP_CUDA(cudaMemcpyAsync(h->api_st->coef, h->st_host->coef, sizeof(h->st_host->coef), cudaMemcpyHostToDevice,

@@ -11,6 +11,11 @@ struct Geometry {
   int nx, ny, nz;
   int64_t n;
   int R;   // stencil radius (max over directions)
+  // explicit banded operator (psp_create_banded): A in row-major band storage with half-width
+  // band_w, A(i, i+p-band_w) = Ab[i (2 band_w + 1) + p]; band_w == 0: the stencil operator
+  int band_w = 0;
+  const double *Ab = nullptr;
+  const float *Ab32 = nullptr;
 };
 
 // Output array that is either a fixed pointer or the ring column selected at run time by

@@ -194,13 +194,15 @@ __global__ void __launch_bounds__(kThreads) k_stencil_vec(InRef<T> xref, OutRef<
 // Restart of Algorithm 1 in FP64: AX = A X_0, r = B - AX; store the history pair
 // (X_0, AX) in the ring column hist_count, V~(:,1) = r (normalised lazily through
 // sigma[0] = 1/||r||), G(1) = ||r||; ||B|| sets the step bound eps_abs = tol ||B||.
+// NDIM == 0: the explicit banded operator (Ab, half-width bw) instead of the stencil.
 template <typename TH, typename TV, int NDIM, int R>
 __global__ void __launch_bounds__(kThreads) k_restart(const double *__restrict__ X,
                                                       const double *__restrict__ B, TH *Px, TH *Py,
                                                       int64_t ldh, TV *V1, DevState *st, double *partial,
-                                                      int nx, int ny, int nz, int mixed) {
+                                                      int nx, int ny, int nz, int mixed,
+                                                      const double *__restrict__ Ab, int bw) {
   double c[3][2 * R + 1];
-  load_coef<double, R>(st, c);
+  if (NDIM > 0) load_coef<double, R>(st, c);
   const int col = st->hist_count;
   TH *px = ring_col(Px, ldh, col, st->mmax);
   TH *py = ring_col(Py, ldh, col, st->mmax);
@@ -212,7 +214,16 @@ __global__ void __launch_bounds__(kThreads) k_restart(const double *__restrict__
     const int rem = i - iz * plane;
     const int iy = rem / nx;
     const int ix = rem - iy * nx;
-    double ax = stencil_point<double, NDIM, R, double>(X, c, ix, iy, iz, nx, ny, nz);
+    double ax;
+    if constexpr (NDIM == 0) {
+      ax = 0.0;
+      for (int p = 0; p <= 2 * bw; ++p) {
+        const int j = i + p - bw;
+        if (j >= 0 && j < n) ax += Ab[(int64_t)i * (2 * bw + 1) + p] * X[j];
+      }
+    } else {
+      ax = stencil_point<double, NDIM, R, double>(X, c, ix, iy, iz, nx, ny, nz);
+    }
     double b = B[i];
     double r = b - ax;
     px[i] = (TH)X[i];
@@ -498,11 +509,40 @@ static int vec_grid(int64_t nvec) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((nvec + kThreads - 1) / kThreads, resident));
 }
 
+// y = A (s x) for the explicit banded operator, one row per thread (xcopy as for the stencil).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_band_matvec(const T *__restrict__ Ab, int bw, InRef<T> xref, OutRef<T> yref,
+                                                         OutRef<T> xcopy, const double *scale, int64_t n,
+                                                         const int *active) {
+  if (active && *active == 0) return;
+  const T *__restrict__ x = xref.get();
+  T *y = yref.get();
+  T *xc = xcopy.base ? xcopy.get() : nullptr;
+  const T sc = scale ? (T)(*scale) : (T)1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T acc = (T)0;
+    for (int p = 0; p <= 2 * bw; ++p) {
+      const int64_t j = i + p - bw;
+      if (j >= 0 && j < n) acc += Ab[i * (2 * bw + 1) + p] * x[j];
+    }
+    y[i] = sc * acc;
+    if (xc) xc[i] = sc * x[i];
+  }
+}
+
 template <typename TI, typename TO, typename TC>
 void launch_stencil(const Geometry &g, InRef<TI> x, OutRef<TO> y, const DevState *st, const int *active,
                     cudaStream_t s, OutRef<TO> xcopy, const double *scale) {
   constexpr bool same = std::is_same<TI, TO>::value && std::is_same<TI, TC>::value;
   if constexpr (same) {
+    if (g.band_w > 0) {
+      const TI *Ab = nullptr;
+      if constexpr (std::is_same<TI, float>::value) Ab = g.Ab32;
+      else Ab = g.Ab;
+      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((g.n + kThreads - 1) / kThreads, 4096));
+      k_band_matvec<TI><<<grid, kThreads, 0, s>>>(Ab, g.band_w, x, y, xcopy, scale, g.n, active);
+      return;
+    }
     constexpr int W = SVec<TI>::W;
     // vector path: rows split into whole aligned vectors, and more vectors per row than
     // halo vectors (so one periodic wrap suffices)
@@ -538,9 +578,14 @@ template <typename TH, typename TV>
 void launch_restart(const Geometry &g, const double *X, const double *B, TH *Px, TH *Py, int64_t ldh,
                     TV *V1, DevState *st, double *partial, int mixed, cudaStream_t s) {
   const int grid = reduce_grid(g.n);
+  if (g.band_w > 0) {
+    k_restart<TH, TV, 0, 1><<<grid, kThreads, 0, s>>>(X, B, Px, Py, ldh, V1, st, partial, g.nx, g.ny, g.nz, mixed,
+                                                     g.Ab, g.band_w);
+    return;
+  }
   PSP_DISPATCH_NDIM(g.ndim, PSP_DISPATCH_R(g.R, (k_restart<TH, TV, DD, RR><<<grid, kThreads, 0, s>>>(
                                                     X, B, Px, Py, ldh, V1, st, partial, g.nx, g.ny,
-                                                    g.nz, mixed))));
+                                                    g.nz, mixed, nullptr, 0))));
 }
 
 template void launch_stencil<double, double, double>(const Geometry &, InRef<double>, OutRef<double>,

@@ -270,3 +270,18 @@ def mock_seven_diagonal(n: int, seed: int) -> np.ndarray:
                 A[i, j] = vals[i]
     A[np.arange(n), np.arange(n)] = 1.0 + np.abs(A).sum(axis=1)
     return A
+
+
+def dense_to_band(A: np.ndarray, w: int) -> np.ndarray:
+    """Row-major band storage band[i, p] = A(i, i + p - w) (zero outside the matrix)."""
+    n = A.shape[0]
+    band = np.zeros((n, 2 * w + 1))
+    for p in range(2 * w + 1):
+        off = p - w
+        lo, hi = max(0, -off), min(n, n - off)
+        band[lo:hi, p] = A[np.arange(lo, hi), np.arange(lo, hi) + off]
+    return band
+
+
+# the sizes of the paper's mock test (Results section)
+MOCK_SIZES = (20, 80, 150, 350, 700)

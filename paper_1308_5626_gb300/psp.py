@@ -63,6 +63,8 @@ _SIGS = {
     "psp_create": [ctypes.POINTER(psp_grid), ctypes.c_int, ctypes.POINTER(psp_term), ctypes.c_int, ctypes.c_int,
                    ctypes.c_int, ctypes.POINTER(psp_opts), _VP, ctypes.POINTER(_VP)],
     "psp_destroy": [_VP],
+    "psp_create_banded": [ctypes.c_int64, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(psp_opts), _VP,
+                          ctypes.POINTER(_VP)],
     "psp_step": [_VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(psp_step_info)],
     "psp_step_host": [_VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(psp_step_info)],
     "psp_matvec": [_VP, _VP, _VP, ctypes.c_double],
@@ -250,17 +252,29 @@ def psp_get_profile(h, reset: bool = False) -> dict:
 # convenience: a handle bound to torch tensors
 # --------------------------------------------------------------------------------------
 
+def _opts(precision, intercept, max_restarts, max_hist_cols, inner_tol, accept_rule, fuse_matvec, adjoint):
+    o = psp_default_opts()
+    o.precision, o.intercept, o.max_restarts = int(precision), int(intercept), int(max_restarts)
+    o.max_hist_cols, o.inner_tol, o.accept_rule = int(max_hist_cols), float(inner_tol), int(accept_rule)
+    o.fuse_matvec, o.adjoint = int(fuse_matvec), int(adjoint)
+    return o
+
+
+def psp_create_banded(n: int, A_band, w: int, b: int, m: int, opts: psp_opts, stream: int = 0):
+    """Handle for an explicit banded operator (A_band: device float64 tensor, n x (2w+1))."""
+    out = _VP()
+    _check(lib().psp_create_banded(int(n), _ptr(A_band), int(w), int(b), int(m), ctypes.byref(opts),
+                                   _VP(stream), ctypes.byref(out)), "psp_create_banded")
+    return out
+
+
 class Solver:
     """Owns one psp handle for a workload; vectors are torch CUDA float64 tensors."""
 
     def __init__(self, shape, order, terms, b, m, precision=PSP_FP64, intercept=1, max_restarts=200,
                  max_hist_cols=0, inner_tol=1e-5, accept_rule=1, fuse_matvec=1, adjoint=0, stream=None):
         import torch
-        o = psp_default_opts()
-        o.precision, o.intercept, o.max_restarts = int(precision), int(intercept), int(max_restarts)
-        o.max_hist_cols, o.inner_tol, o.accept_rule = int(max_hist_cols), float(inner_tol), int(accept_rule)
-        o.fuse_matvec = int(fuse_matvec)
-        o.adjoint = int(adjoint)
+        o = _opts(precision, intercept, max_restarts, max_hist_cols, inner_tol, accept_rule, fuse_matvec, adjoint)
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s
         self.shape = tuple(int(v) for v in shape)
@@ -269,6 +283,21 @@ class Solver:
             self.n *= v
         self.b = int(b)
         self.handle = psp_create(self.shape, order, terms, b, m, o, int(s.cuda_stream))
+
+    @classmethod
+    def banded(cls, A_band, w, b, m, precision=PSP_FP64, intercept=1, max_restarts=200, max_hist_cols=0,
+               inner_tol=1e-5, accept_rule=1, adjoint=0, stream=None):
+        """A solver whose operator is the explicit banded matrix A_band (device float64, n x (2w+1))."""
+        import torch
+        obj = cls.__new__(cls)
+        o = _opts(precision, intercept, max_restarts, max_hist_cols, inner_tol, accept_rule, 0, adjoint)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        obj.stream = s
+        obj.n = A_band.numel() // (2 * int(w) + 1)
+        obj.shape = (obj.n,)
+        obj.b = int(b)
+        obj.handle = psp_create_banded(obj.n, A_band.contiguous(), w, b, m, o, int(s.cuda_stream))
+        return obj
 
     def step(self, u_n, dt, tol, out=None, allow_noconv=False):
         import torch
