@@ -56,6 +56,7 @@ def _args():
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-standalone", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-e1", action="store_true")
     ap.add_argument("--nx", type=int, default=1024, help="grid points per direction (default: the full workload)")
     return ap.parse_args()
 
@@ -389,6 +390,30 @@ def _adjoint_line(device):
     return out
 
 
+def _e1_line(device):
+    """The paper's mock test (Results section): for each of its sizes, a seeded seven-diagonal
+    diagonally dominant A (explicit banded operator), u^n = (1..n), d = 1, restart 10, relative
+    tolerance 1e-10: iterations of step 1 (N = I, plain restarted GMRES) and of step 2 (the
+    fitted tridiagonal N tried on its first cycle, kept if it converges at least as fast)."""
+    import torch
+    from paper_1308_5626_gb300 import inputs, psp
+    rows = []
+    for n in inputs.MOCK_SIZES:
+        A = inputs.mock_seven_diagonal(n, seed=n)
+        band = torch.tensor(inputs.dense_to_band(A, 3).reshape(-1), dtype=torch.float64, device=device)
+        s = psp.Solver.banded(band, 3, 1, 10)
+        u = torch.arange(1, n + 1, dtype=torch.float64, device=device)
+        its = []
+        for _ in range(2):
+            _, info = s.step(u, 1.0, 1e-10)
+            its.append((int(info.iters), bool(info.flags & psp.PSP_FLAG_CANDIDATE_ACCEPTED)))
+        s.close()
+        rows.append({"n": n, "gmres_iters": its[0][0], "psp_iters": its[1][0], "candidate_kept": its[1][1]})
+    return {"rows": rows,
+            "paper_context": "the paper's figure: about 40 -> 30 iterations at n = 20 and about 400 -> 200 at "
+                             "n = 700 (its restart length and tolerance are not stated)"}
+
+
 def _e2e(w, precision, steps, device):
     """Same metric through the C ABI with host buffers: psp_step_host copies u^n from pinned
     host memory to the device and u^{n+1} back every step."""
@@ -563,6 +588,9 @@ def main():
     adj = None
     if not a.no_adjoint and rank == 0:
         adj = _adjoint_line(device)
+    e1 = None
+    if not a.no_e1 and rank == 0:
+        e1 = _e1_line(device)
 
     if rank != 0:
         if world > 1:
@@ -630,6 +658,7 @@ def main():
          "ms_per_step_with_events": prof_ms},
         "standalone": standalone,
         "adjoint": adj,
+        "mock_test": e1,
         "cpu_baseline": cpu, "clocks": clk,
     }
     if fp64:
