@@ -368,16 +368,20 @@ __device__ __forceinline__ void mv(T (&y)[B], const T *M, int i, int G, int g, c
 // elimination y_i = f_i - Mul_i y_{i-1}, back substitution x_i = Minv_i (y_i - Up_i x_{i+1})
 // (both in place in f); p = x goes to L.p (group-interleaved), and the separator terms of
 // the next level to cR, cL and seprhs.
+// The factor blocks are read at stride fG and index fg (the level's G and g in global memory,
+// or the CTA's group count and the thread's slot when staged in shared memory); the outputs
+// always use G and g.
 template <typename T, int B, int Q, bool RO>
-__device__ __forceinline__ void down_group(const LevelApply<T> &L, int g, T (&f)[Q][B], const T (&sep)[B]) {
+__device__ __forceinline__ void down_group(const LevelApply<T> &L, int g, T (&f)[Q][B], const T (&sep)[B], int fG,
+                                           int fg) {
   const int G = L.G;
 #pragma unroll
-  for (int i = 1; i < Q; ++i) mv_sub<T, B, RO>(f[i], L.Mul, i, G, g, f[i - 1]);
+  for (int i = 1; i < Q; ++i) mv_sub<T, B, RO>(f[i], L.Mul, i, fG, fg, f[i - 1]);
 #pragma unroll
   for (int i = Q - 1; i >= 0; --i) {
-    if (i < Q - 1) mv_sub<T, B, RO>(f[i], L.Up, i, G, g, f[i + 1]);
+    if (i < Q - 1) mv_sub<T, B, RO>(f[i], L.Up, i, fG, fg, f[i + 1]);
     T x[B];
-    mv<T, B, RO>(x, L.Minv, i, G, g, f[i]);
+    mv<T, B, RO>(x, L.Minv, i, fG, fg, f[i]);
 #pragma unroll
     for (int r = 0; r < B; ++r) f[i][r] = x[r];
   }
@@ -388,13 +392,13 @@ __device__ __forceinline__ void down_group(const LevelApply<T> &L, int g, T (&f)
   if (G > 1) {
     if (g < G - 1) {
       T c[B];
-      mv<T, B, RO>(c, L.LoSep, 0, G, g, f[Q - 1]);
+      mv<T, B, RO>(c, L.LoSep, 0, fG, fg, f[Q - 1]);
 #pragma unroll
       for (int r = 0; r < B; ++r) { L.cR[g * B + r] = -c[r]; L.seprhs[g * B + r] = sep[r]; }
     }
     if (g > 0) {
       T c[B];
-      mv<T, B, RO>(c, L.UpSepPrev, 0, G, g, f[0]);
+      mv<T, B, RO>(c, L.UpSepPrev, 0, fG, fg, f[0]);
 #pragma unroll
       for (int r = 0; r < B; ++r) L.cL[g * B + r] = -c[r];
     }
@@ -404,7 +408,7 @@ __device__ __forceinline__ void down_group(const LevelApply<T> &L, int g, T (&f)
 // Up sweep of group g: x_i = p_i - W_i sl - V_i sr (independent blocks); out(i, r)
 // receives interior block i (i < Q) and the separator block (i == Q, only for g < G-1).
 template <typename T, int B, int Q, bool RO, typename Out>
-__device__ __forceinline__ void up_group(const LevelApply<T> &L, int g, const T *solnext, Out out) {
+__device__ __forceinline__ void up_group(const LevelApply<T> &L, int g, const T *solnext, Out out, int fG, int fg) {
   const int G = L.G;
   T sl[B], sr[B];
 #pragma unroll
@@ -418,8 +422,8 @@ __device__ __forceinline__ void up_group(const LevelApply<T> &L, int g, const T 
 #pragma unroll
     for (int r = 0; r < B; ++r) x[r] = L.p[gi(i, r, G, g, B)];
     if (G > 1) {
-      mv_sub<T, B, RO>(x, L.W, i, G, g, sl);
-      mv_sub<T, B, RO>(x, L.Vs, i, G, g, sr);
+      mv_sub<T, B, RO>(x, L.W, i, fG, fg, sl);
+      mv_sub<T, B, RO>(x, L.Vs, i, fG, fg, sr);
     }
 #pragma unroll
     for (int r = 0; r < B; ++r) out(i, r, x[r]);
@@ -435,7 +439,8 @@ constexpr int kQ = 4;            // ... on the levels above
 
 // Level >= 1 down: right-hand side of block j = prev.seprhs[j] + prev.cR[j] + prev.cL[j+1].
 template <typename T, int B, bool RO>
-__device__ __forceinline__ void down_level_group(const LevelApply<T> &L, const LevelApply<T> &P, int g) {
+__device__ __forceinline__ void down_level_group(const LevelApply<T> &L, const LevelApply<T> &P, int g, int fG,
+                                                 int fg) {
   const int G = L.G;
   T f[kQ][B], sep[B];
 #pragma unroll
@@ -449,41 +454,101 @@ __device__ __forceinline__ void down_level_group(const LevelApply<T> &L, const L
       else sep[r] = v;
     }
   }
-  down_group<T, B, kQ, RO>(L, g, f, sep);
+  down_group<T, B, kQ, RO>(L, g, f, sep, fG, fg);
 }
 
 template <typename T, int B, bool RO>
-__device__ __forceinline__ void up_level_group(const LevelApply<T> &L, const T *solnext, int g) {
+__device__ __forceinline__ void up_level_group(const LevelApply<T> &L, const T *solnext, int g, int fG, int fg) {
   T *sol = L.sol;
   const int nb = L.nb;
   auto out = [&](int i, int r, T v) {
     const int j = g * (kQ + 1) + i;
     if (j < nb) sol[j * B + r] = v;
   };
-  up_group<T, B, kQ, RO>(L, g, solnext, out);
+  up_group<T, B, kQ, RO>(L, g, solnext, out, fG, fg);
 }
 
-constexpr int kGroupsPerCta = 64;
 constexpr int kMaxLevels = 24;
 constexpr int kTailSmem = 200 * 1024;   // shared memory of the single-CTA top levels
 
-// Level 0 down: stage the CTA's rows of v (times *scale) in shared memory, one group per thread.
+// The factor blocks a CTA's groups read are staged in shared memory before the sweeps:
+// every thread issues asynchronous copies (cp.async, 4 or 8 bytes) of its own group's
+// elements, all in flight at once, instead of the sweep's dependent loads one step at a
+// time.  Shared layout: element e of the array for CTA slot t at e * nt + t (nt = groups per
+// CTA), the global layout with stride nt.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  if constexpr (sizeof(T) == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+template <typename T>
+__device__ __forceinline__ void stage_group(T *dst, const T *src, int cnt, int G, int g, int nt, int t) {
+  for (int e = 0; e < cnt; ++e) cp_async_elem(dst + e * nt + t, src + (int64_t)e * G + g);
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// Shared memory of the staged factors (elements of T) for nt groups of q blocks: the down
+// sweep reads Mul, Minv, Up (q blocks each) and LoSep, UpSepPrev (one block each); the up
+// sweep W and Vs (q blocks each).
+__host__ __device__ constexpr int down_stage_elems(int q, int B, int nt) { return (3 * q + 2) * B * B * nt; }
+__host__ __device__ constexpr int up_stage_elems(int q, int B, int nt) { return 2 * q * B * B * nt; }
+
+// A copy of L whose down-sweep factors point at the staged arrays (outputs unchanged).
 template <typename T, int B>
-__global__ void __launch_bounds__(kGroupsPerCta) k_down0(const T *__restrict__ v, const double *scale,
-                                                         const int *active, LevelApply<T> L, int64_t n) {
+__device__ __forceinline__ LevelApply<T> stage_down(const LevelApply<T> &L, T *sm, int q, int g, int nt) {
+  constexpr int BB = B * B;
+  const int t = threadIdx.x;
+  LevelApply<T> S = L;
+  T *mul = sm, *minv = mul + q * BB * nt, *up = minv + q * BB * nt, *lo = up + q * BB * nt, *usp = lo + BB * nt;
+  if (g < L.G) {
+    stage_group(mul, L.Mul, q * BB, L.G, g, nt, t);
+    stage_group(minv, L.Minv, q * BB, L.G, g, nt, t);
+    stage_group(up, L.Up, q * BB, L.G, g, nt, t);
+    stage_group(lo, L.LoSep, BB, L.G, g, nt, t);
+    stage_group(usp, L.UpSepPrev, BB, L.G, g, nt, t);
+  }
+  S.Mul = mul; S.Minv = minv; S.Up = up; S.LoSep = lo; S.UpSepPrev = usp;
+  return S;
+}
+template <typename T, int B>
+__device__ __forceinline__ LevelApply<T> stage_up(const LevelApply<T> &L, T *sm, int q, int g, int nt) {
+  constexpr int BB = B * B;
+  const int t = threadIdx.x;
+  LevelApply<T> S = L;
+  T *w = sm, *vs = w + q * BB * nt;
+  if (g < L.G) {
+    stage_group(w, L.W, q * BB, L.G, g, nt, t);
+    stage_group(vs, L.Vs, q * BB, L.G, g, nt, t);
+  }
+  S.W = w; S.Vs = vs;
+  return S;
+}
+
+// Level 0 down: the CTA's rows of v (times *scale) and its groups' factors staged in shared
+// memory, one group per thread (NT groups per CTA).
+template <typename T, int B, int NT>
+__global__ void __launch_bounds__(NT) k_down0(const T *__restrict__ v, const double *scale, const int *active,
+                                              LevelApply<T> L, int64_t n) {
   if (active && *active == 0) return;
   constexpr int SPAN = (kQ0 + 1) * B;
   constexpr int PITCH = SPAN + 1;
-  __shared__ T tile[kGroupsPerCta * PITCH];
+  __shared__ T tile[NT * PITCH];
+  extern __shared__ __align__(16) unsigned char bsm[];
+  const int g0 = blockIdx.x * NT;
+  const int g = g0 + threadIdx.x;
+  const LevelApply<T> S = stage_down<T, B>(L, reinterpret_cast<T *>(bsm), kQ0, g, NT);
   const T sc = scale ? (T)(*scale) : (T)1;
-  const int g0 = blockIdx.x * kGroupsPerCta;
   const int64_t row0 = (int64_t)g0 * SPAN;
-  for (int e = threadIdx.x; e < kGroupsPerCta * SPAN; e += kGroupsPerCta) {
+  for (int e = threadIdx.x; e < NT * SPAN; e += NT) {
     const int64_t row = row0 + e;
     tile[(e / SPAN) * PITCH + (e % SPAN)] = (row < n) ? sc * v[row] : (T)0;
   }
+  cp_async_wait_all();
   __syncthreads();
-  const int g = g0 + threadIdx.x;
   if (g < L.G) {
     const T *mine = tile + threadIdx.x * PITCH;
     T f[kQ0][B], sep[B];
@@ -493,30 +558,34 @@ __global__ void __launch_bounds__(kGroupsPerCta) k_down0(const T *__restrict__ v
       for (int r = 0; r < B; ++r) f[i][r] = mine[i * B + r];
 #pragma unroll
     for (int r = 0; r < B; ++r) sep[r] = mine[kQ0 * B + r];
-    down_group<T, B, kQ0, true>(L, g, f, sep);
+    down_group<T, B, kQ0, false>(S, g, f, sep, NT, threadIdx.x);
   }
 }
 
 // Level 0 up: x for the CTA's groups staged in shared memory, then written in row order
 // through the epilogue: mode 0 y = x (fixed or ring-column output), mode 1 X += x (FP64).
-template <typename T, int B>
-__global__ void __launch_bounds__(kGroupsPerCta) k_up0(const int *active, LevelApply<T> L, const T *solnext,
-                                                       OutRef<T> yref, double *X, int mode, int64_t n) {
+template <typename T, int B, int NT>
+__global__ void __launch_bounds__(NT) k_up0(const int *active, LevelApply<T> L, const T *solnext, OutRef<T> yref,
+                                            double *X, int mode, int64_t n) {
   if (active && *active == 0) return;
   constexpr int SPAN = (kQ0 + 1) * B;
   constexpr int PITCH = SPAN + 1;
-  __shared__ T tile[kGroupsPerCta * PITCH];
-  const int g0 = blockIdx.x * kGroupsPerCta;
+  __shared__ T tile[NT * PITCH];
+  extern __shared__ __align__(16) unsigned char bsm[];
+  const int g0 = blockIdx.x * NT;
   const int g = g0 + threadIdx.x;
+  const LevelApply<T> S = stage_up<T, B>(L, reinterpret_cast<T *>(bsm), kQ0, g, NT);
+  cp_async_wait_all();
+  __syncthreads();
   if (g < L.G) {
     T *mine = tile + threadIdx.x * PITCH;
     auto out = [&](int i, int r, T v) { mine[i * B + r] = v; };
-    up_group<T, B, kQ0, true>(L, g, solnext, out);
+    up_group<T, B, kQ0, false>(S, g, solnext, out, NT, threadIdx.x);
   }
   __syncthreads();
   const int64_t row0 = (int64_t)g0 * SPAN;
   T *y = (mode == 0) ? yref.get() : nullptr;
-  for (int e = threadIdx.x; e < kGroupsPerCta * SPAN; e += kGroupsPerCta) {
+  for (int e = threadIdx.x; e < NT * SPAN; e += NT) {
     const int64_t row = row0 + e;
     if (row < n && (g0 + e / SPAN) < L.G) {
       const T v = tile[(e / SPAN) * PITCH + (e % SPAN)];
@@ -526,18 +595,28 @@ __global__ void __launch_bounds__(kGroupsPerCta) k_up0(const int *active, LevelA
   }
 }
 
+constexpr int kLevelCta = 64;   // groups per CTA of the level kernels
+
 template <typename T, int B>
-__global__ void k_down_level(const int *active, LevelApply<T> L, LevelApply<T> P) {
+__global__ void __launch_bounds__(kLevelCta) k_down_level(const int *active, LevelApply<T> L, LevelApply<T> P) {
   if (active && *active == 0) return;
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g < L.G) down_level_group<T, B, true>(L, P, g);
+  extern __shared__ __align__(16) unsigned char bsm[];
+  const int g = blockIdx.x * kLevelCta + threadIdx.x;
+  const LevelApply<T> S = stage_down<T, B>(L, reinterpret_cast<T *>(bsm), kQ, g, kLevelCta);
+  cp_async_wait_all();
+  __syncthreads();
+  if (g < L.G) down_level_group<T, B, false>(S, P, g, kLevelCta, threadIdx.x);
 }
 
 template <typename T, int B>
-__global__ void k_up_level(const int *active, LevelApply<T> L, const T *solnext) {
+__global__ void __launch_bounds__(kLevelCta) k_up_level(const int *active, LevelApply<T> L, const T *solnext) {
   if (active && *active == 0) return;
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g < L.G) up_level_group<T, B, true>(L, solnext, g);
+  extern __shared__ __align__(16) unsigned char bsm[];
+  const int g = blockIdx.x * kLevelCta + threadIdx.x;
+  const LevelApply<T> S = stage_up<T, B>(L, reinterpret_cast<T *>(bsm), kQ, g, kLevelCta);
+  cp_async_wait_all();
+  __syncthreads();
+  if (g < L.G) up_level_group<T, B, false>(S, solnext, g, kLevelCta, threadIdx.x);
 }
 
 // Levels first..last (last = top, one group) in one CTA: their factors and vectors are
@@ -606,13 +685,13 @@ __global__ void __launch_bounds__(512) k_tail(const int *active, const LevelAppl
   for (int l = first; l <= last; ++l) {
     const LevelApply<T> L = S[l - first];
     const LevelApply<T> P = (l == first) ? lv[l - 1] : S[l - 1 - first];
-    for (int g = threadIdx.x; g < L.G; g += blockDim.x) down_level_group<T, B, false>(L, P, g);
+    for (int g = threadIdx.x; g < L.G; g += blockDim.x) down_level_group<T, B, false>(L, P, g, L.G, g);
     __syncthreads();
   }
   for (int l = last; l >= first; --l) {
     const LevelApply<T> L = S[l - first];
     const T *solnext = (l < last) ? S[l + 1 - first].sol : nullptr;
-    for (int g = threadIdx.x; g < L.G; g += blockDim.x) up_level_group<T, B, false>(L, solnext, g);
+    for (int g = threadIdx.x; g < L.G; g += blockDim.x) up_level_group<T, B, false>(L, solnext, g, L.G, g);
     __syncthreads();
   }
 }
@@ -775,6 +854,24 @@ static void bind_apply_t(const std::vector<LevelShape> &lv, int b, char *&p, con
   }
 }
 
+// Groups per CTA of the level-0 kernels: 64 in FP32, 32 in FP64 (the staged factors of a
+// CTA then take the same ~107 KB of shared memory).
+template <typename T>
+constexpr int level0_cta() { return sizeof(T) == 4 ? 64 : 32; }
+
+template <typename T, int B>
+static void set_apply_attrs() {
+  constexpr int NT = level0_cta<T>();
+  cudaFuncSetAttribute(k_down0<T, B, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(down_stage_elems(kQ0, B, NT) * sizeof(T)));
+  cudaFuncSetAttribute(k_up0<T, B, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(up_stage_elems(kQ0, B, NT) * sizeof(T)));
+  cudaFuncSetAttribute(k_down_level<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(down_stage_elems(kQ, B, kLevelCta) * sizeof(T)));
+  cudaFuncSetAttribute(k_up_level<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(up_stage_elems(kQ, B, kLevelCta) * sizeof(T)));
+}
+
 void BandSolver::bind_apply(void *mem) {
   char *p = reinterpret_cast<char *>(mem);
   const std::vector<LevelF64> f64[kSlots] = {slots[0].f, slots[1].f, slots[2].f};
@@ -785,7 +882,8 @@ void BandSolver::bind_apply(void *mem) {
   if (!attrs) {
     attrs = true;
 #define PSP_TAIL_ATTR(T_, B_) \
-  cudaFuncSetAttribute(k_tail<T_, B_>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTailSmem + 1024);
+  cudaFuncSetAttribute(k_tail<T_, B_>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTailSmem + 1024); \
+  set_apply_attrs<T_, B_>();
     PSP_TAIL_ATTR(float, 1) PSP_TAIL_ATTR(float, 2) PSP_TAIL_ATTR(float, 3) PSP_TAIL_ATTR(float, 4)
     PSP_TAIL_ATTR(double, 1) PSP_TAIL_ATTR(double, 2) PSP_TAIL_ATTR(double, 3) PSP_TAIL_ATTR(double, 4)
 #undef PSP_TAIL_ATTR
@@ -826,16 +924,20 @@ template <typename T, int B>
 static void apply_b(const BandSolver &bs, const std::vector<LevelApply<T>> &a, const LevelApply<T> *dev,
                     const T *v, const double *scale, const int *active, OutRef<T> y, double *X, int mode,
                     cudaStream_t s) {
+  constexpr int NT = level0_cta<T>();
   const int L = (int)a.size();
-  const int g0 = (a[0].G + kGroupsPerCta - 1) / kGroupsPerCta;
-  k_down0<T, B><<<g0, kGroupsPerCta, 0, s>>>(v, scale, active, a[0], bs.n);
+  const int g0 = (a[0].G + NT - 1) / NT;
+  k_down0<T, B, NT><<<g0, NT, down_stage_elems(kQ0, B, NT) * sizeof(T), s>>>(v, scale, active, a[0], bs.n);
   const int tf = bs.tail_first;
   for (int l = 1; l < tf && l < L; ++l)
-    k_down_level<T, B><<<(a[l].G + 63) / 64, 64, 0, s>>>(active, a[l], a[l - 1]);
+    k_down_level<T, B><<<(a[l].G + kLevelCta - 1) / kLevelCta, kLevelCta, down_stage_elems(kQ, B, kLevelCta) * sizeof(T),
+                         s>>>(active, a[l], a[l - 1]);
   if (L > 1) k_tail<T, B><<<1, 512, bs.tail_smem_bytes(tf, L - 1, sizeof(T)), s>>>(active, dev, tf, L - 1);
   for (int l = std::min(tf, L) - 1; l >= 1; --l)
-    k_up_level<T, B><<<(a[l].G + 63) / 64, 64, 0, s>>>(active, a[l], a[l + 1].sol);
-  k_up0<T, B><<<g0, kGroupsPerCta, 0, s>>>(active, a[0], L > 1 ? a[1].sol : nullptr, y, X, mode, bs.n);
+    k_up_level<T, B><<<(a[l].G + kLevelCta - 1) / kLevelCta, kLevelCta, up_stage_elems(kQ, B, kLevelCta) * sizeof(T),
+                       s>>>(active, a[l], a[l + 1].sol);
+  k_up0<T, B, NT><<<g0, NT, up_stage_elems(kQ0, B, NT) * sizeof(T), s>>>(active, a[0], L > 1 ? a[1].sol : nullptr, y,
+                                                                         X, mode, bs.n);
 }
 
 template <typename T>
