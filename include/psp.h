@@ -172,6 +172,21 @@ const char *psp_last_error(void);
 psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, double tol,
                     psp_step_info *info);
 
+/*
+ * One implicit step of many independent handles (the batched form of the blueprint's
+ * configuration 4): handle i steps u_n[i] -> u_np1[i] with dt[i] and the common tolerance
+ * tol, exactly as psp_step would.  nthreads host threads take the instances in order, each
+ * stepping one handle at a time on that handle's stream, so up to nthreads instances' cycle
+ * graphs run on the GPU concurrently; handles should therefore be created with distinct
+ * streams.  infos, seconds (host wall time of each instance's step) and statuses are
+ * host arrays of count entries or NULL.  Returns PSP_OK, PSP_ERR_NOCONV if an instance
+ * reached max_restarts, or the first other error status of an instance (all instances are
+ * attempted).  A handle must not appear twice.
+ */
+psp_status psp_step_batch(psp_handle *handles, int count, const double *const *u_n, double *const *u_np1,
+                          const double *dt, double tol, int nthreads, psp_step_info *infos, double *seconds,
+                          psp_status *statuses);
+
 /* psp_step on host arrays: copies u_n_host to the device, steps, copies the result to
  * u_np1_host (both n doubles, pageable or pinned). */
 psp_status psp_step_host(psp_handle h, const double *u_n_host, double *u_np1_host, double dt,

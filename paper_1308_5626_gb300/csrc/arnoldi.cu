@@ -592,13 +592,12 @@ __global__ void __launch_bounds__(kThreads) k_update_z(int64_t n, const T *__res
 // ---------------------------------------------------------------------------------------
 
 int arnoldi_grid() {
-  static int g = 0;
-  if (g == 0) {
+  static const int g = [] {   // thread-safe one-time initialisation
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    g = sms > 0 ? std::min(sms, kMaxArnCta) : 152;
-  }
+    return sms > 0 ? std::min(sms, kMaxArnCta) : 152;
+  }();
   return g;
 }
 

@@ -12,7 +12,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
+#include <chrono>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "band_solve.cuh"
@@ -585,6 +588,14 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
   int cur = try_cand ? h->cand : h->adopted;
   double trial_beta = -1.0, trial_R = 0.0, main_beta = -1.0, main_R = 0.0;
   int trial_iters = 0, main_iters = 0;
+  int hist_before_trial = 0;
+  const int prev_adopted = h->adopted;
+  bool adopted_now = false;   // the candidate was adopted in this step (band copied at its end)
+  if (try_cand) {   // the history length to restore if the trial cycle breaks down
+    PSP_CUDA(cudaMemcpyAsync(h->int_host + 3, &h->st->hist_count, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PSP_CUDA(cudaStreamSynchronize(s));
+    hist_before_trial = h->int_host[3];
+  }
   for (int c = 0; c < h->opts.max_restarts; ++c) {
     const int which = cur < 0 ? 0 : cur + 1;
     psp_status ps = ensure_graph(h, which);
@@ -599,6 +610,32 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
     bnorm = sm.bnorm;
     if (sm.error) return fail(PSP_ERR_DEVICE, "device error flag " + std::to_string(sm.error) +
                                                   " (a bounded wait expired or a launch was misconfigured)");
+    const bool broken = (sm.status & kStNumeric) || !std::isfinite(sm.R_end) || !std::isfinite(sm.beta);
+    if (broken && ((c == 0 && try_cand) || adopted_now)) {
+      // the fresh candidate broke a cycle of this step (in the mixed form an ill-conditioned
+      // N can overflow the FP32 solve): it is rejected like a slow one and the step restarts
+      // from u^n with the previous N -- X back to u^n, the pairs of the cycles run with the
+      // candidate dropped from the history
+      flags |= PSP_FLAG_CANDIDATE_TRIED;
+      flags &= ~PSP_FLAG_CANDIDATE_ACCEPTED;
+      PSP_CUDA(cudaMemcpyAsync(h->X, u_n, n * 8, cudaMemcpyDeviceToDevice, s));
+      h->int_host[3] = hist_before_trial;
+      PSP_CUDA(cudaMemcpyAsync(&h->st->hist_count, h->int_host + 3, sizeof(int), cudaMemcpyHostToDevice, s));
+      PSP_CUDA(cudaStreamSynchronize(s));
+      if (adopted_now) {
+        h->adopted = prev_adopted;
+        h->adopted_version += 1;
+        adopted_now = false;
+        h->wait_len = std::max(h->wait_len, 1);
+      }
+      h->wait = h->wait_len;
+      h->wait_len *= 2;
+      cur = h->adopted;
+      h->cand = -1;
+      main_beta = -1.0;
+      main_iters = 0;
+      continue;
+    }
     if (sm.status & kStNumeric) { numeric = true; break; }
     if (sm.status & kStBreakdown) flags |= PSP_FLAG_BREAKDOWN;
     // residual at the end of the cycle: the FP64 true residual of a converged restart
@@ -618,8 +655,7 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
         h->adopted_version += 1;
         h->wait_len = 1;
         flags |= PSP_FLAG_CANDIDATE_ACCEPTED;
-        PSP_CUDA(cudaMemcpyAsync(h->band_adopted, h->band_cand, (size_t)n * (2 * h->b + 1) * 8,
-                                 cudaMemcpyDeviceToDevice, s));
+        adopted_now = true;
       } else {
         h->wait = h->wait_len;
         h->wait_len *= 2;
@@ -636,6 +672,9 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
   if (main_iters > 0 && main_beta > 0.0) h->rate_ref = rate_of(main_R, main_beta, main_iters);
   else if (trial_iters > 0 && trial_beta > 0.0) h->rate_ref = rate_of(trial_R, trial_beta, trial_iters);
 
+  if (adopted_now)
+    PSP_CUDA(cudaMemcpyAsync(h->band_adopted, h->band_cand, (size_t)n * (2 * h->b + 1) * 8,
+                             cudaMemcpyDeviceToDevice, s));
   psp_status result = PSP_OK;
   if (numeric) result = fail(PSP_ERR_NUMERIC, "non-finite residual");
   else if (!converged) result = fail(PSP_ERR_NOCONV, "max_restarts reached");
@@ -679,6 +718,51 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
     info->launches = launches;
   }
   return result;
+}
+
+psp_status psp_step_batch(psp_handle *hs, int count, const double *const *u_n, double *const *u_np1,
+                          const double *dt, double tol, int nthreads, psp_step_info *infos, double *seconds,
+                          psp_status *statuses) {
+  if (!hs || !u_n || !u_np1 || !dt || count < 0) return fail(PSP_ERR_ARG, "NULL argument or negative count");
+  if (!(tol > 0.0)) return fail(PSP_ERR_ARG, "tol must be > 0");
+  for (int i = 0; i < count; ++i)
+    if (!hs[i]) return fail(PSP_ERR_ARG, "NULL handle in the batch");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int nt = std::max(1, std::min(nthreads < 1 ? 1 : nthreads, std::max(count, 1)));
+  // instances are taken from a shared counter in order; every worker thread steps one
+  // handle at a time on that handle's own stream, so the GPU runs nt instances' cycle
+  // graphs concurrently while each thread waits for its instance's cycle summaries
+  std::atomic<int> next{0};
+  std::atomic<int> first_err{(int)PSP_OK};   // first status other than OK and NOCONV
+  std::atomic<bool> noconv{false};
+  auto work = [&]() {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= count) break;
+      const auto t0 = std::chrono::steady_clock::now();
+      psp_step_info info{};
+      const psp_status st = psp_step(hs[i], u_n[i], u_np1[i], dt[i], tol, &info);
+      const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (infos) infos[i] = info;
+      if (seconds) seconds[i] = sec;
+      if (statuses) statuses[i] = st;
+      if (st == PSP_ERR_NOCONV) {
+        noconv = true;
+      } else if (st != PSP_OK) {
+        int expected = (int)PSP_OK;
+        first_err.compare_exchange_strong(expected, (int)st);
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+  work();
+  for (auto &th : pool) th.join();
+  if (first_err.load() != (int)PSP_OK)
+    return fail((psp_status)first_err.load(), "at least one instance of the batch failed (see statuses)");
+  return noconv.load() ? fail(PSP_ERR_NOCONV, "an instance reached max_restarts") : PSP_OK;
 }
 
 psp_status psp_step_host(psp_handle h, const double *u_n_host, double *u_np1_host, double dt, double tol,

@@ -475,16 +475,15 @@ __global__ void __launch_bounds__(kTileXV * kTileY, 2) k_stencil_3d(InRef<T> xre
 // Planes per CTA of k_stencil_3d: the fewest chunks of z that fill the resident slots.
 template <typename T, int R>
 static int tile3d_tz(int gx, int gy, int nz) {
-  static int resident = 0;
-  if (resident == 0) {
+  static const int resident = [] {   // thread-safe one-time initialisation
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int bytes = kStage3 * tile3d_slot_vecs<T, R>() * 16;
     cudaFuncSetAttribute(k_stencil_3d<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_stencil_3d<T, R>, kTileXV * kTileY, bytes);
-    resident = std::max(1, sms) * std::max(1, per);
-  }
+    return std::max(1, sms) * std::max(1, per);
+  }();
   const int chunks = std::max(1, std::min(nz, resident / std::max(1, gx * gy)));
   return (nz + chunks - 1) / chunks;
 }
@@ -498,14 +497,13 @@ bool stencil_3d_tiled(const Geometry &g, int elem_bytes) {
 // at once, else every resident slot (a grid-stride loop covers the rest).
 template <typename T, int NDIM, int R>
 static int vec_grid(int64_t nvec) {
-  static int resident = 0;
-  if (resident == 0) {
+  static const int resident = [] {   // thread-safe one-time initialisation
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_stencil_vec<T, NDIM, R>, kThreads, 0);
-    resident = std::max(1, sms) * std::max(1, per);
-  }
+    return std::max(1, sms) * std::max(1, per);
+  }();
   return (int)std::max<int64_t>(1, std::min<int64_t>((nvec + kThreads - 1) / kThreads, resident));
 }
 

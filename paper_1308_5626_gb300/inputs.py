@@ -194,6 +194,34 @@ def c5(n: int = 512) -> Tuple[Workload, np.ndarray]:
     return w, factors
 
 
+def c4_instance(i: int, e_range: Tuple[int, int] = (10, 18)) -> Workload:
+    """Instance i of the batched workload (seed 4 + i): a coin picks the 1D form of c1 or the
+    2D form of c2; n = 2^e with e uniform over the integers of e_range (log-uniform sizes; a
+    2D grid splits as n_x = 2^ceil(e/2), n_y = 2^floor(e/2)); accuracy order from
+    {2, 4, 6, 8}; b from 1..4; CFL ~ U[1, 20]; restart 30; tolerance 1e-8."""
+    rng = np.random.default_rng(4 + i)
+    two_d = bool(rng.integers(0, 2))
+    e = int(rng.integers(e_range[0], e_range[1] + 1))
+    order = int(rng.choice([2, 4, 6, 8]))
+    b = int(rng.integers(1, 5))
+    cfl = float(rng.uniform(1.0, 20.0))
+    if two_d:
+        nx, ny = 2 ** ((e + 1) // 2), 2 ** (e // 2)
+        a = rng.uniform(0.5, 2.0, 2)
+        nu = rng.uniform(0.5, 2.0, 2) * 1e-3
+        terms = [Term(1, 0, float(a[0])), Term(1, 1, float(a[1])),
+                 Term(2, 0, float(nu[0])), Term(2, 1, float(nu[1]))]
+        u0 = gaussian_random_field((nx, ny), rng, power=-2.0)
+        shape, dt = (nx, ny), cfl * (TWO_PI / nx) / float(a.max())
+    else:
+        n = 2 ** e
+        terms = [Term(1, 0, 1.0), Term(2, 0, 0.01)]
+        u0 = sines_1d(n, 16, rng)
+        shape, dt = (n,), cfl * (TWO_PI / n)
+    return Workload("c4_%d_%s" % (i, "x".join(str(s) for s in shape)), shape, order, terms, b=b, m=30,
+                    steps=10, tol=1e-8, dt=dt, rho_dt=None, u0=u0, seed=4 + i)
+
+
 WORKLOADS = {"c1": c1, "c2": c2, "c3": c3}
 
 

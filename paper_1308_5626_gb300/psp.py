@@ -70,6 +70,9 @@ _SIGS = {
     "psp_matvec": [_VP, _VP, _VP, ctypes.c_double],
     "psp_matvec_f32": [_VP, _VP, _VP, ctypes.c_double],
     "psp_apply_L": [_VP, ctypes.c_int, _VP, _VP],
+    "psp_step_batch": [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                       ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_int, ctypes.POINTER(psp_step_info),
+                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)],
     "psp_fit_band": [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_int)],
     "psp_fit_band_f32": [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_int)],
     "psp_set_band": [_VP, _VP],
@@ -174,6 +177,23 @@ def psp_step_host(h, u_n_host, u_np1_host, dt: float, tol: float) -> psp_step_in
 def psp_matvec(h, x, y, dt: float) -> None:
     fn = lib().psp_matvec_f32 if str(x.dtype) == "torch.float32" else lib().psp_matvec
     _check(fn(h, _ptr(x), _ptr(y), float(dt)), "psp_matvec")
+
+
+def psp_step_batch(handles, u_n, u_np1, dt, tol: float, nthreads: int = 8, allow_noconv: bool = False):
+    """One step of every handle (lists of equal length; u tensors float64 on the device).
+    Returns (infos, seconds, statuses)."""
+    cnt = len(handles)
+    hs = (_VP * cnt)(*[h for h in handles])
+    ui = (_VP * cnt)(*[_ptr(u) for u in u_n])
+    uo = (_VP * cnt)(*[_ptr(u) for u in u_np1])
+    dts = (ctypes.c_double * cnt)(*[float(d) for d in dt])
+    infos = (psp_step_info * cnt)()
+    secs = (ctypes.c_double * cnt)()
+    sts = (ctypes.c_int * cnt)()
+    st = lib().psp_step_batch(hs, cnt, ui, uo, dts, float(tol), int(nthreads), infos, secs, sts)
+    if st != PSP_OK and not (allow_noconv and st == PSP_ERR_NOCONV):
+        _check(st, "psp_step_batch")
+    return list(infos), list(secs), list(sts)
 
 
 def psp_apply_L(h, term: int, x, y) -> None:
