@@ -213,10 +213,19 @@ __device__ void dcgs_scalar(DevState *st, int j, int final_step, const T *partia
       HcTw[(int64_t)(j - 1) * ld + r] = v;
     }
   __syncthreads();
-  for (int r = threadIdx.x; r <= j; r += blockDim.x) {   // t = Hbar a
-    T t = (T)0;
-    for (int i = (r > 0 ? r - 1 : 0); i < j; ++i) t += ((i == j - 1) ? s_hcol[r] : sH[i * ld + r]) * s_a[i];
-    s_t[r] = t;
+  {  // t = Hbar a: 8 lanes per row, each a strided share of the row's terms, then a shuffle sum
+    constexpr int LPR = 8;
+    const int sub = threadIdx.x % LPR, rows = blockDim.x / LPR;
+    for (int rb = 0; rb <= j; rb += rows) {   // the same trip count for every lane of a warp
+      const int r = rb + threadIdx.x / LPR;
+      T t = (T)0;
+      if (r <= j)
+        for (int i = (r > 0 ? r - 1 : 0) + sub; i < j; i += LPR)
+          t += ((i == j - 1) ? s_hcol[r] : sH[i * ld + r]) * s_a[i];
+#pragma unroll
+      for (int off = LPR / 2; off >= 1; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+      if (r <= j && sub == 0) s_t[r] = t;
+    }
   }
   __syncthreads();
   const T inv = (nu > (T)0) ? (T)1 / nu : (T)0;

@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kThreads) k_restart(const double *__restrict__
   const int n = nx * ny * nz;
   const int plane = nx * ny;
   double rr = 0.0, bb = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  auto point = [&](int i) {
     const int iz = i / plane;
     const int rem = i - iz * plane;
     const int iy = rem / nx;
@@ -224,13 +224,19 @@ __global__ void __launch_bounds__(kThreads) k_restart(const double *__restrict__
     } else {
       ax = stencil_point<double, NDIM, R, double>(X, c, ix, iy, iz, nx, ny, nz);
     }
-    double b = B[i];
-    double r = b - ax;
+    const double b = B[i];
+    const double r = b - ax;
     px[i] = (TH)X[i];
     py[i] = (TH)ax;
     V1[i] = (TV)r;
     rr += r * r;
     bb += b * b;
+  };
+  // two points per round, independent: their loads and FP64 chains overlap
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 2 * stride) {
+    point(i);
+    if (i + stride < n) point(i + stride);
   }
   __shared__ double s_rr[kThreads / 32], s_bb[kThreads / 32];
   rr = warp_sum(rr);
