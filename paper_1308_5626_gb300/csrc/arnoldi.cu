@@ -415,17 +415,20 @@ __global__ void __launch_bounds__(kDotThreads, 1) k_dcgs_dots(const T *__restric
     if (threadIdx.x == 0) atomicExch(&st->error, 3);
     return;
   }
-  if (st->active == 0) return;
   using VT = typename Vec<T>::type;
   constexpr int W = Vec<T>::W;
   extern __shared__ __align__(16) double dsm[];
   __shared__ T s_acc[kDotWarps][kAccLd];
   __shared__ T s_c[3][2 * kMaxR + 1];
   for (int e = threadIdx.x; e < kDotWarps * kAccLd; e += blockDim.x) (&s_acc[0][0])[e] = (T)0;
+  // launched as a programmatic dependent of the previous kernel (pass B of the last
+  // iteration): nothing it writes is read before this wait
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   if (MV != 0 && threadIdx.x < 3 * (2 * kMaxR + 1))
     s_c[threadIdx.x / (2 * kMaxR + 1)][threadIdx.x % (2 * kMaxR + 1)] =
         (T)st->coef[threadIdx.x / (2 * kMaxR + 1)][threadIdx.x % (2 * kMaxR + 1)];
   __syncthreads();
+  if (st->active == 0) return;
   const int k = j + 1;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const VT *vjp = reinterpret_cast<const VT *>(V + (int64_t)j * ldv);
@@ -513,6 +516,9 @@ __global__ void __launch_bounds__(kUpdThreads) k_dcgs_update(T *__restrict__ V, 
   // Launched as a programmatic dependent of pass A: the CTAs may be scheduled while pass
   // A's last CTA still forms the coefficients, and wait here for that grid to finish.
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  // the next pass A (a programmatic dependent of this grid) may be scheduled onto SMs as
+  // this grid's CTAs retire; it waits for this grid's completion before reading its data
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (st->active == 0) return;   // the cycle ended: nothing to do
   extern __shared__ __align__(16) double dsm[];
   // block 0 is the Givens CTA: the first block is scheduled first, so it runs alongside the
@@ -641,9 +647,20 @@ void launch_arnoldi(int j, int final_step, int64_t n, T *V, int64_t ldv, const T
     // the folded matvec is instantiated per dimension and stencil radius: 8 ndim + R
     const int sel = (mv && !final_step) ? 8 * m.ndim + m.R : 0;
     T *pt = reinterpret_cast<T *>(partial);
+    // a programmatic dependent of the previous kernel (see k_dcgs_dots and k_dcgs_update)
+    cudaLaunchConfig_t cfa = {};
+    cfa.gridDim = dim3((unsigned)grid);
+    cfa.blockDim = dim3(kDotThreads);
+    cfa.dynamicSmemBytes = sm;
+    cfa.stream = s;
+    cudaLaunchAttribute ata[1];
+    ata[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    ata[0].val.programmaticStreamSerializationAllowed = 1;
+    cfa.attrs = ata;
+    cfa.numAttrs = 1;
     switch (sel) {
 #define PSP_DOTS(MV_) \
-  case MV_: k_dcgs_dots<T, MV_><<<grid, kDotThreads, sm, s>>>(V, ldv, Py, ldh, j, woff, st, pt, nv, final_step, m); break;
+  case MV_: cudaLaunchKernelEx(&cfa, k_dcgs_dots<T, MV_>, (const T *)V, ldv, Py, ldh, j, woff, st, pt, nv, final_step, m); break;
       PSP_DOTS(0) PSP_DOTS(9) PSP_DOTS(10) PSP_DOTS(11) PSP_DOTS(12) PSP_DOTS(13) PSP_DOTS(17) PSP_DOTS(18)
       PSP_DOTS(19) PSP_DOTS(20) PSP_DOTS(21) PSP_DOTS(25) PSP_DOTS(26) PSP_DOTS(27) PSP_DOTS(28) PSP_DOTS(29)
 #undef PSP_DOTS
