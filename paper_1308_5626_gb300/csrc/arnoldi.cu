@@ -36,10 +36,41 @@ namespace psp {
 
 constexpr double kBreakdownRel = 1e-14;
 
+// L2 eviction-priority policies (PTX createpolicy): the first basis columns of a cycle are
+// read by both passes of every iteration, so they are loaded and stored with evict_last and
+// stay resident in L2; the other columns stream through with evict_first.
+__device__ __forceinline__ uint64_t l2_evict_last() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
 template <typename T> struct Vec;
 template <> struct Vec<float> {
   using type = float4;
   static constexpr int W = 4;
+  // 16-byte loads and stores with an L2 cache policy (ldnc: read-only for the kernel)
+  __device__ static __forceinline__ float4 ldnc(const float4 *p, uint64_t pol) {
+    float4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p), "l"(pol));
+    return v;
+  }
+  __device__ static __forceinline__ float4 ld(const float4 *p, uint64_t pol) {
+    float4 v;
+    asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p), "l"(pol) : "memory");
+    return v;
+  }
+  __device__ static __forceinline__ void st(float4 *p, float4 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;"
+                 :: "l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol) : "memory");
+  }
   __device__ static __forceinline__ float dot(float4 a, float4 b) {
     return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
   }
@@ -51,6 +82,21 @@ template <> struct Vec<float> {
 template <> struct Vec<double> {
   using type = double2;
   static constexpr int W = 2;
+  __device__ static __forceinline__ double2 ldnc(const double2 *p, uint64_t pol) {
+    double2 v;
+    asm("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
+    return v;
+  }
+  __device__ static __forceinline__ double2 ld(const double2 *p, uint64_t pol) {
+    double2 v;
+    asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+                 : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol) : "memory");
+    return v;
+  }
+  __device__ static __forceinline__ void st(double2 *p, double2 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" :: "l"(p), "d"(v.x), "d"(v.y), "l"(pol)
+                 : "memory");
+  }
   __device__ static __forceinline__ double dot(double2 a, double2 b) { return a.x * b.x + a.y * b.y; }
   __device__ static __forceinline__ double2 axpy(double c, double2 x, double2 y) {
     return make_double2(y.x - c * x.x, y.y - c * x.y);
@@ -408,7 +454,7 @@ template <typename T, int MV>
 __global__ void __launch_bounds__(kDotThreads, 1) k_dcgs_dots(const T *__restrict__ V, int64_t ldv,
                                                                 const T *__restrict__ Pyb, int64_t ldh, int j,
                                                                 int woff, DevState *st, T *partial, int64_t nv,
-                                                                int final_step, const TileMatvec<T> mv) {
+                                                                int final_step, const TileMatvec<T> mv, int hot) {
   // launch self-check: the engine's cross-CTA sums cover at most kMaxArnCta CTAs and the
   // partial rows kMaxCta; a larger grid records a device error instead of reading past them
   if (gridDim.x > kMaxArnCta || gridDim.x > kMaxCta || blockDim.x != kDotThreads) {
@@ -445,6 +491,9 @@ __global__ void __launch_bounds__(kDotThreads, 1) k_dcgs_dots(const T *__restric
     wout = reinterpret_cast<VT *>(mv.w.get());
     xcp = mv.xcopy.base ? reinterpret_cast<VT *>(mv.xcopy.get()) : nullptr;
   }
+  // columns below `hot` stay resident in L2 between the passes and iterations
+  const uint64_t pol_last = l2_evict_last(), pol_first = l2_evict_first();
+  const uint64_t pol_j = j < hot ? pol_last : pol_first;
   for (int64_t it = 0; it < iters; ++it) {
     const int64_t i0 = it * 2 * stride + blockIdx.x * (int64_t)blockDim.x + threadIdx.x, i1 = i0 + stride;
     const bool ok0 = i0 < nv, ok1 = i1 < nv;
@@ -457,12 +506,12 @@ __global__ void __launch_bounds__(kDotThreads, 1) k_dcgs_dots(const T *__restric
       if (i1 < nvg) { wout[i1] = w1; if (xcp) xcp[i1] = c1; }
       if (xcp) { v0 = c0; v1 = c1; }
       else {
-        if (ok0) v0 = vjp[i0];
-        if (ok1) v1 = vjp[i1];
+        if (ok0) v0 = Vec<T>::ldnc(vjp + i0, pol_j);
+        if (ok1) v1 = Vec<T>::ldnc(vjp + i1, pol_j);
       }
     } else {
-      if (ok0) { v0 = vjp[i0]; if (!final_step) w0 = wp[i0]; }
-      if (ok1) { v1 = vjp[i1]; if (!final_step) w1 = wp[i1]; }
+      if (ok0) { v0 = Vec<T>::ldnc(vjp + i0, pol_j); if (!final_step) w0 = wp[i0]; }
+      if (ok1) { v1 = Vec<T>::ldnc(vjp + i1, pol_j); if (!final_step) w1 = wp[i1]; }
     }
     for (int c0 = 0; c0 < k; c0 += 8) {
       VT a0[8], a1[8];
@@ -470,8 +519,9 @@ __global__ void __launch_bounds__(kDotThreads, 1) k_dcgs_dots(const T *__restric
       for (int u = 0; u < 8; ++u) {
         const int col = min(c0 + u, j);
         const VT *qc = reinterpret_cast<const VT *>(V + (int64_t)col * ldv);
-        a0[u] = ok0 ? qc[i0] : VT{};
-        a1[u] = ok1 ? qc[i1] : VT{};
+        const uint64_t pol = col < hot ? pol_last : pol_first;
+        a0[u] = ok0 ? Vec<T>::ldnc(qc + i0, pol) : VT{};
+        a1[u] = ok1 ? Vec<T>::ldnc(qc + i1, pol) : VT{};
       }
       T val[16];
 #pragma unroll
@@ -510,9 +560,9 @@ __global__ void __launch_bounds__(kDotThreads, 1) k_dcgs_dots(const T *__restric
 constexpr int kUpdThreads = 256;
 
 template <typename T>
-__global__ void __launch_bounds__(kUpdThreads) k_dcgs_update(T *__restrict__ V, int64_t ldv, const T *__restrict__ Pyb,
+__global__ void __launch_bounds__(kUpdThreads, 4) k_dcgs_update(T *__restrict__ V, int64_t ldv, const T *__restrict__ Pyb,
                                                              int64_t ldh, int j, int woff, DevState *st, int64_t nv,
-                                                             int final_step, int mixed) {
+                                                             int final_step, int mixed, int hot) {
   // Launched as a programmatic dependent of pass A: the CTAs may be scheduled while pass
   // A's last CTA still forms the coefficients, and wait here for that grid to finish.
   asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -540,11 +590,16 @@ __global__ void __launch_bounds__(kUpdThreads) k_dcgs_update(T *__restrict__ V, 
   VT *vn = reinterpret_cast<VT *>(V + (int64_t)(j + 1) * ldv);
   const VT *w = reinterpret_cast<const VT *>(Pyb + (int64_t)((st->hist_base + woff) % st->mmax) * ldh);
   const int64_t stride = (int64_t)(gridDim.x - 1) * blockDim.x;   // streaming CTAs
+  // columns below `hot` stay resident in L2 (as in pass A); v_j and v_{j+1} are stored with
+  // the policy of their column, the others are read with evict_first
+  const uint64_t pol_last = l2_evict_last(), pol_first = l2_evict_first();
+  const uint64_t pol_j = j < hot ? pol_last : pol_first;
+  const uint64_t pol_n = j + 1 < hot ? pol_last : pol_first;
   for (int64_t iv = (blockIdx.x - 1) * (int64_t)blockDim.x + threadIdx.x; iv < nv; iv += 2 * stride) {
     const int64_t iv2 = iv + stride;
     const bool two = iv2 < nv;
     const int64_t jv2 = two ? iv2 : iv;
-    const VT v0 = vj[iv], v1 = vj[jv2];
+    const VT v0 = Vec<T>::ld(vj + iv, pol_j), v1 = Vec<T>::ld(vj + jv2, pol_j);
     const VT x0 = w[iv], x1 = w[jv2];
     VT q0 = Vec<T>::scale(sv, v0), q1 = Vec<T>::scale(sv, v1);
     VT y0 = Vec<T>::axpy(cv, v0, Vec<T>::scale(sw, x0)), y1 = Vec<T>::axpy(cv, v1, Vec<T>::scale(sw, x1));
@@ -554,8 +609,10 @@ __global__ void __launch_bounds__(kUpdThreads) k_dcgs_update(T *__restrict__ V, 
       for (int u = 0; u < 8; ++u) {
         const int col = min(c0 + u, j - 1);
         const VT *qc = reinterpret_cast<const VT *>(V + (int64_t)col * ldv);
-        a0[u] = qc[iv];
-        a1[u] = qc[jv2];
+        // columns below j are not written by this grid: read-only loads
+        const uint64_t pol = col < hot ? pol_last : pol_first;
+        a0[u] = Vec<T>::ldnc(qc + iv, pol);
+        a1[u] = Vec<T>::ldnc(qc + jv2, pol);
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
@@ -566,11 +623,11 @@ __global__ void __launch_bounds__(kUpdThreads) k_dcgs_update(T *__restrict__ V, 
         y1 = Vec<T>::axpy(cd, a1[u], y1);
       }
     }
-    vj[iv] = q0;
-    vn[iv] = y0;
+    Vec<T>::st(vj + iv, q0, pol_j);
+    Vec<T>::st(vn + iv, y0, pol_n);
     if (two) {
-      vj[iv2] = q1;
-      vn[iv2] = y1;
+      Vec<T>::st(vj + iv2, q1, pol_j);
+      Vec<T>::st(vn + iv2, y1, pol_n);
     }
   }
 }
@@ -606,6 +663,23 @@ __global__ void __launch_bounds__(kThreads) k_update_z(int64_t n, const T *__res
 
 // ---------------------------------------------------------------------------------------
 
+// Basis columns kept resident in L2 across the two passes and the iterations of a cycle:
+// as many as fit in PSP_L2_HOT_FRACTION of the L2 (the rest of it serves the streamed
+// columns, the matvec and the other kernels of the step).
+#ifndef PSP_L2_HOT_FRACTION
+#define PSP_L2_HOT_FRACTION 0.4
+#endif
+int l2_hot_columns(int64_t col_bytes) {
+  static const int64_t l2 = [] {
+    int dev = 0, b = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b, cudaDevAttrL2CacheSize, dev);
+    return (int64_t)b;
+  }();
+  if (col_bytes <= 0) return 0;
+  return (int)std::min<int64_t>(kMaxM + 1, (int64_t)(PSP_L2_HOT_FRACTION * (double)l2) / col_bytes);
+}
+
 int arnoldi_grid() {
   static const int g = [] {   // thread-safe one-time initialisation
     int dev = 0, sms = 0;
@@ -631,6 +705,7 @@ static void set_attrs_t() {
 
 void arnoldi_setup() {
   arnoldi_grid();
+  l2_hot_columns(1);
   set_attrs_t<float>();
   set_attrs_t<double>();
 }
@@ -639,6 +714,7 @@ template <typename T>
 void launch_arnoldi(int j, int final_step, int64_t n, T *V, int64_t ldv, const T *Py, int64_t ldh, DevState *st,
                     double *partial, int mixed, cudaStream_t s, cudaEvent_t *ev, const TileMatvec<T> *mv) {
   const TileMatvec<T> m = mv ? *mv : TileMatvec<T>{};
+  const int hot = l2_hot_columns(ldv * (int64_t)sizeof(T));
   const int woff = 1 + j;   // ring column of w_j relative to the cycle's restart column
   const int64_t nv = (ldv + Vec<T>::W - 1) / Vec<T>::W;
   {
@@ -660,7 +736,7 @@ void launch_arnoldi(int j, int final_step, int64_t n, T *V, int64_t ldv, const T
     cfa.numAttrs = 1;
     switch (sel) {
 #define PSP_DOTS(MV_) \
-  case MV_: cudaLaunchKernelEx(&cfa, k_dcgs_dots<T, MV_>, (const T *)V, ldv, Py, ldh, j, woff, st, pt, nv, final_step, m); break;
+  case MV_: cudaLaunchKernelEx(&cfa, k_dcgs_dots<T, MV_>, (const T *)V, ldv, Py, ldh, j, woff, st, pt, nv, final_step, m, hot); break;
       PSP_DOTS(0) PSP_DOTS(9) PSP_DOTS(10) PSP_DOTS(11) PSP_DOTS(12) PSP_DOTS(13) PSP_DOTS(17) PSP_DOTS(18)
       PSP_DOTS(19) PSP_DOTS(20) PSP_DOTS(21) PSP_DOTS(25) PSP_DOTS(26) PSP_DOTS(27) PSP_DOTS(28) PSP_DOTS(29)
 #undef PSP_DOTS
@@ -684,7 +760,7 @@ void launch_arnoldi(int j, int final_step, int64_t n, T *V, int64_t ldv, const T
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_dcgs_update<T>, V, ldv, Py, ldh, j, woff, st, nv, final_step, mixed);
+    cudaLaunchKernelEx(&cfg, k_dcgs_update<T>, V, ldv, Py, ldh, j, woff, st, nv, final_step, mixed, hot);
   }
   if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);
 }
