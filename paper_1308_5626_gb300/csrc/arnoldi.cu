@@ -212,8 +212,11 @@ template <> __device__ __forceinline__ double *coef_copy<double>(DevState *st, i
   return which == 0 ? st->cA : (which == 1 ? st->cD : st->c3);
 }
 
+// The inputs from earlier iterations (columns 0..j-2 of the Hessenberg copy into sH, h_{j-1}
+// into hf_pre) were staged into shared memory by engine_stage at the start of the kernel.
 template <typename T>
-__device__ void dcgs_scalar(DevState *st, int j, int final_step, const T *partial, int nb, T *scratch) {
+__device__ void dcgs_scalar(DevState *st, int j, int final_step, const T *partial, int nb, T *scratch,
+                            const double *hf_pre) {
   constexpr int ld = kMaxM + 1;
   T *s_sum = scratch;                                             // 2 kMaxM + 2
   T *sH = s_sum + 2 * kMaxM + 2;                                  // kMaxM * ld
@@ -221,12 +224,12 @@ __device__ void dcgs_scalar(DevState *st, int j, int final_step, const T *partia
   T *s_t = s_a + kMaxM;                                           // kMaxM + 1
   T *s_hcol = s_t + kMaxM + 1;                                    // kMaxM + 2
   T *s_sc = s_hcol + kMaxM + 2;                                   // 4
-  const T *HcT = hc_copy<T>(st);
   T *HcTw = hc_copy<T>(st);
   const int k = j + 1;
-  for (int e = threadIdx.x; e < (j > 1 ? (j - 1) * ld : 0); e += blockDim.x) sH[e] = HcT[e];
+  cp_async_wait_all();
+  __syncthreads();
   if (j >= 1)
-    for (int r = threadIdx.x; r < j; r += blockDim.x) s_hcol[r] = (T)st->Hf[(int64_t)(j - 1) * ld + r];
+    for (int r = threadIdx.x; r < j; r += blockDim.x) s_hcol[r] = (T)hf_pre[r];
   grid_sums<T>(partial, 2 * k, nb, s_sum);   // ends with a barrier
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (wid == 0) {
@@ -294,6 +297,21 @@ __device__ void dcgs_scalar(DevState *st, int j, int final_step, const T *partia
     c3[1] = cj * inv;
     c3[2] = inv;
   }
+}
+
+// Stage the scalar engine's inputs from earlier iterations (written by earlier launches)
+// into shared memory with asynchronous copies: issued by every CTA of pass A right after its
+// grid-dependency wait, so that they are in place, at no latency, when the last CTA to
+// arrive runs the engine.  Layout as in dcgs_scalar.
+template <typename T>
+__device__ __forceinline__ void engine_stage(DevState *st, int j, T *scratch, double *hf_pre) {
+  constexpr int ld = kMaxM + 1;
+  T *sH = scratch + 2 * kMaxM + 2;
+  const T *HcT = hc_copy<T>(st);
+  for (int e = threadIdx.x; e < (j > 1 ? (j - 1) * ld : 0); e += blockDim.x) cp_async_elem(sH + e, HcT + e);
+  if (j >= 1)
+    for (int r = threadIdx.x; r < j; r += blockDim.x) cp_async_elem(hf_pre + r, st->Hf + (int64_t)(j - 1) * ld + r);
+  asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 // Givens step for column j-1 (completed by the scalar engine of this iteration), the
@@ -466,31 +484,37 @@ __global__ void __launch_bounds__(kDotThreads, 1) k_dcgs_dots(const T *__restric
   extern __shared__ __align__(16) double dsm[];
   __shared__ T s_acc[kDotWarps][kAccLd];
   __shared__ T s_c[3][2 * kMaxR + 1];
+  __shared__ double s_hfpre[kMaxM + 1];
   for (int e = threadIdx.x; e < kDotWarps * kAccLd; e += blockDim.x) (&s_acc[0][0])[e] = (T)0;
   // launched as a programmatic dependent of the previous kernel (pass B of the last
   // iteration): nothing it writes is read before this wait
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  if (MV != 0 && threadIdx.x < 3 * (2 * kMaxR + 1))
-    s_c[threadIdx.x / (2 * kMaxR + 1)][threadIdx.x % (2 * kMaxR + 1)] =
-        (T)st->coef[threadIdx.x / (2 * kMaxR + 1)][threadIdx.x % (2 * kMaxR + 1)];
-  __syncthreads();
-  if (st->active == 0) return;
-  const int k = j + 1;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const VT *vjp = reinterpret_cast<const VT *>(V + (int64_t)j * ldv);
-  const int wcol = (st->hist_base + woff) % st->mmax;
-  const VT *wp = reinterpret_cast<const VT *>(Pyb + (int64_t)wcol * ldh);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t iters = (nv + 2 * stride - 1) / (2 * stride);
+  // the state this pass needs is read in one batch of independent loads (the active flag,
+  // the ring positions, the stencil coefficients) before anything waits on one of them
+  const int active = st->active;
   int64_t nvg = nv;   // vectors inside the grid (the rest of the column is zero padding)
   const T *xin = nullptr;
   VT *wout = nullptr, *xcp = nullptr;
+  const VT *wp = nullptr;
   if constexpr (MV != 0) {
     nvg = (int64_t)mv.nx * mv.ny * mv.nz / W;
     xin = mv.x.get();
     wout = reinterpret_cast<VT *>(mv.w.get());
     xcp = mv.xcopy.base ? reinterpret_cast<VT *>(mv.xcopy.get()) : nullptr;
+    if (threadIdx.x < 3 * (2 * kMaxR + 1))
+      s_c[threadIdx.x / (2 * kMaxR + 1)][threadIdx.x % (2 * kMaxR + 1)] =
+          (T)st->coef[threadIdx.x / (2 * kMaxR + 1)][threadIdx.x % (2 * kMaxR + 1)];
+  } else {
+    wp = reinterpret_cast<const VT *>(Pyb + (int64_t)((st->hist_base + woff) % st->mmax) * ldh);
   }
+  if (active) engine_stage<T>(st, j, reinterpret_cast<T *>(dsm), s_hfpre);
+  __syncthreads();
+  if (active == 0) return;
+  const int k = j + 1;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const VT *vjp = reinterpret_cast<const VT *>(V + (int64_t)j * ldv);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t iters = (nv + 2 * stride - 1) / (2 * stride);
   // columns below `hot` stay resident in L2 between the passes and iterations
   const uint64_t pol_last = l2_evict_last(), pol_first = l2_evict_first();
   const uint64_t pol_j = j < hot ? pol_last : pol_first;
@@ -545,9 +569,12 @@ __global__ void __launch_bounds__(kDotThreads, 1) k_dcgs_dots(const T *__restric
     for (int g = 0; g < kDotWarps; ++g) s += s_acc[g][half * (kMaxM + 1) + i];
     partial[(int64_t)t * kMaxCta + blockIdx.x] = s;
   }
-  if (!last_block_arrive(&st->counter[1])) return;
+  if (!last_block_arrive(&st->counter[1])) {
+    cp_async_wait_all();   // no copies left in flight when the CTA exits
+    return;
+  }
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  dcgs_scalar<T>(st, j, final_step, partial, gridDim.x, reinterpret_cast<T *>(dsm));
+  dcgs_scalar<T>(st, j, final_step, partial, gridDim.x, reinterpret_cast<T *>(dsm), s_hfpre);
   last_block_reset(&st->counter[1]);
 }
 
@@ -569,26 +596,29 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_dcgs_update(T *__restrict__ 
   // the next pass A (a programmatic dependent of this grid) may be scheduled onto SMs as
   // this grid's CTAs retire; it waits for this grid's completion before reading its data
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  if (st->active == 0) return;   // the cycle ended: nothing to do
   extern __shared__ __align__(16) double dsm[];
   // block 0 is the Givens CTA: the first block is scheduled first, so it runs alongside the
   // streaming CTAs instead of waiting for a free slot after them
   if (blockIdx.x == 0) {
+    if (st->active == 0) return;   // the cycle ended: nothing to do
     dcgs_givens(st, j, final_step, mixed, dsm);
     return;
   }
   using VT = typename Vec<T>::type;
   __shared__ T s_sa[kMaxM], s_sd[kMaxM];
+  // the active flag, the coefficients and the ring position in one batch of independent loads
+  const int active = st->active;
   const T *cA = coef_copy<T>(st, 0), *cD = coef_copy<T>(st, 1), *c3 = coef_copy<T>(st, 2);
   for (int i = threadIdx.x; i < kMaxM; i += blockDim.x) {
     s_sa[i] = (i < j) ? cA[i] : (T)0;
     s_sd[i] = (i < j) ? cD[i] : (T)0;
   }
   const T sv = c3[0], cv = c3[1], sw = c3[2];
+  const VT *w = reinterpret_cast<const VT *>(Pyb + (int64_t)((st->hist_base + woff) % st->mmax) * ldh);
   __syncthreads();
+  if (active == 0) return;   // the cycle ended: nothing to do
   VT *vj = reinterpret_cast<VT *>(V + (int64_t)j * ldv);
   VT *vn = reinterpret_cast<VT *>(V + (int64_t)(j + 1) * ldv);
-  const VT *w = reinterpret_cast<const VT *>(Pyb + (int64_t)((st->hist_base + woff) % st->mmax) * ldh);
   const int64_t stride = (int64_t)(gridDim.x - 1) * blockDim.x;   // streaming CTAs
   // columns below `hot` stay resident in L2 (as in pass A); v_j and v_{j+1} are stored with
   // the policy of their column, the others are read with evict_first

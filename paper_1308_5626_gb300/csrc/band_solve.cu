@@ -477,18 +477,8 @@ constexpr int kTailSmem = 200 * 1024;   // shared memory of the single-CTA top l
 // time.  Shared layout: element e of the array for CTA slot t at e * nt + t (nt = groups per
 // CTA), the global layout with stride nt.
 template <typename T>
-__device__ __forceinline__ void cp_async_elem(T *dst, const T *src) {
-  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
-  if constexpr (sizeof(T) == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
-  else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
-}
-template <typename T>
 __device__ __forceinline__ void stage_group(T *dst, const T *src, int cnt, int G, int g, int nt, int t) {
   for (int e = 0; e < cnt; ++e) cp_async_elem(dst + e * nt + t, src + (int64_t)e * G + g);
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // Shared memory of the staged factors (elements of T) for nt groups of q blocks: the down

@@ -58,6 +58,20 @@ inline OutRef<T> ring_out(T *base, int64_t ld, const int *counter, int mmax, int
   return OutRef<T>{base, ld, counter, mmax, off};
 }
 
+// One 4- or 8-byte asynchronous copy global -> shared (cp.async), and the wait for all of
+// the calling thread's copies.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "cp.async element of 4 or 8 bytes");
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  if constexpr (sizeof(T) == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 int reduce_grid(int64_t n);
 // The 3D geometry is taken by the z-marching tiled stencil (x a whole number of tiles of
 // 32 16-byte vectors, y of 8 rows).
