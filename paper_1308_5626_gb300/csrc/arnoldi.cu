@@ -748,7 +748,10 @@ void launch_arnoldi(int j, int final_step, int64_t n, T *V, int64_t ldv, const T
   const int woff = 1 + j;   // ring column of w_j relative to the cycle's restart column
   const int64_t nv = (ldv + Vec<T>::W - 1) / Vec<T>::W;
   {
-    const int grid = arnoldi_grid();
+    // one CTA per SM at most, and no more CTAs than two vectors per thread need: a small
+    // system leaves the other SMs to the work on other streams (and the engine sums fewer
+    // partials)
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(arnoldi_grid(), (nv + 2 * kDotThreads - 1) / (2 * kDotThreads)));
     const size_t sm = (size_t)kScalarDoubles * sizeof(double);
     // the folded matvec is instantiated per dimension and stencil radius: 8 ndim + R
     const int sel = (mv && !final_step) ? 8 * m.ndim + m.R : 0;
