@@ -144,9 +144,23 @@ struct psp_ctx {
   psp_profile prof{};
   double *hostbuf = nullptr;   // pinned staging for psp_step_host
   double *dev_un = nullptr, *dev_unp1 = nullptr;
+  // host waits of psp_step: a stream synchronisation (the driver spins), or with
+  // blocking_wait a blocking-sync event, on which the thread sleeps -- set by psp_step_batch
+  // when it runs more threads than the host has cores
+  bool blocking_wait = false;
+  cudaEvent_t wait_ev = nullptr;
 };
 
 namespace {
+
+// Wait for everything enqueued on s so far (see psp_ctx::blocking_wait).
+cudaError_t host_wait(psp_ctx *h, cudaStream_t s) {
+  if (h->blocking_wait && h->wait_ev) {
+    cudaError_t e = cudaEventRecord(h->wait_ev, s);
+    return e != cudaSuccess ? e : cudaEventSynchronize(h->wait_ev);
+  }
+  return cudaStreamSynchronize(s);
+}
 
 void set_coef(const psp_ctx *h, double dt, double (*coef)[2 * kMaxR + 1]) {
   for (int d = 0; d < 3; ++d)
@@ -244,7 +258,7 @@ psp_status factor_into(psp_ctx *h, int slot, const double *band) {
     if (e != cudaSuccess) return fail(PSP_ERR_CUDA, std::string("band factorisation launch: ") + cudaGetErrorString(e));
   }
   PSP_CUDA(cudaMemcpyAsync(h->int_host, h->dev_int, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-  PSP_CUDA(cudaStreamSynchronize(h->stream));
+  PSP_CUDA(host_wait(h, h->stream));
   if (h->int_host[0]) return fail(PSP_ERR_NUMERIC, "band factorisation: zero or non-finite pivot");
   return PSP_OK;
 }
@@ -258,7 +272,7 @@ psp_status fit_into(psp_ctx *h, const TH *Px, const TH *Py, int64_t ld, int M, d
     if (e != cudaSuccess) return fail(PSP_ERR_CUDA, std::string("band fit launch: ") + cudaGetErrorString(e));
   }
   PSP_CUDA(cudaMemcpyAsync(h->int_host + 1, h->dev_int + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-  PSP_CUDA(cudaStreamSynchronize(h->stream));
+  PSP_CUDA(host_wait(h, h->stream));
   if (singular) *singular = h->int_host[1];
   return PSP_OK;
 }
@@ -423,6 +437,7 @@ psp_status psp_destroy(psp_handle h) {
   if (h->int_host) cudaFreeHost(h->int_host);
   if (h->hostbuf) cudaFreeHost(h->hostbuf);
   if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->wait_ev) cudaEventDestroy(h->wait_ev);
   delete h;
   return PSP_OK;
 }
@@ -593,7 +608,7 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
   bool adopted_now = false;   // the candidate was adopted in this step (band copied at its end)
   if (try_cand) {   // the history length to restore if the trial cycle breaks down
     PSP_CUDA(cudaMemcpyAsync(h->int_host + 3, &h->st->hist_count, sizeof(int), cudaMemcpyDeviceToHost, s));
-    PSP_CUDA(cudaStreamSynchronize(s));
+    PSP_CUDA(host_wait(h, s));
     hist_before_trial = h->int_host[3];
   }
   for (int c = 0; c < h->opts.max_restarts; ++c) {
@@ -601,7 +616,7 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
     psp_status ps = ensure_graph(h, which);
     if (ps != PSP_OK) return ps;
     PSP_CUDA(cudaGraphLaunch(h->graph[which], s));
-    PSP_CUDA(cudaStreamSynchronize(s));
+    PSP_CUDA(host_wait(h, s));
     const CycleSummary sm = *h->sum_host;
     cycles += 1;
     iters += sm.k_end;
@@ -621,7 +636,7 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
       PSP_CUDA(cudaMemcpyAsync(h->X, u_n, n * 8, cudaMemcpyDeviceToDevice, s));
       h->int_host[3] = hist_before_trial;
       PSP_CUDA(cudaMemcpyAsync(&h->st->hist_count, h->int_host + 3, sizeof(int), cudaMemcpyHostToDevice, s));
-      PSP_CUDA(cudaStreamSynchronize(s));
+      PSP_CUDA(host_wait(h, s));
       if (adopted_now) {
         h->adopted = prev_adopted;
         h->adopted_version += 1;
@@ -684,7 +699,7 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
   int hist = 0;
   {
     PSP_CUDA(cudaMemcpyAsync(h->int_host + 2, &h->st->hist_count, sizeof(int), cudaMemcpyDeviceToHost, s));
-    PSP_CUDA(cudaStreamSynchronize(s));
+    PSP_CUDA(host_wait(h, s));
     hist = std::min(h->int_host[2], h->mmax);
   }
   const int need = 2 * h->b + (h->opts.intercept ? 2 : 1);
@@ -730,6 +745,15 @@ psp_status psp_step_batch(psp_handle *hs, int count, const double *const *u_n, d
   int dev = 0;
   cudaGetDevice(&dev);
   const int nt = std::max(1, std::min(nthreads < 1 ? 1 : nthreads, std::max(count, 1)));
+  // more threads than cores: the threads wait on blocking-sync events instead of spinning
+  const unsigned cores = std::thread::hardware_concurrency();
+  const bool block = cores > 0 && (unsigned)nt > cores;
+  for (int i = 0; i < count; ++i) {
+    if (block && !hs[i]->wait_ev &&
+        cudaEventCreateWithFlags(&hs[i]->wait_ev, cudaEventBlockingSync | cudaEventDisableTiming) != cudaSuccess)
+      return fail(PSP_ERR_CUDA, "blocking-sync event");
+    hs[i]->blocking_wait = block;
+  }
   // instances are taken from a shared counter in order; every worker thread steps one
   // handle at a time on that handle's own stream, so the GPU runs nt instances' cycle
   // graphs concurrently while each thread waits for its instance's cycle summaries
@@ -760,6 +784,7 @@ psp_status psp_step_batch(psp_handle *hs, int count, const double *const *u_n, d
   for (int t = 1; t < nt; ++t) pool.emplace_back(work);
   work();
   for (auto &th : pool) th.join();
+  for (int i = 0; i < count; ++i) hs[i]->blocking_wait = false;
   if (first_err.load() != (int)PSP_OK)
     return fail((psp_status)first_err.load(), "at least one instance of the batch failed (see statuses)");
   return noconv.load() ? fail(PSP_ERR_NOCONV, "an instance reached max_restarts") : PSP_OK;
