@@ -4,49 +4,86 @@ the final update X = X_0 + N^{-1} Z.
 The paper notes that for d = 1 (tridiagonal N) the solve is the O(n) Thomas algorithm;
 wider bands are a banded LU.  Band storage throughout: band[i, p] = N(i, i + p - d)
 for p = 0..2d (entries whose column falls outside [0, n) are ignored).
+
+Cyclic band (``cyclic=True``, not in the paper): the same storage read with the column
+index taken modulo n, band[i, p] = N(i, (i + p - d) mod n) -- the structure of a periodic
+1D stencil, whose first and last d rows couple to the other end of the grid.  Its solve is
+the plain definition: a sparse LU of the assembled matrix.
 """
 from __future__ import annotations
 
 import numpy as np
 import scipy.linalg
+import scipy.sparse
+import scipy.sparse.linalg
 
 
-def band_to_dense(band: np.ndarray, d: int) -> np.ndarray:
+def _check_cyclic(n: int, d: int):
+    if n < 2 * d + 1:
+        raise ValueError("a cyclic band needs n >= 2d + 1 (distinct columns per row)")
+
+
+def band_to_dense(band: np.ndarray, d: int, cyclic: bool = False) -> np.ndarray:
     n = band.shape[0]
+    if cyclic:
+        _check_cyclic(n, d)
     A = np.zeros((n, n))
     for i in range(n):
         for p in range(2 * d + 1):
             j = i + p - d
-            if 0 <= j < n:
+            if cyclic:
+                A[i, j % n] = band[i, p]
+            elif 0 <= j < n:
                 A[i, j] = band[i, p]
     return A
 
 
-def dense_to_band(A: np.ndarray, d: int) -> np.ndarray:
+def dense_to_band(A: np.ndarray, d: int, cyclic: bool = False) -> np.ndarray:
     n = A.shape[0]
+    if cyclic:
+        _check_cyclic(n, d)
     band = np.zeros((n, 2 * d + 1))
     for i in range(n):
         for p in range(2 * d + 1):
             j = i + p - d
-            if 0 <= j < n:
+            if cyclic:
+                band[i, p] = A[i, j % n]
+            elif 0 <= j < n:
                 band[i, p] = A[i, j]
     return band
 
 
-def transpose_band(band: np.ndarray, d: int) -> np.ndarray:
-    """Band storage of N^T: N^T(i, i + p - d) = N(i + p - d, i)."""
+def transpose_band(band: np.ndarray, d: int, cyclic: bool = False) -> np.ndarray:
+    """Band storage of N^T: N^T(i, i + p - d) = N(i + p - d, i) (row index modulo n for a
+    cyclic band)."""
     n = band.shape[0]
     out = np.zeros_like(band)
     for i in range(n):
         for p in range(2 * d + 1):
             j = i + p - d
-            if 0 <= j < n:
+            if cyclic:
+                out[i, p] = band[j % n, 2 * d - p]
+            elif 0 <= j < n:
                 out[i, p] = band[j, 2 * d - p]
     return out
 
 
-def solve(band: np.ndarray, d: int, v: np.ndarray, transpose: bool = False) -> np.ndarray:
-    """N^{-1} v (or N^{-T} v): LAPACK banded LU with partial pivoting."""
+def _cyclic_sparse(band: np.ndarray, d: int):
+    n = band.shape[0]
+    _check_cyclic(n, d)
+    rows = np.repeat(np.arange(n), 2 * d + 1)
+    cols = (rows + np.tile(np.arange(2 * d + 1) - d, n)) % n
+    return scipy.sparse.csc_matrix((band.reshape(-1), (rows, cols)), shape=(n, n))
+
+
+def solve(band: np.ndarray, d: int, v: np.ndarray, transpose: bool = False, cyclic: bool = False) -> np.ndarray:
+    """N^{-1} v (or N^{-T} v): LAPACK banded LU with partial pivoting; for a cyclic band a
+    sparse LU (SuperLU) of the assembled matrix."""
+    if cyclic:
+        S = _cyclic_sparse(np.asarray(band, dtype=np.float64), d)
+        if transpose:
+            S = S.T.tocsc()
+        return scipy.sparse.linalg.splu(S).solve(np.asarray(v, dtype=np.float64))
     if transpose:
         band = transpose_band(band, d)
     n = band.shape[0]

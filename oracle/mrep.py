@@ -18,6 +18,10 @@ Readings (listed with the others in the design notes):
   N*(j) multiplies.
 * ``intercept=False`` drops the row of ones (and the boundary intercept): a (2d+1)^2
   Gram of lagged products of P_x alone.  The paper's form is ``intercept=True``.
+* ``cyclic=True`` (not in the paper): every row, the first and last d included, regresses
+  on the rows i-d .. i+d taken modulo n, and the band is read cyclically
+  (band[i, p] = N(i, (i + p - d) mod n)).  For a periodic 1D grid that is the structure
+  of A itself, so a history that spans it recovers A exactly.
 * Singular rows.  The normal equations are factored by Cholesky; a row whose relative
   pivot L_jj^2 / G_jj (the share of regressor j not explained by the ones before it)
   is <= 1e-12, or that fails to factor, is degenerate and gets the identity row
@@ -83,8 +87,9 @@ def linear_fit(x: np.ndarray, y: np.ndarray, intercept: bool = True) -> Tuple[fl
     return 0.0, float(beta[0]), sing
 
 
-def mrep(Px: np.ndarray, Py: np.ndarray, d: int, intercept: bool = True):
-    """N in band storage band[i, p] = N(i, i + p - d), and the per-row singular flags."""
+def mrep(Px: np.ndarray, Py: np.ndarray, d: int, intercept: bool = True, cyclic: bool = False):
+    """N in band storage band[i, p] = N(i, i + p - d) (modulo n when cyclic), and the per-row
+    singular flags."""
     Px = np.asarray(Px, dtype=np.float64)
     Py = np.asarray(Py, dtype=np.float64)
     n, m = Px.shape
@@ -94,6 +99,14 @@ def mrep(Px: np.ndarray, Py: np.ndarray, d: int, intercept: bool = True):
         raise ValueError("need n >= 2d + 1 rows")
     band = np.zeros((n, 2 * d + 1))
     singular = np.zeros(n, dtype=bool)
+    if cyclic:
+        # every row is an interior row of the periodic grid: pad P_x with d wrapped rows on
+        # each side and fit all n rows as the interior rows of the padded history
+        Pad = np.concatenate([Px[n - d:], Px, Px[:d]], axis=0)
+        Ypad = np.concatenate([Py[n - d:], Py, Py[:d]], axis=0)
+        bp, sp = _interior(Pad, Ypad, d, intercept, band=np.zeros((n + 2 * d, 2 * d + 1)),
+                           singular=np.zeros(n + 2 * d, dtype=bool))
+        return bp[d:d + n], sp[d:d + n]
 
     # first d and last d rows: simple linear fit, N(i, i) = beta_1
     for i in list(range(d)) + list(range(n - d, n)):
@@ -104,7 +117,12 @@ def mrep(Px: np.ndarray, Py: np.ndarray, d: int, intercept: bool = True):
         else:
             band[i, d] = b1
 
-    # interior rows i = d .. n-d-1: regress P_y(i, :) on [1; P_x(i-d .. i+d, :)]
+    return _interior(Px, Py, d, intercept, band, singular)
+
+
+def _interior(Px, Py, d, intercept, band, singular):
+    """Rows i = d .. n-d-1: regress P_y(i, :) on [1; P_x(i-d .. i+d, :)]."""
+    n, m = Px.shape
     win = sliding_window_view(Px, 2 * d + 1, axis=0)      # win[r, c, j] = Px[r + j, c]
     off = 1 if intercept else 0
     q = 2 * d + 1 + off

@@ -21,6 +21,9 @@ open (listed with the others in the design notes):
   candidate waits w steps (w = 1, 2, 4, ... doubling with consecutive rejections).  The
   reference rate is that of the cycles of the last step run with the adopted
   preconditioner.
+* ``cyclic=True`` (not in the paper): the fit and the solve use the cyclic band (every
+  row regresses on its wrapped neighbours; see mrep and banded), the structure of A on a
+  periodic 1D grid.
 """
 from __future__ import annotations
 
@@ -55,7 +58,7 @@ def _rate(R_end: float, beta: float, k: int) -> float:
 class Stepper:
     def __init__(self, op: Operator, b: int, m: int, intercept: bool = True,
                  max_restarts: int = 200, max_hist: Optional[int] = None, gs: str = "mgs",
-                 accept_rule: bool = True):
+                 accept_rule: bool = True, cyclic: bool = False):
         self.op = op
         self.b = int(b)
         self.m = int(m)
@@ -64,6 +67,7 @@ class Stepper:
         self.max_hist = int(max_hist) if max_hist else 2 * (self.m + 1)
         self.gs = gs
         self.accept_rule = bool(accept_rule)
+        self.cyclic = bool(cyclic)
         self.N: Optional[np.ndarray] = None          # adopted preconditioner (None = I)
         self.candidate: Optional[np.ndarray] = None  # freshly fitted, not yet tried
         self.rate_ref: Optional[float] = None
@@ -78,7 +82,7 @@ class Stepper:
         if band is None:
             return None
         d = self.b
-        return lambda v: banded.solve(band, d, v)
+        return lambda v: banded.solve(band, d, v, cyclic=self.cyclic)
 
     def step(self, u_n: np.ndarray, dt: float, tol: float):
         u_n = np.asarray(u_n, dtype=np.float64)
@@ -138,7 +142,7 @@ class Stepper:
         if cols >= need:
             Px = np.stack(self.hist_x, axis=1)
             Py = np.stack(self.hist_y, axis=1)
-            band, flags = mrep.mrep(Px, Py, self.b, self.intercept)
+            band, flags = mrep.mrep(Px, Py, self.b, self.intercept, cyclic=self.cyclic)
             self.candidate = band
             sing = int(flags.sum())
             refit = True
