@@ -57,6 +57,7 @@ def _args():
     ap.add_argument("--no-standalone", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-e1", action="store_true")
+    ap.add_argument("--no-cyclic", action="store_true")
     ap.add_argument("--batch", type=int, default=512, help="instances of the batched line (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--batch-threads", type=int, default=16)
@@ -417,6 +418,48 @@ def _e1_line(device):
                              "n = 700 (its restart length and tolerance are not stated)"}
 
 
+def _cyclic_line(device, steps: int = 10):
+    """The cyclic band on the 1D workload (inputs.c1 recipe at n = 1024 and n = 2^20): FP64
+    and mixed, the paper's boundary rows against the cyclic band (N = A fitted exactly):
+    iterations per step over `steps` steps after two warm-up steps (the first runs with
+    N = I and makes the fit; at n = 2^20 it may reach max_restarts, which the warm-up
+    tolerates), and implicit steps/s (CUDA events around the timed steps)."""
+    import torch
+    from paper_1308_5626_gb300 import inputs, psp
+    rows = []
+    for n in (1024, 1 << 20):
+        w = inputs.c1(n)
+        for prec in (psp.PSP_FP64, psp.PSP_MIXED):
+            for cyc in (0, 1):
+                stream = torch.cuda.Stream(device=device)
+                with torch.cuda.stream(stream):
+                    s = psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=prec, stream=stream, cyclic=cyc)
+                    u = torch.tensor(w.u0, dtype=torch.float64, device=device)
+                    out = torch.empty_like(u)
+                    warm_its = []
+                    for _ in range(2):   # at n = 2^20 the N = I step may stall; it only makes the fit
+                        _, info = s.step(u, w.dt, w.tol, out=out, allow_noconv=True)
+                        warm_its.append(int(info.iters))
+                        u, out = out, u
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    its = 0
+                    e0.record(stream)
+                    for _ in range(steps):
+                        _, info = s.step(u, w.dt, w.tol, out=out)
+                        its += info.iters
+                        u, out = out, u
+                    e1.record(stream)
+                    torch.cuda.synchronize(device)
+                    ms = e0.elapsed_time(e1) / steps
+                    s.close()
+                rows.append({"n": n, "form": "fp64" if prec == psp.PSP_FP64 else "mixed",
+                             "band": "cyclic" if cyc else "paper boundary rows",
+                             "warmup_iters": warm_its, "iters_per_step": its / steps, "ms_per_step": ms,
+                             "steps_per_s": 1e3 / ms})
+    return {"workload": "c1_1d_adv_diff (4th order, CFL 10, b = 2, m = 30, tol 1e-10)", "rows": rows}
+
+
 def _batch_line(device, count: int, steps: int, nthreads: int):
     """The batched workload: `count` independent instances (inputs.c4_instance: 1D/2D, n from
     2^10 to 2^18, orders 2-8, b 1-4, CFL 1-20, mixed form, tol 1e-8), each on its own stream,
@@ -640,6 +683,9 @@ def main():
     batch = None
     if a.batch > 0 and rank == 0:
         batch = _batch_line(device, a.batch, a.batch_steps, a.batch_threads)
+    cyclic = None
+    if not a.no_cyclic and rank == 0:
+        cyclic = _cyclic_line(device)
 
     if rank != 0:
         if world > 1:
@@ -709,6 +755,7 @@ def main():
         "adjoint": adj,
         "mock_test": e1,
         "batched": batch,
+        "cyclic_band": cyclic,
         "cpu_baseline": cpu, "clocks": clk,
     }
     if fp64:

@@ -93,6 +93,16 @@ typedef struct {
   int adjoint;       /* 0 (default): the handle solves with A = I - dt L.  1: with
                         A^T = I - dt L^T (every stencil mirrored, w_j -> w_-j, exact on the
                         periodic grid): the adjoint system of a step, for gradients. */
+  int cyclic;        /* 0 (default): Algorithm 2's boundary rows (the first and last b rows
+                        of N keep only N(i,i), from a simple linear fit).  1: cyclic band for a
+                        periodic 1D grid (psp_create with ndim = 1 and n >= 4b+2, else
+                        PSP_ERR_ARG): every row regresses on rows i-b..i+b modulo n, and the
+                        band storage reads band[i][p] = N(i, (i+p-b) mod n) everywhere (fit,
+                        psp_set_band, psp_get_band, the solves).  The solve treats the
+                        wrapped corner entries exactly (Sherman-Morrison-Woodbury on the
+                        in-range band; a singular capacitance matrix drops the N like a zero
+                        pivot).  Not in the paper; for a periodic 1D stencil N = A can then be
+                        fitted exactly. */
 } psp_opts;
 
 typedef struct {

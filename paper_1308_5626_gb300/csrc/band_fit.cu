@@ -11,7 +11,8 @@
 // 2(2b+1)+2 FP64 moments per row; a second kernel (k_fit_solve) assembles each row's
 // Gram from the moments of rows i-b..i+b and solves it by Cholesky in registers.  The
 // first and last b rows take the slope of the simple linear fit on P_x(i,:) (diagonal
-// of N only), as the paper prescribes.  A row whose relative Cholesky pivot is <= 1e-12
+// of N only), as the paper prescribes; with a cyclic band (periodic 1D grid) every row is an
+// interior row and the neighbour indices wrap modulo n.  A row whose relative Cholesky pivot is <= 1e-12
 // (regressors collinear in the sample) gets the identity row and is counted.
 //
 // Moments of an FP32 history are accumulated in double-float (an FP32 pair): every product
@@ -60,7 +61,7 @@ template <> struct FitAcc<float> { using type = AccF2; };
 template <typename TH, int B>
 __global__ void __launch_bounds__(kFitRows) k_fit_moments(int64_t n, int M, const TH *__restrict__ Px,
                                                           const TH *__restrict__ Py, int64_t ld,
-                                                          double *__restrict__ mom) {
+                                                          double *__restrict__ mom, int cyclic) {
   constexpr int TW = kFitRows + 3 * B;   // P_x rows r0-B .. r0+kFitRows+2B-1
   constexpr int NM = 4 * B + 4;
   using Acc = typename FitAcc<TH>::type;
@@ -76,7 +77,8 @@ __global__ void __launch_bounds__(kFitRows) k_fit_moments(int64_t n, int M, cons
       const TH *px = Px + (int64_t)(c0 + cc) * ld;
       const TH *py = Py + (int64_t)(c0 + cc) * ld;
       for (int t = tid; t < TW; t += kFitRows) {
-        const int64_t row = r0 - B + t;
+        int64_t row = r0 - B + t;
+        if (cyclic) row = ((row % n) + n) % n;   // periodic neighbours
         sx[cc][t] = (cc < nc && row >= 0 && row < n) ? px[row] : (TH)0;
       }
       const int64_t row = r0 + tid;
@@ -156,7 +158,7 @@ __device__ __forceinline__ bool chol_solve(double (&G)[Q][Q], double (&rhs)[Q], 
 template <int B>
 __global__ void __launch_bounds__(128) k_fit_solve(int64_t n, int M, int intercept,
                                                    const double *__restrict__ mom, double *__restrict__ band,
-                                                   int *singular_count) {
+                                                   int *singular_count, int cyclic) {
   constexpr int NM = 4 * B + 4;
   constexpr int W = 2 * B + 1;
   constexpr int Q = 2 * B + 2;
@@ -166,7 +168,13 @@ __global__ void __launch_bounds__(128) k_fit_solve(int64_t n, int M, int interce
   const double *mi = mom + i * NM;
   bool ok;
   double beta[Q];
-  const bool interior = (i >= B) && (i < n - B);
+  const bool interior = cyclic || ((i >= B) && (i < n - B));
+  // moments of row i - B + p (taken modulo n for a cyclic band)
+  auto mrow = [&](int p) -> const double * {
+    int64_t r = i - B + p;
+    r += (r < 0) ? n : ((r >= n) ? -n : 0);
+    return mom + r * NM;
+  };
   if (interior) {
     double G[Q][Q], rhs[Q];
     const int o = intercept ? 1 : 0;
@@ -175,7 +183,7 @@ __global__ void __launch_bounds__(128) k_fit_solve(int64_t n, int M, int interce
       G[0][0] = (double)M;
 #pragma unroll
       for (int p = 0; p < W; ++p) {
-        const double s = mom[(i - B + p) * NM + 4 * B + 2];
+        const double s = mrow(p)[4 * B + 2];
         G[0][1 + p] = s;
         G[1 + p][0] = s;
       }
@@ -187,7 +195,7 @@ __global__ void __launch_bounds__(128) k_fit_solve(int64_t n, int M, int interce
       for (int qq = 0; qq < W; ++qq) {
         const int lo = p < qq ? p : qq;
         const int lag = p < qq ? qq - p : p - qq;
-        const double v = mom[(i - B + lo) * NM + lag];
+        const double v = mrow(lo)[lag];
         if (intercept) G[1 + p][1 + qq] = v; else G[p][qq] = v;
       }
       rhs[o + p] = mi[W + p];
@@ -216,14 +224,14 @@ __global__ void __launch_bounds__(128) k_fit_solve(int64_t n, int M, int interce
 
 template <typename TH>
 void launch_fit(int b, int intercept, int64_t n, int M, const TH *Px, const TH *Py, int64_t ld, double *moments,
-                double *band, int *singular_count, cudaStream_t s) {
+                double *band, int *singular_count, cudaStream_t s, int cyclic) {
   const int g1 = (int)((n + kFitRows - 1) / kFitRows);
   const int g2 = (int)((n + 127) / 128);
   switch (b) {
 #define PSP_FIT(B_)                                                                              \
   case B_:                                                                                       \
-    k_fit_moments<TH, B_><<<g1, kFitRows, 0, s>>>(n, M, Px, Py, ld, moments);                    \
-    k_fit_solve<B_><<<g2, 128, 0, s>>>(n, M, intercept, moments, band, singular_count);          \
+    k_fit_moments<TH, B_><<<g1, kFitRows, 0, s>>>(n, M, Px, Py, ld, moments, cyclic);            \
+    k_fit_solve<B_><<<g2, 128, 0, s>>>(n, M, intercept, moments, band, singular_count, cyclic);  \
     break;
     PSP_FIT(1) PSP_FIT(2) PSP_FIT(3) PSP_FIT(4)
 #undef PSP_FIT
@@ -232,8 +240,8 @@ void launch_fit(int b, int intercept, int64_t n, int M, const TH *Px, const TH *
 }
 
 template void launch_fit<float>(int, int, int64_t, int, const float *, const float *, int64_t, double *, double *,
-                                int *, cudaStream_t);
+                                int *, cudaStream_t, int);
 template void launch_fit<double>(int, int, int64_t, int, const double *, const double *, int64_t, double *,
-                                 double *, int *, cudaStream_t);
+                                 double *, int *, cudaStream_t, int);
 
 }  // namespace psp

@@ -26,6 +26,8 @@
 //   up:   x_I = p - W x_{s-1} - V x_s.
 // Arrays of a level are stored group-interleaved (element e of block i of group g at
 // (i*b*b + e)*G + g) so that the one-thread-per-group sweeps read coalesced.
+#include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "band_solve.cuh"
@@ -687,19 +689,83 @@ __global__ void __launch_bounds__(512) k_tail(const int *active, const LevelAppl
 }
 
 // N^T in band storage: bandT[i][p] = N^T(i, i+p-b) = N(i+p-b, i) = band[i+p-b][2b-p]
-// (zero where row i+p-b is outside [0, n)).
-__global__ void k_transpose_band(const double *__restrict__ band, double *__restrict__ bandT, int64_t n, int b) {
+// (zero where row i+p-b is outside [0, n); taken modulo n for a cyclic band).
+__global__ void k_transpose_band(const double *__restrict__ band, double *__restrict__ bandT, int64_t n, int b,
+                                 int cyclic) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int w = 2 * b + 1;
   for (int p = 0; p < w; ++p) {
-    const int64_t r = i + p - b;
+    int64_t r = i + p - b;
+    if (cyclic) r += (r < 0) ? n : ((r >= n) ? -n : 0);
     bandT[i * w + p] = (r >= 0 && r < n) ? band[r * w + (2 * b - p)] : 0.0;
   }
 }
 
-void launch_transpose_band(const double *band, double *bandT, int64_t n, int b, cudaStream_t s) {
-  k_transpose_band<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(band, bandT, n, b);
+void launch_transpose_band(const double *band, double *bandT, int64_t n, int b, cudaStream_t s, bool cyclic) {
+  k_transpose_band<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(band, bandT, n, b, cyclic ? 1 : 0);
+}
+
+// ---------------------------------------------------------------------------------------
+// cyclic band (Sherman-Morrison-Woodbury on the in-range band; see BandSolver::cyclic)
+// ---------------------------------------------------------------------------------------
+
+// Corner column c of the 2b: C_c = n-b+c for c < b, c-b otherwise.
+__device__ __forceinline__ int64_t corner_col(int64_t n, int b, int c) { return c < b ? n - b + c : c - b; }
+
+// u = U(:, c): the wrapped entries of N in column C_c (rows 0..b-1 and n-b..n-1).
+__global__ void k_corner_rhs(const double *__restrict__ band, int64_t n, int b, int c, double *__restrict__ u) {
+  const int w = 2 * b + 1;
+  const int64_t cc = corner_col(n, b, c);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    if (i < b || i >= n - b)
+      for (int p = 0; p < w; ++p) {
+        const int64_t col = i + p - b;
+        if (col < 0 && col + n == cc) v = band[i * w + p];
+        if (col >= n && col - n == cc) v = band[i * w + p];
+      }
+    u[i] = v;
+  }
+}
+
+// Z(:, c) = z (Z row-major n x 2b).
+__global__ void k_put_z(const double *__restrict__ z, double *__restrict__ Z, int64_t n, int w2, int c) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    Z[i * w2 + c] = z[i];
+}
+
+// Kc = Z(C, :) (2b x 2b), one thread.
+__global__ void k_gather_corner_rows(const double *__restrict__ Z, int64_t n, int b, double *__restrict__ Kc) {
+  const int w2 = 2 * b;
+  for (int r = 0; r < w2; ++r)
+    for (int c = 0; c < w2; ++c) Kc[r * w2 + c] = Z[corner_col(n, b, r) * w2 + c];
+}
+
+// y = yb - Z K^{-1} yb(C) (mode 0, into the fixed or ring column of yref), or X += that
+// (mode 1).  Every CTA forms s = K^{-1} yb(C) itself from the 2b gathered values.
+template <typename T>
+__global__ void __launch_bounds__(256) k_smw(const T *__restrict__ yb, const T *__restrict__ Z,
+                                             const T *__restrict__ Kinv, int64_t n, int b, const int *active,
+                                             OutRef<T> yref, double *X, int mode) {
+  if (active && *active == 0) return;
+  __shared__ T g[8], sv[8];
+  const int w2 = 2 * b;
+  if (threadIdx.x < w2) g[threadIdx.x] = yb[corner_col(n, b, threadIdx.x)];
+  __syncthreads();
+  if (threadIdx.x < w2) {
+    T acc = (T)0;
+    for (int c = 0; c < w2; ++c) acc += Kinv[threadIdx.x * w2 + c] * g[c];
+    sv[threadIdx.x] = acc;
+  }
+  __syncthreads();
+  T *y = (mode == 0) ? yref.get() : nullptr;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T v = yb[i];
+    for (int c = 0; c < w2; ++c) v -= Z[i * w2 + c] * sv[c];
+    if (mode == 0) y[i] = v;
+    else X[i] += (double)v;
+  }
 }
 
 __global__ void k_to_f32(const double *__restrict__ in, float *__restrict__ out, int64_t count) {
@@ -774,6 +840,11 @@ size_t BandSolver::slot_bytes() const {
     total += 5 * (((gq * 4 + 255) / 256) * 256) + 2 * (((gs * 4 + 255) / 256) * 256);  // FP32
     if (l + 1 < levels.size()) total += 3 * ((((size_t)(s.G - 1) * BB * 8 + 255) / 256) * 256);
   }
+  if (cyclic) {
+    const size_t nz = (size_t)n * 2 * b, nk = (size_t)4 * b * b;
+    total += ((nz * 8 + 255) / 256) * 256 + ((nz * 4 + 255) / 256) * 256;
+    total += ((nk * 8 + 255) / 256) * 256 + ((nk * 4 + 255) / 256) * 256;
+  }
   return total + 4096;
 }
 
@@ -788,7 +859,10 @@ static size_t apply_bytes_t(const std::vector<LevelShape> &lv, int b) {
   return total + 2 * ((((size_t)lv.size() * sizeof(LevelApply<T>)) + 255) / 256) * 256 + 4096;
 }
 
-size_t BandSolver::apply_bytes() const { return apply_bytes_t<double>(levels, b) + apply_bytes_t<float>(levels, b); }
+size_t BandSolver::apply_bytes() const {
+  const size_t cyc = cyclic ? 2 * ((((size_t)n * 8) + 255) / 256) * 256 : 0;
+  return apply_bytes_t<double>(levels, b) + apply_bytes_t<float>(levels, b) + cyc;
+}
 
 void BandSolver::bind(void *slot_mem, int slot) {
   char *p = reinterpret_cast<char *>(slot_mem);
@@ -814,6 +888,11 @@ void BandSolver::bind(void *slot_mem, int slot) {
       const size_t nn = (size_t)(s.G - 1) * BB;
       S.nLo[l] = carve<double>(p, nn); S.nDi[l] = carve<double>(p, nn); S.nUp[l] = carve<double>(p, nn);
     }
+  }
+  if (cyclic) {
+    const size_t nz = (size_t)n * 2 * b, nk = (size_t)4 * b * b;
+    S.Z64 = carve<double>(p, nz); S.Z32 = carve<float>(p, nz);
+    S.K64 = carve<double>(p, nk); S.K32 = carve<float>(p, nk);
   }
 }
 
@@ -868,6 +947,10 @@ void BandSolver::bind_apply(void *mem) {
   const std::vector<LevelF32> f32[kSlots] = {slots[0].h, slots[1].h, slots[2].h};
   bind_apply_t<double>(levels, b, p, f64, app64, dev_app64);
   bind_apply_t<float>(levels, b, p, f32, app32, dev_app32);
+  if (cyclic) {
+    cyc_y = carve<double>(p, (size_t)n);
+    cyc_u = carve<double>(p, (size_t)n);
+  }
   static bool attrs = false;
   if (!attrs) {
     attrs = true;
@@ -942,6 +1025,78 @@ static const LevelApply<float> *dev_of(const BandSolver &bs, int slot, float *) 
 template <typename T>
 void BandSolver::apply(int slot, const T *v, const double *scale, const int *active, OutRef<T> y, double *X,
                        int mode, cudaStream_t s) const {
+  if (!cyclic) {
+    apply_banded<T>(slot, v, scale, active, y, X, mode, s);
+    return;
+  }
+  T *yb = reinterpret_cast<T *>(cyc_y);
+  apply_banded<T>(slot, v, scale, active, fixed_out<T>(yb), nullptr, 0, s);
+  const Slot &S = slots[slot];
+  const T *Z = sizeof(T) == 8 ? reinterpret_cast<const T *>(S.Z64) : reinterpret_cast<const T *>(S.Z32);
+  const T *K = sizeof(T) == 8 ? reinterpret_cast<const T *>(S.K64) : reinterpret_cast<const T *>(S.K32);
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
+  k_smw<T><<<g, 256, 0, s>>>(yb, Z, K, n, b, active, y, X, mode);
+}
+
+bool BandSolver::prepare_cyclic(int slot, const double *band, cudaStream_t s) {
+  Slot &S = slots[slot];
+  const int w2 = 2 * b;
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
+  for (int c = 0; c < w2; ++c) {
+    k_corner_rhs<<<g, 256, 0, s>>>(band, n, b, c, cyc_u);
+    apply_banded<double>(slot, cyc_u, nullptr, nullptr, fixed_out<double>(cyc_y), nullptr, 0, s);
+    k_put_z<<<g, 256, 0, s>>>(cyc_y, S.Z64, n, w2, c);
+  }
+  k_gather_corner_rows<<<1, 1, 0, s>>>(S.Z64, n, b, S.K64);
+  std::vector<double> Kc((size_t)w2 * w2);
+  if (cudaMemcpyAsync(Kc.data(), S.K64, Kc.size() * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return false;
+  // K = I + Z(C, :), inverted by Gauss-Jordan elimination with partial pivoting in long double
+  std::vector<long double> M((size_t)w2 * 2 * w2, 0.0L);
+  long double scale = 0.0L;
+  for (int r = 0; r < w2; ++r)
+    for (int c = 0; c < w2; ++c) {
+      const long double v = (long double)Kc[(size_t)r * w2 + c] + (r == c ? 1.0L : 0.0L);
+      M[(size_t)r * 2 * w2 + c] = v;
+      scale = std::max(scale, std::fabs(v));
+    }
+  for (int r = 0; r < w2; ++r) M[(size_t)r * 2 * w2 + w2 + r] = 1.0L;
+  if (!(scale > 0.0L) || !std::isfinite((double)scale)) return false;
+  for (int col = 0; col < w2; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < w2; ++r)
+      if (std::fabs(M[(size_t)r * 2 * w2 + col]) > std::fabs(M[(size_t)piv * 2 * w2 + col])) piv = r;
+    if (!(std::fabs(M[(size_t)piv * 2 * w2 + col]) > 1e-13L * scale)) return false;
+    if (piv != col)
+      for (int c = 0; c < 2 * w2; ++c) std::swap(M[(size_t)piv * 2 * w2 + c], M[(size_t)col * 2 * w2 + c]);
+    const long double d = M[(size_t)col * 2 * w2 + col];
+    for (int c = 0; c < 2 * w2; ++c) M[(size_t)col * 2 * w2 + c] /= d;
+    for (int r = 0; r < w2; ++r) {
+      if (r == col) continue;
+      const long double f = M[(size_t)r * 2 * w2 + col];
+      if (f != 0.0L)
+        for (int c = 0; c < 2 * w2; ++c) M[(size_t)r * 2 * w2 + c] -= f * M[(size_t)col * 2 * w2 + c];
+    }
+  }
+  std::vector<double> K64((size_t)w2 * w2);
+  std::vector<float> K32((size_t)w2 * w2);
+  for (int r = 0; r < w2; ++r)
+    for (int c = 0; c < w2; ++c) {
+      const double v = (double)M[(size_t)r * 2 * w2 + w2 + c];
+      if (!std::isfinite(v)) return false;
+      K64[(size_t)r * w2 + c] = v;
+      K32[(size_t)r * w2 + c] = (float)v;
+    }
+  launch_to_f32(S.Z64, S.Z32, n * w2, s);
+  return cudaMemcpyAsync(S.K64, K64.data(), K64.size() * 8, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+         cudaMemcpyAsync(S.K32, K32.data(), K32.size() * 4, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+         cudaStreamSynchronize(s) == cudaSuccess;
+}
+
+template <typename T>
+void BandSolver::apply_banded(int slot, const T *v, const double *scale, const int *active, OutRef<T> y, double *X,
+                              int mode, cudaStream_t s) const {
   const std::vector<LevelApply<T>> &a = apps_of<T>(*this, slot);
   const LevelApply<T> *dev = dev_of(*this, slot, (T *)nullptr);
   switch (b) {
@@ -953,6 +1108,10 @@ void BandSolver::apply(int slot, const T *v, const double *scale, const int *act
   }
 }
 
+template void BandSolver::apply_banded<float>(int, const float *, const double *, const int *, OutRef<float>,
+                                              double *, int, cudaStream_t) const;
+template void BandSolver::apply_banded<double>(int, const double *, const double *, const int *, OutRef<double>,
+                                               double *, int, cudaStream_t) const;
 template void BandSolver::apply<float>(int, const float *, const double *, const int *, OutRef<float>, double *,
                                        int, cudaStream_t) const;
 template void BandSolver::apply<double>(int, const double *, const double *, const int *, OutRef<double>,

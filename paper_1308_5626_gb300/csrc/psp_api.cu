@@ -260,13 +260,19 @@ psp_status factor_into(psp_ctx *h, int slot, const double *band) {
   PSP_CUDA(cudaMemcpyAsync(h->int_host, h->dev_int, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   PSP_CUDA(host_wait(h, h->stream));
   if (h->int_host[0]) return fail(PSP_ERR_NUMERIC, "band factorisation: zero or non-finite pivot");
+  // cyclic band: the corner columns' solves and the capacitance matrix of the slot
+  if (h->bs.cyclic && !h->bs.prepare_cyclic(slot, band, h->stream)) {
+    cudaGetLastError();
+    return fail(PSP_ERR_NUMERIC, "cyclic band: singular capacitance matrix");
+  }
   return PSP_OK;
 }
 
 template <typename TH>
 psp_status fit_into(psp_ctx *h, const TH *Px, const TH *Py, int64_t ld, int M, double *band, int *singular) {
   PSP_CUDA(cudaMemsetAsync(h->dev_int + 1, 0, sizeof(int), h->stream));
-  launch_fit<TH>(h->b, h->opts.intercept, h->geo.n, M, Px, Py, ld, h->moments, band, h->dev_int + 1, h->stream);
+  launch_fit<TH>(h->b, h->opts.intercept, h->geo.n, M, Px, Py, ld, h->moments, band, h->dev_int + 1, h->stream,
+                 h->opts.cyclic);
   {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(PSP_ERR_CUDA, std::string("band fit launch: ") + cudaGetErrorString(e));
@@ -316,7 +322,7 @@ double rate_of(double R_end, double beta, int k) {
 // Slot 2 holds the factors of N^T for the adopted N (made on first use after a change).
 psp_status ensure_transposed(psp_ctx *h) {
   if (h->t_version == h->adopted_version) return PSP_OK;
-  launch_transpose_band(h->band_adopted, h->band_T, h->geo.n, h->b, h->stream);
+  launch_transpose_band(h->band_adopted, h->band_T, h->geo.n, h->b, h->stream, h->bs.cyclic);
   PSP_CUDA(cudaGetLastError());
   psp_status s = factor_into(h, 2, h->band_T);
   if (s != PSP_OK) return s;
@@ -371,6 +377,7 @@ psp_status psp_default_opts(psp_opts *o) {
   o->accept_rule = 1;
   o->fuse_matvec = 1;
   o->adjoint = 0;
+  o->cyclic = 0;
   return PSP_OK;
 }
 
@@ -382,6 +389,7 @@ psp_status psp_create_banded(int64_t n, const double *A_band, int w, int b, int 
   psp_opts o;
   psp_default_opts(&o);
   if (opts) o = *opts;
+  if (o.cyclic) return fail(PSP_ERR_ARG, "a cyclic band needs a periodic grid (psp_create, ndim = 1)");
   const int adjoint = o.adjoint;
   o.adjoint = 0;
   o.fuse_matvec = 0;
@@ -477,6 +485,10 @@ psp_status psp_create(const psp_grid *grid, int order, const psp_term *terms, in
   const int64_t n = nn[0] * nn[1] * nn[2];
   if (n > (int64_t)1 << 31) { delete h; return fail(PSP_ERR_ARG, "at most 2^31 unknowns"); }
   if (n < 2 * b + 1) { delete h; return fail(PSP_ERR_ARG, "need n >= 2b+1"); }
+  if (o.cyclic && (grid->ndim != 1 || n < 4 * b + 2)) {
+    delete h;
+    return fail(PSP_ERR_ARG, "a cyclic band needs a 1D grid with n >= 4b+2");
+  }
   int R = 1;
   for (int t = 0; t < nterms; ++t) {
     const psp_term &tm = terms[t];
@@ -538,6 +550,7 @@ psp_status psp_create(const psp_grid *grid, int order, const psp_term *terms, in
   ok = ok && dalloc((void **)&h->band_T, (size_t)n * (2 * b + 1) * 8);
   ok = ok && dalloc((void **)&h->dev_int, 64);
   if (ok) {
+    h->bs.cyclic = o.cyclic != 0;
     h->bs.plan(n, b);
     for (int s = 0; s < BandSolver::kSlots && ok; ++s) {
       ok = dalloc(&h->slot_mem[s], h->bs.slot_bytes());

@@ -118,9 +118,9 @@ template <typename T>
 void launch_update_z(int64_t n, const T *V, int64_t ldv, T *Z, double *X, int add_to_x, const DevState *st,
                      cudaStream_t s);
 
-// band_fit.cu
+// band_fit.cu (cyclic: every row regresses on its neighbours modulo n)
 template <typename TH>
 void launch_fit(int b, int intercept, int64_t n, int M, const TH *Px, const TH *Py, int64_t ld,
-                double *moments, double *band, int *singular_count, cudaStream_t s);
+                double *moments, double *band, int *singular_count, cudaStream_t s, int cyclic = 0);
 
 }  // namespace psp

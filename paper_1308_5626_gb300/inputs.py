@@ -251,6 +251,18 @@ def random_band(n: int, b: int, seed: int, dominance: float = 1.5) -> np.ndarray
     return band
 
 
+def random_cyclic_band(n: int, b: int, seed: int, dominance: float = 1.5) -> np.ndarray:
+    """Random cyclic band (band[i, p] = N(i, (i + p - b) mod n)): as ``random_band`` but
+    with every cell filled, the wrapped corner cells of the first and last b rows included."""
+    rng = np.random.default_rng(seed)
+    band = rng.uniform(-1.0, 1.0, (n, 2 * b + 1))
+    band[:, b] = 0.0
+    diag = dominance * np.abs(band).sum(axis=1) + 1.0
+    sign = np.where(rng.uniform(0.0, 1.0, n) < 0.5, -1.0, 1.0)
+    band[:, b] = sign * diag
+    return band
+
+
 def random_pd_part_band(n: int, b: int, seed: int, skew: float = 3.0) -> np.ndarray:
     """Banded matrix with positive-definite symmetric part but no diagonal dominance.
 
