@@ -58,6 +58,7 @@ def _args():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-e1", action="store_true")
     ap.add_argument("--no-cyclic", action="store_true")
+    ap.add_argument("--no-integrators", action="store_true")
     ap.add_argument("--batch", type=int, default=512, help="instances of the batched line (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--batch-threads", type=int, default=16)
@@ -460,6 +461,44 @@ def _cyclic_line(device, steps: int = 10):
     return {"workload": "c1_1d_adv_diff (4th order, CFL 10, b = 2, m = 30, tol 1e-10)", "rows": rows}
 
 
+def _integrators_line(w, device, steps: int = 5):
+    """The second-order integrators on the step (psp_step_bdf2, psp_step_sdirk2) on the
+    headline workload, mixed form, against implicit Euler: ms per time step and iterations
+    per time step (CUDA events around `steps` steps after 2 warm-up steps; BDF2 is started
+    by one Euler step).  An SDIRK step is two solves at gamma dt, a BDF2 step one at 2/3 dt."""
+    import torch
+    from paper_1308_5626_gb300 import psp
+    rows = []
+    for method in ("euler", "bdf2", "sdirk2"):
+        stream = torch.cuda.Stream(device=device)
+        with torch.cuda.stream(stream):
+            s = psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=psp.PSP_MIXED, stream=stream)
+            hist = [torch.tensor(w.u0, dtype=torch.float64, device=device)]
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            its = 0
+            for k in range(2 + steps):
+                if k == 2:
+                    torch.cuda.synchronize(device)
+                    e0.record(stream)
+                out = torch.empty_like(hist[-1])
+                if method == "euler" or (method == "bdf2" and k == 0):
+                    _, info = s.step(hist[-1], w.dt, w.tol, out=out)
+                elif method == "bdf2":
+                    _, info = s.step_bdf2(hist[-2], hist[-1], w.dt, w.tol, out=out)
+                else:
+                    _, info = s.step_sdirk2(hist[-1], w.dt, w.tol, out=out)
+                if k >= 2:
+                    its += info.iters
+                hist = (hist + [out])[-2:]
+            e1.record(stream)
+            torch.cuda.synchronize(device)
+            s.close()
+        ms = e0.elapsed_time(e1) / steps
+        rows.append({"method": method, "ms_per_step": ms, "steps_per_s": 1e3 / ms, "iters_per_step": its / steps})
+    return {"workload": w.name, "form": "mixed", "rows": rows}
+
+
 def _batch_line(device, count: int, steps: int, nthreads: int):
     """The batched workload: `count` independent instances (inputs.c4_instance: 1D/2D, n from
     2^10 to 2^18, orders 2-8, b 1-4, CFL 1-20, mixed form, tol 1e-8), each on its own stream,
@@ -686,6 +725,9 @@ def main():
     cyclic = None
     if not a.no_cyclic and rank == 0:
         cyclic = _cyclic_line(device)
+    integ = None
+    if not a.no_integrators and rank == 0:
+        integ = _integrators_line(w, device)
 
     if rank != 0:
         if world > 1:
@@ -756,6 +798,7 @@ def main():
         "mock_test": e1,
         "batched": batch,
         "cyclic_band": cyclic,
+        "integrators": integ,
         "cpu_baseline": cpu, "clocks": clk,
     }
     if fp64:

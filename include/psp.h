@@ -197,6 +197,23 @@ psp_status psp_step_batch(psp_handle *handles, int count, const double *const *u
                           const double *dt, double tol, int nthreads, psp_step_info *infos, double *seconds,
                           psp_status *statuses);
 
+/* Second-order implicit integrators on the step (not in the paper): each solves with the
+ * same matrix-free PSP-GMRES and progressive preconditioner as psp_step, on another
+ * right-hand side and a scaled time step.  Vectors are device FP64 arrays of n values (u_np1
+ * must not overlap the inputs); info sums iterations, cycles and launches over the solves.
+ * PDE handles only (psp_create; PSP_ERR_ARG for psp_create_banded handles).
+ *
+ * psp_step_bdf2: BDF2, (I - 2/3 dt L) u^{n+1} = (4 u^n - u^{n-1}) / 3 -- one step of the
+ *   handle at dt' = 2 dt / 3 (start a BDF2 run with one psp_step for u^1).
+ * psp_step_sdirk2: Alexander's two-stage L-stable SDIRK (gamma = 1 - 1/sqrt 2):
+ *   (I - gamma dt L) U1 = u^n; (I - gamma dt L) u^{n+1} = u^n + (1 - gamma) dt L U1 --
+ *   two steps of the handle at gamma dt, so both stages share the history and N.
+ *   A stage that reaches max_restarts gives PSP_ERR_NOCONV after the second stage ran. */
+psp_status psp_step_bdf2(psp_handle h, const double *u_nm1, const double *u_n, double *u_np1, double dt,
+                         double tol, psp_step_info *info);
+psp_status psp_step_sdirk2(psp_handle h, const double *u_n, double *u_np1, double dt, double tol,
+                           psp_step_info *info);
+
 /* psp_step on host arrays: copies u_n_host to the device, steps, copies the result to
  * u_np1_host (both n doubles, pageable or pinned). */
 psp_status psp_step_host(psp_handle h, const double *u_n_host, double *u_np1_host, double dt,
@@ -212,7 +229,8 @@ psp_status psp_matvec_f32(psp_handle h, const float *x, float *y, double dt);
  * arrays (column c starts at c*ld, ld >= n), N_band is the device output (band storage,
  * half-width b of the handle).  Rows 0..b-1 and n-b..n-1 get the slope of a simple
  * linear fit on the diagonal; interior rows the least-squares fit on
- * [1; Px(i-b..i+b, :)] (or without the row of ones when opts.intercept = 0).  Rows whose
+ * [1; Px(i-b..i+b, :)] (or without the row of ones when opts.intercept = 0).  With
+ * opts.cyclic every row is an interior row, its neighbours taken modulo n.  Rows whose
  * normal equations are degenerate (relative Cholesky pivot <= 1e-12) get the identity
  * row; their count goes to *singular_rows (host, may be NULL).  Requires M >= 1.
  * Does not change the handle's preconditioner.

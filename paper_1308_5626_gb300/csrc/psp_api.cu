@@ -149,6 +149,8 @@ struct psp_ctx {
   // when it runs more threads than the host has cores
   bool blocking_wait = false;
   cudaEvent_t wait_ev = nullptr;
+  // integrators (psp_step_bdf2, psp_step_sdirk2): right-hand side and first-stage vectors
+  double *int_rhs = nullptr, *int_u1 = nullptr;
 };
 
 namespace {
@@ -437,7 +439,7 @@ psp_status psp_destroy(psp_handle h) {
   void *dev[] = {h->V, h->Px, h->Py, h->Z, h->X, h->B, h->partial, h->st, h->api_st, h->moments,
                  h->band_adopted, h->band_cand, h->dev_int, h->slot_mem[0], h->slot_mem[1], h->slot_mem[2],
                  h->band_T, h->Ab, h->Ab32, h->apply_mem,
-                 h->dev_un, h->dev_unp1};
+                 h->dev_un, h->dev_unp1, h->int_rhs, h->int_u1};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (h->sum_host) cudaFreeHost(h->sum_host);
@@ -801,6 +803,66 @@ psp_status psp_step_batch(psp_handle *hs, int count, const double *const *u_n, d
   if (first_err.load() != (int)PSP_OK)
     return fail((psp_status)first_err.load(), "at least one instance of the batch failed (see statuses)");
   return noconv.load() ? fail(PSP_ERR_NOCONV, "an instance reached max_restarts") : PSP_OK;
+}
+
+namespace {
+psp_status integrator_buffers(psp_ctx *h) {
+  if (h->geo.band_w > 0) return fail(PSP_ERR_ARG, "the integrators need a PDE handle (psp_create): dt scales L");
+  const size_t bytes = (size_t)h->geo.n * 8;
+  if (!h->int_rhs && cudaMalloc((void **)&h->int_rhs, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PSP_ERR_OOM, "integrator buffers");
+  }
+  if (!h->int_u1 && cudaMalloc((void **)&h->int_u1, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PSP_ERR_OOM, "integrator buffers");
+  }
+  return PSP_OK;
+}
+}  // namespace
+
+psp_status psp_step_bdf2(psp_handle h, const double *u_nm1, const double *u_n, double *u_np1, double dt, double tol,
+                         psp_step_info *info) {
+  if (!h || !u_nm1 || !u_n || !u_np1) return fail(PSP_ERR_ARG, "NULL argument");
+  if (!(dt > 0.0)) return fail(PSP_ERR_ARG, "dt must be > 0");
+  psp_status bs = integrator_buffers(h);
+  if (bs != PSP_OK) return bs;
+  // (I - 2/3 dt L) u^{n+1} = (4 u^n - u^{n-1}) / 3
+  launch_axpby(h->geo.n, 4.0 / 3.0, u_n, -1.0 / 3.0, u_nm1, h->int_rhs, h->stream);
+  PSP_CUDA(cudaGetLastError());
+  psp_status st = psp_step(h, h->int_rhs, u_np1, 2.0 * dt / 3.0, tol, info);
+  if (info) info->launches += 1;
+  return st;
+}
+
+psp_status psp_step_sdirk2(psp_handle h, const double *u_n, double *u_np1, double dt, double tol,
+                           psp_step_info *info) {
+  if (!h || !u_n || !u_np1) return fail(PSP_ERR_ARG, "NULL argument");
+  if (!(dt > 0.0)) return fail(PSP_ERR_ARG, "dt must be > 0");
+  psp_status bs = integrator_buffers(h);
+  if (bs != PSP_OK) return bs;
+  const double g = 1.0 - 1.0 / std::sqrt(2.0);
+  psp_step_info i1{}, i2{};
+  // stage 1: (I - gamma dt L) U1 = u^n
+  psp_status s1 = psp_step(h, u_n, h->int_u1, g * dt, tol, &i1);
+  if (s1 != PSP_OK && s1 != PSP_ERR_NOCONV) return s1;
+  // stage 2: (I - gamma dt L) u^{n+1} = u^n + (1 - gamma) dt L U1
+  psp_status sl = psp_apply_L(h, -1, h->int_u1, h->int_rhs);
+  if (sl != PSP_OK) return sl;
+  launch_axpby(h->geo.n, 1.0, u_n, (1.0 - g) * dt, h->int_rhs, h->int_rhs, h->stream);
+  PSP_CUDA(cudaGetLastError());
+  psp_status s2 = psp_step(h, h->int_rhs, u_np1, g * dt, tol, &i2);
+  if (info) {
+    *info = i2;
+    info->iters = i1.iters + i2.iters;
+    info->cycles = i1.cycles + i2.cycles;
+    info->flags = i1.flags | i2.flags;
+    info->rel_res = std::max(i1.rel_res, i2.rel_res);
+    info->launches = i1.launches + i2.launches + 2;
+    info->status = (s2 != PSP_OK) ? s2 : s1;
+  }
+  if (s2 != PSP_OK) return s2;
+  return s1 == PSP_OK ? PSP_OK : fail(s1, "SDIRK2 stage 1 reached max_restarts");
 }
 
 psp_status psp_step_host(psp_handle h, const double *u_n_host, double *u_np1_host, double dt, double tol,

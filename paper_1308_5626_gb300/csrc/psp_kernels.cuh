@@ -73,6 +73,8 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 int reduce_grid(int64_t n);
+// z = a x + b y (FP64; z may alias x or y)
+void launch_axpby(int64_t n, double a, const double *x, double b, const double *y, double *z, cudaStream_t s);
 // The 3D geometry is taken by the z-marching tiled stencil (x a whole number of tiles of
 // 32 16-byte vectors, y of 8 rows).
 bool stencil_3d_tiled(const Geometry &g, int elem_bytes);

@@ -299,6 +299,19 @@ __global__ void __launch_bounds__(kThreads) k_restart(const double *__restrict__
 // launchers
 // ---------------------------------------------------------------------------------------
 
+// z = a x + b y (FP64, elementwise; z may alias x or y): the right-hand sides of the
+// integrators built on the step.
+__global__ void __launch_bounds__(kThreads) k_axpby(int64_t n, double a, const double *x, double b, const double *y,
+                                                   double *z) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    z[i] = a * x[i] + b * y[i];
+}
+
+void launch_axpby(int64_t n, double a, const double *x, double b, const double *y, double *z, cudaStream_t s) {
+  const int64_t g = std::min<int64_t>((n + kThreads - 1) / kThreads, 152 * 8);
+  k_axpby<<<(unsigned)std::max<int64_t>(g, 1), kThreads, 0, s>>>(n, a, x, b, y, z);
+}
+
 int reduce_grid(int64_t n) {
   int64_t g = (n + kThreads * 4 - 1) / (kThreads * 4);
   if (g < 1) g = 1;

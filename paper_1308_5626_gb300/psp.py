@@ -67,6 +67,8 @@ _SIGS = {
                           ctypes.POINTER(_VP)],
     "psp_step": [_VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(psp_step_info)],
     "psp_step_host": [_VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(psp_step_info)],
+    "psp_step_bdf2": [_VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(psp_step_info)],
+    "psp_step_sdirk2": [_VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(psp_step_info)],
     "psp_matvec": [_VP, _VP, _VP, ctypes.c_double],
     "psp_matvec_f32": [_VP, _VP, _VP, ctypes.c_double],
     "psp_apply_L": [_VP, ctypes.c_int, _VP, _VP],
@@ -161,6 +163,24 @@ def psp_step(h, u_n, u_np1, dt: float, tol: float, allow_noconv: bool = False) -
     info = psp_step_info()
     allow = (PSP_OK, PSP_ERR_NOCONV) if allow_noconv else (PSP_OK,)
     _check(lib().psp_step(h, _ptr(u_n), _ptr(u_np1), float(dt), float(tol), ctypes.byref(info)), "psp_step", allow)
+    return info
+
+
+def psp_step_bdf2(h, u_nm1, u_n, u_np1, dt: float, tol: float, allow_noconv: bool = False) -> psp_step_info:
+    """BDF2 step (I - 2/3 dt L) u^{n+1} = (4 u^n - u^{n-1}) / 3; device float64 tensors."""
+    info = psp_step_info()
+    allow = (PSP_OK, PSP_ERR_NOCONV) if allow_noconv else (PSP_OK,)
+    _check(lib().psp_step_bdf2(h, _ptr(u_nm1), _ptr(u_n), _ptr(u_np1), float(dt), float(tol), ctypes.byref(info)),
+           "psp_step_bdf2", allow)
+    return info
+
+
+def psp_step_sdirk2(h, u_n, u_np1, dt: float, tol: float, allow_noconv: bool = False) -> psp_step_info:
+    """Two-stage SDIRK step (gamma = 1 - 1/sqrt 2); device float64 tensors."""
+    info = psp_step_info()
+    allow = (PSP_OK, PSP_ERR_NOCONV) if allow_noconv else (PSP_OK,)
+    _check(lib().psp_step_sdirk2(h, _ptr(u_n), _ptr(u_np1), float(dt), float(tol), ctypes.byref(info)),
+           "psp_step_sdirk2", allow)
     return info
 
 
@@ -324,6 +344,18 @@ class Solver:
         import torch
         out = torch.empty_like(u_n) if out is None else out
         info = psp_step(self.handle, u_n, out, dt, tol, allow_noconv)
+        return out, info
+
+    def step_bdf2(self, u_nm1, u_n, dt, tol, out=None, allow_noconv=False):
+        import torch
+        out = torch.empty_like(u_n) if out is None else out
+        info = psp_step_bdf2(self.handle, u_nm1, u_n, out, dt, tol, allow_noconv)
+        return out, info
+
+    def step_sdirk2(self, u_n, dt, tol, out=None, allow_noconv=False):
+        import torch
+        out = torch.empty_like(u_n) if out is None else out
+        info = psp_step_sdirk2(self.handle, u_n, out, dt, tol, allow_noconv)
         return out, info
 
     def close(self):
