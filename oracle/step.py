@@ -24,6 +24,9 @@ open (listed with the others in the design notes):
 * ``cyclic=True`` (not in the paper): the fit and the solve use the cyclic band (every
   row regresses on its wrapped neighbours; see mrep and banded), the structure of A on a
   periodic 1D grid.
+* ``solver="bicgstab"`` (not in the paper): the cycles are restarted BiCGSTAB
+  (oracle/bicgstab.py) instead of Algorithm 1's GMRES; history, fit and acceptance are
+  the same.
 """
 from __future__ import annotations
 
@@ -32,7 +35,7 @@ from typing import List, Optional
 
 import numpy as np
 
-from . import banded, gmres, mrep
+from . import banded, bicgstab, gmres, mrep
 from .operator import Operator
 
 
@@ -58,7 +61,7 @@ def _rate(R_end: float, beta: float, k: int) -> float:
 class Stepper:
     def __init__(self, op: Operator, b: int, m: int, intercept: bool = True,
                  max_restarts: int = 200, max_hist: Optional[int] = None, gs: str = "mgs",
-                 accept_rule: bool = True, cyclic: bool = False):
+                 accept_rule: bool = True, cyclic: bool = False, solver: str = "gmres"):
         self.op = op
         self.b = int(b)
         self.m = int(m)
@@ -68,6 +71,9 @@ class Stepper:
         self.gs = gs
         self.accept_rule = bool(accept_rule)
         self.cyclic = bool(cyclic)
+        if solver not in ("gmres", "bicgstab"):
+            raise ValueError("solver must be 'gmres' or 'bicgstab'")
+        self.solver = solver
         self.N: Optional[np.ndarray] = None          # adopted preconditioner (None = I)
         self.candidate: Optional[np.ndarray] = None  # freshly fitted, not yet tried
         self.rate_ref: Optional[float] = None
@@ -84,6 +90,11 @@ class Stepper:
         d = self.b
         return lambda v: banded.solve(band, d, v, cyclic=self.cyclic)
 
+    def _cycles(self, A, B, N_solve, eps, X0, n_r):
+        if self.solver == "bicgstab":
+            return bicgstab.psp_bicgstab(A, B, N_solve, eps, self.m, X0, n_r)
+        return gmres.pspgmres(A, B, N_solve, eps, self.m, X0, n_r, self.gs)
+
     def step(self, u_n: np.ndarray, dt: float, tol: float):
         u_n = np.asarray(u_n, dtype=np.float64)
         nrm = float(np.linalg.norm(u_n))
@@ -99,7 +110,7 @@ class Stepper:
         restarts_left = self.max_restarts
         if self.candidate is not None and self.wait == 0:
             tried = True
-            r1 = gmres.pspgmres(A, u_n, self._solver(self.candidate), eps, self.m, X0, 1, self.gs)
+            r1 = self._cycles(A, u_n, self._solver(self.candidate), eps, X0, 1)
             runs.append(r1)
             restarts_left -= 1
             k1 = len(r1.cycle_R[0])
@@ -118,8 +129,7 @@ class Stepper:
 
         main = None
         if not (runs and runs[0].converged):
-            main = gmres.pspgmres(A, u_n, self._solver(self.N), eps, self.m, X0,
-                                  max(restarts_left, 1), self.gs)
+            main = self._cycles(A, u_n, self._solver(self.N), eps, X0, max(restarts_left, 1))
             runs.append(main)
         self.last = runs
         X = runs[-1].X
