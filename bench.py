@@ -59,6 +59,7 @@ def _args():
     ap.add_argument("--no-e1", action="store_true")
     ap.add_argument("--no-cyclic", action="store_true")
     ap.add_argument("--no-integrators", action="store_true")
+    ap.add_argument("--no-bicgstab", action="store_true")
     ap.add_argument("--batch", type=int, default=512, help="instances of the batched line (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--batch-threads", type=int, default=16)
@@ -499,6 +500,41 @@ def _integrators_line(w, device, steps: int = 5):
     return {"workload": w.name, "form": "mixed", "rows": rows}
 
 
+def _bicgstab_line(w, device, steps: int = 3):
+    """The BiCGSTAB solver against GMRES (Algorithm 1) on the headline workload, both FP64
+    (BiCGSTAB runs in FP64 only): ms per step, iterations and matvecs per step (CUDA events
+    around `steps` steps after 2 warm-up steps)."""
+    import torch
+    from paper_1308_5626_gb300 import psp
+    rows = []
+    for name, solver in (("gmres", psp.PSP_SOLVER_GMRES), ("bicgstab", psp.PSP_SOLVER_BICGSTAB)):
+        stream = torch.cuda.Stream(device=device)
+        with torch.cuda.stream(stream):
+            s = psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=psp.PSP_FP64, stream=stream, solver=solver)
+            u = torch.tensor(w.u0, dtype=torch.float64, device=device)
+            out = torch.empty_like(u)
+            for _ in range(2):
+                s.step(u, w.dt, w.tol, out=out)
+                u, out = out, u
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            its = cyc = 0
+            e0.record(stream)
+            for _ in range(steps):
+                _, info = s.step(u, w.dt, w.tol, out=out)
+                its += info.iters
+                cyc += info.cycles
+                u, out = out, u
+            e1.record(stream)
+            torch.cuda.synchronize(device)
+            s.close()
+        ms = e0.elapsed_time(e1) / steps
+        mv = (its + cyc) if name == "gmres" else (2 * its + cyc)
+        rows.append({"solver": name, "ms_per_step": ms, "steps_per_s": 1e3 / ms, "iters_per_step": its / steps,
+                     "matvecs_per_step": mv / steps})
+    return {"workload": w.name, "form": "fp64", "rows": rows}
+
+
 def _batch_line(device, count: int, steps: int, nthreads: int):
     """The batched workload: `count` independent instances (inputs.c4_instance: 1D/2D, n from
     2^10 to 2^18, orders 2-8, b 1-4, CFL 1-20, mixed form, tol 1e-8), each on its own stream,
@@ -728,6 +764,9 @@ def main():
     integ = None
     if not a.no_integrators and rank == 0:
         integ = _integrators_line(w, device)
+    bicg = None
+    if not a.no_bicgstab and rank == 0:
+        bicg = _bicgstab_line(w, device)
 
     if rank != 0:
         if world > 1:
@@ -799,6 +838,7 @@ def main():
         "batched": batch,
         "cyclic_band": cyclic,
         "integrators": integ,
+        "bicgstab": bicg,
         "cpu_baseline": cpu, "clocks": clk,
     }
     if fp64:

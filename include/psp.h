@@ -74,6 +74,9 @@ typedef struct {
   double alpha;
 } psp_term;
 
+#define PSP_SOLVER_GMRES 0
+#define PSP_SOLVER_BICGSTAB 1
+
 typedef struct {
   int precision;     /* PSP_FP64 (default): every vector in FP64.  PSP_MIXED: Krylov
                         vectors, history, stencil and band solve in FP32 with FP32
@@ -103,6 +106,13 @@ typedef struct {
                         in-range band; a singular capacitance matrix drops the N like a zero
                         pivot).  Not in the paper; for a periodic 1D stencil N = A can then be
                         fitted exactly. */
+  int solver;        /* PSP_SOLVER_GMRES (default): Algorithm 1.  PSP_SOLVER_BICGSTAB:
+                        restarted right-preconditioned BiCGSTAB (van der Vorst 1992), m
+                        iterations per restart cycle, each storing its two matvec pairs
+                        (p^, A p^), (s^, A s^) -- scaled by 1/||r|| -- in the same history, so
+                        the fit, the acceptance rule and the preconditioner are unchanged.
+                        PSP_FP64 and m >= 3 only (else PSP_ERR_ARG); the profiling mode
+                        times GMRES cycles only.  Not in the paper. */
 } psp_opts;
 
 typedef struct {

@@ -222,11 +222,51 @@ void enqueue_cycle(psp_ctx *h, int slot, cudaStream_t s) {
   cudaMemcpyAsync(h->sum_host, &h->st->sum, sizeof(CycleSummary), cudaMemcpyDeviceToHost, s);
 }
 
+// One restart cycle of BiCGSTAB (FP64): the restart (true residual, restart pair), then m
+// iterations, each storing its two matvec pairs (scaled by 1/||r||) at ring columns
+// hist_base+1+2j and hist_base+2+2j; X is updated every iteration.
+void enqueue_bicgstab_cycle(psp_ctx *h, int slot, cudaStream_t s) {
+  double *V = reinterpret_cast<double *>(h->V);
+  double *Px = reinterpret_cast<double *>(h->Px);
+  double *Py = reinterpret_cast<double *>(h->Py);
+  const Geometry &g = h->geo;
+  const int64_t n = g.n, ld = h->ld;
+  DevState *st = h->st;
+  const int *active = &st->active;
+  launch_restart<double, double>(g, h->X, h->B, Px, Py, ld, V, st, h->partial, 0, s);
+  launch_bi_start(n, V, ld, st, s);
+  const OutRef<double> none{nullptr, 0, nullptr, 1, 0};
+  for (int j = 0; j < h->m; ++j) {
+    const int c1 = 1 + 2 * j, c2 = 2 + 2 * j;   // ring offsets of the iteration's two pairs
+    launch_bi_p(j == 0, n, V, ld, ring_in<double>(Py, ld, &st->hist_base, h->mmax, j > 0 ? c1 - 2 : 0),
+                slot < 0 ? ring_out<double>(Px, ld, &st->hist_base, h->mmax, c1) : none, st, s);
+    if (slot >= 0)
+      h->bs.apply<double>(slot, V + 2 * ld, &st->bi[4], active, ring_out<double>(Px, ld, &st->hist_base, h->mmax, c1),
+                          nullptr, 0, s);
+    launch_stencil<double, double, double>(g, ring_in<double>(Px, ld, &st->hist_base, h->mmax, c1),
+                                           ring_out<double>(Py, ld, &st->hist_base, h->mmax, c1), st, active, s);
+    launch_bi_alpha(n, V, ld, ring_in<double>(Py, ld, &st->hist_base, h->mmax, c1), st, h->partial, s);
+    launch_bi_s(n, V, ld, ring_in<double>(Py, ld, &st->hist_base, h->mmax, c1),
+                slot < 0 ? ring_out<double>(Px, ld, &st->hist_base, h->mmax, c2) : none, st, s);
+    if (slot >= 0)
+      h->bs.apply<double>(slot, V + 3 * ld, &st->bi[4], active, ring_out<double>(Px, ld, &st->hist_base, h->mmax, c2),
+                          nullptr, 0, s);
+    launch_stencil<double, double, double>(g, ring_in<double>(Px, ld, &st->hist_base, h->mmax, c2),
+                                           ring_out<double>(Py, ld, &st->hist_base, h->mmax, c2), st, active, s);
+    launch_bi_omega(n, V, ld, ring_in<double>(Py, ld, &st->hist_base, h->mmax, c2), st, h->partial, s);
+    launch_bi_xr(j, h->m, n, h->X, V, ld, ring_in<double>(Px, ld, &st->hist_base, h->mmax, c1),
+                 ring_in<double>(Px, ld, &st->hist_base, h->mmax, c2),
+                 ring_in<double>(Py, ld, &st->hist_base, h->mmax, c2), st, h->partial, s);
+  }
+  cudaMemcpyAsync(h->sum_host, &h->st->sum, sizeof(CycleSummary), cudaMemcpyDeviceToHost, s);
+}
+
 psp_status capture(psp_ctx *h, int which) {
   cudaGraph_t graph;
   PSP_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
   const int slot = which - 1;
-  if (h->mixed) enqueue_cycle<float>(h, slot, h->cap);
+  if (h->opts.solver == PSP_SOLVER_BICGSTAB) enqueue_bicgstab_cycle(h, slot, h->cap);
+  else if (h->mixed) enqueue_cycle<float>(h, slot, h->cap);
   else enqueue_cycle<double>(h, slot, h->cap);
   cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
   if (e != cudaSuccess) return fail(PSP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
@@ -380,6 +420,7 @@ psp_status psp_default_opts(psp_opts *o) {
   o->fuse_matvec = 1;
   o->adjoint = 0;
   o->cyclic = 0;
+  o->solver = PSP_SOLVER_GMRES;
   return PSP_OK;
 }
 
@@ -467,6 +508,9 @@ psp_status psp_create(const psp_grid *grid, int order, const psp_term *terms, in
   if (o.precision != PSP_FP64 && o.precision != PSP_MIXED) return fail(PSP_ERR_ARG, "bad precision");
   if (o.max_restarts < 1) return fail(PSP_ERR_ARG, "max_restarts must be >= 1");
   if (!(o.inner_tol > 0.0 && o.inner_tol < 1.0)) return fail(PSP_ERR_ARG, "inner_tol must be in (0, 1)");
+  if (o.solver != PSP_SOLVER_GMRES && o.solver != PSP_SOLVER_BICGSTAB) return fail(PSP_ERR_ARG, "bad solver");
+  if (o.solver == PSP_SOLVER_BICGSTAB && (o.precision != PSP_FP64 || m < 3))   // V columns r, rh, p, s
+    return fail(PSP_ERR_ARG, "the BiCGSTAB solver runs in FP64 with m >= 3");
 
   psp_ctx *h = new psp_ctx();
   h->order = order;
@@ -636,7 +680,7 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
     cycles += 1;
     iters += sm.k_end;
     launches += h->graph_kernels[which];
-    if (h->profiling) accumulate_profile(h, which, sm.k_end);
+    if (h->profiling && h->opts.solver == PSP_SOLVER_GMRES) accumulate_profile(h, which, sm.k_end);
     bnorm = sm.bnorm;
     if (sm.error) return fail(PSP_ERR_DEVICE, "device error flag " + std::to_string(sm.error) +
                                                   " (a bounded wait expired or a launch was misconfigured)");

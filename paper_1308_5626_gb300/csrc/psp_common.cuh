@@ -78,6 +78,12 @@ struct DevState {
   unsigned int counter[8];
   int error;         // internal error flag (0 = none)
   int first;         // 1 before the first restart of a step (sets ||B|| and eps_abs)
+  // BiCGSTAB scalars (rho, alpha, omega, beta, sigma = 1/||r||, ||r||^2), 1/sigma of the
+  // previous iteration, and the rh . v = 0 breakdown flag
+  double bi[6];
+  double bi_isig_prev;
+  int bi_flag;
+  int bi_pad;
 };
 
 // Column `col` of a ring of `mmax` columns of length ld.

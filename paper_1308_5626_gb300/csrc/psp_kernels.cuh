@@ -120,6 +120,18 @@ template <typename T>
 void launch_update_z(int64_t n, const T *V, int64_t ldv, T *Z, double *X, int add_to_x, const DevState *st,
                      cudaStream_t s);
 
+// bicgstab.cu: the kernels of one BiCGSTAB iteration (FP64; V columns 0..3 = r, rh, p, s)
+void launch_bi_start(int64_t n, double *V, int64_t ldv, DevState *st, cudaStream_t s);
+void launch_bi_p(int first, int64_t n, double *V, int64_t ldv, InRef<double> v, OutRef<double> px, DevState *st,
+                 cudaStream_t s);
+void launch_bi_alpha(int64_t n, const double *V, int64_t ldv, InRef<double> v, DevState *st, double *partial,
+                     cudaStream_t s);
+void launch_bi_s(int64_t n, double *V, int64_t ldv, InRef<double> v, OutRef<double> sx, DevState *st, cudaStream_t s);
+void launch_bi_omega(int64_t n, const double *V, int64_t ldv, InRef<double> t, DevState *st, double *partial,
+                     cudaStream_t s);
+void launch_bi_xr(int j, int m, int64_t n, double *X, double *V, int64_t ldv, InRef<double> p, InRef<double> sx,
+                  InRef<double> t, DevState *st, double *partial, cudaStream_t s);
+
 // band_fit.cu (cyclic: every row regresses on its neighbours modulo n)
 template <typename TH>
 void launch_fit(int b, int intercept, int64_t n, int M, const TH *Px, const TH *Py, int64_t ld,

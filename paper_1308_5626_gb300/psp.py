@@ -18,6 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpsp.so")
 
 PSP_OK, PSP_ERR_ARG, PSP_ERR_CUDA, PSP_ERR_OOM, PSP_ERR_NOCONV, PSP_ERR_NUMERIC, PSP_ERR_DEVICE = range(7)
+PSP_SOLVER_GMRES, PSP_SOLVER_BICGSTAB = 0, 1
 PSP_FP64, PSP_MIXED = 0, 1
 PSP_FLAG_SINGULAR_FIT = 0x1
 PSP_FLAG_CANDIDATE_TRIED = 0x2
@@ -40,7 +41,8 @@ class psp_term(ctypes.Structure):
 class psp_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("intercept", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("max_hist_cols", ctypes.c_int), ("inner_tol", ctypes.c_double), ("accept_rule", ctypes.c_int),
-                ("fuse_matvec", ctypes.c_int), ("adjoint", ctypes.c_int), ("cyclic", ctypes.c_int)]
+                ("fuse_matvec", ctypes.c_int), ("adjoint", ctypes.c_int), ("cyclic", ctypes.c_int),
+                ("solver", ctypes.c_int)]
 
 
 class psp_step_info(ctypes.Structure):
@@ -292,11 +294,12 @@ def psp_get_profile(h, reset: bool = False) -> dict:
 # convenience: a handle bound to torch tensors
 # --------------------------------------------------------------------------------------
 
-def _opts(precision, intercept, max_restarts, max_hist_cols, inner_tol, accept_rule, fuse_matvec, adjoint, cyclic=0):
+def _opts(precision, intercept, max_restarts, max_hist_cols, inner_tol, accept_rule, fuse_matvec, adjoint, cyclic=0,
+          solver=0):
     o = psp_default_opts()
     o.precision, o.intercept, o.max_restarts = int(precision), int(intercept), int(max_restarts)
     o.max_hist_cols, o.inner_tol, o.accept_rule = int(max_hist_cols), float(inner_tol), int(accept_rule)
-    o.fuse_matvec, o.adjoint, o.cyclic = int(fuse_matvec), int(adjoint), int(cyclic)
+    o.fuse_matvec, o.adjoint, o.cyclic, o.solver = int(fuse_matvec), int(adjoint), int(cyclic), int(solver)
     return o
 
 
@@ -312,10 +315,11 @@ class Solver:
     """Owns one psp handle for a workload; vectors are torch CUDA float64 tensors."""
 
     def __init__(self, shape, order, terms, b, m, precision=PSP_FP64, intercept=1, max_restarts=200,
-                 max_hist_cols=0, inner_tol=1e-5, accept_rule=1, fuse_matvec=1, adjoint=0, stream=None, cyclic=0):
+                 max_hist_cols=0, inner_tol=1e-5, accept_rule=1, fuse_matvec=1, adjoint=0, stream=None, cyclic=0,
+                 solver=0):
         import torch
         o = _opts(precision, intercept, max_restarts, max_hist_cols, inner_tol, accept_rule, fuse_matvec, adjoint,
-                  cyclic)
+                  cyclic, solver)
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s
         self.shape = tuple(int(v) for v in shape)
