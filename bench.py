@@ -152,11 +152,17 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+# The translation unit of the kernels whose DRAM traffic profiles/traffic.json records (the
+# two Gram-Schmidt passes) and the headers it includes: a change to any of them makes the
+# recorded traffic stale.
+TRAFFIC_SOURCES = ("paper_1308_5626_gb300/csrc/arnoldi.cu", "paper_1308_5626_gb300/csrc/psp_kernels.cuh",
+                   "paper_1308_5626_gb300/csrc/psp_common.cuh", "include/psp.h")
+
+
 def _kernel_source_hash() -> str:
     h = hashlib.sha256()
-    cdir = os.path.join(ROOT, "paper_1308_5626_gb300", "csrc")
-    for f in sorted(os.listdir(cdir)):
-        with open(os.path.join(cdir, f), "rb") as fh:
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
