@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <string>
@@ -801,6 +802,12 @@ psp_status psp_step_batch(psp_handle *hs, int count, const double *const *u_n, d
   if (!(tol > 0.0)) return fail(PSP_ERR_ARG, "tol must be > 0");
   for (int i = 0; i < count; ++i)
     if (!hs[i]) return fail(PSP_ERR_ARG, "NULL handle in the batch");
+  {  // two threads must never step one handle (its stream and workspace are not shared)
+    std::vector<psp_handle> sorted(hs, hs + count);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+      return fail(PSP_ERR_ARG, "a handle appears twice in the batch");
+  }
   int dev = 0;
   cudaGetDevice(&dev);
   const int nt = std::max(1, std::min(nthreads < 1 ? 1 : nthreads, std::max(count, 1)));

@@ -5,6 +5,7 @@ workload's recipe, each on its own stream, stepped together by a pool of host th
   kappa * 2 tol (mixed form, tol 1e-8 as the batched configuration asks).
 * The batch is deterministic and free of cross-instance interference: each instance equals
   the same instance stepped alone by psp_step on a twin handle, to 1e-13.
+* A handle listed twice is refused (PSP_ERR_ARG) before any instance is stepped.
 """
 import numpy as np
 import pytest
@@ -57,3 +58,15 @@ def test_batch_matches_exact_and_single(dev):
         us, outs = outs, us
     for s in batch + twins:
         s.close()
+
+
+def test_batch_refuses_a_repeated_handle(dev):
+    import torch
+    from paper_1308_5626_gb300 import psp
+    w = inputs.c4_instance(0)
+    s = psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=psp.PSP_MIXED)
+    u = [t64(w.u0, dev), t64(w.u0, dev)]
+    out = [torch.empty_like(u[0]), torch.empty_like(u[0])]
+    with pytest.raises(RuntimeError):
+        psp.psp_step_batch([s.handle, s.handle], u, out, [w.dt, w.dt], 1e-8, nthreads=2)
+    s.close()
