@@ -723,6 +723,7 @@ def main():
     ms_max = _max_over_ranks(mixed["ms_total"], world, device)
     value = aggregate_value(a.steps, world, ms_max)
     infos = mixed["infos"]
+    u_mixed = mixed["u"]
     mixed["solver"].close()
     # per-kernel device times come from a second timed region of the same steps with the
     # library's event sampling on: the event records split the cycle graphs and slow the
@@ -739,9 +740,13 @@ def main():
     if not a.no_fp64_form:
         r = _time_form(w, psp.PSP_FP64, a.steps, a.warmup, device, world, False)
         ms64 = _max_over_ranks(r["ms_total"], world, device)
+        # both forms ran the same warm-up + timed steps from u^0: the relative difference of
+        # their final iterates (each step solved to the relative tolerance)
+        diff = float(torch.linalg.vector_norm(u_mixed - r["u"]) / torch.linalg.vector_norm(r["u"]))
         fp64 = {"value": aggregate_value(a.steps, world, ms64), "ms_per_step": ms64 / a.steps,
                 "iters_per_step": sum(i.iters for i in r["infos"]) / a.steps,
-                "cycles_per_step": sum(i.cycles for i in r["infos"]) / a.steps}
+                "cycles_per_step": sum(i.cycles for i in r["infos"]) / a.steps,
+                "mixed_vs_fp64_rel_diff": diff, "steps_compared": a.warmup + a.steps}
         r["solver"].close()
 
     e2e = None
