@@ -54,3 +54,35 @@ def test_tridiagonal_mock_is_recovered():
     ref = inputs.dense_to_band(A, 1)
     # interior rows are A's rows; the first and last row keep only the diagonal (paper)
     np.testing.assert_allclose(band[1:-1], ref[1:-1], rtol=1e-8, atol=1e-8)
+
+
+def _mock_golden():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "mock_test_setup.txt")
+    out = {}
+    with open(path) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].split()
+            if line:
+                out[line[0]] = line[1:]
+    return out
+
+
+def test_mock_inputs_follow_the_papers_setup():
+    """The seeded inputs reproduce the setup the paper states (tests/golden/mock_test_setup.txt):
+    its five sizes, a seven-diagonal diagonally dominant A, d = 1 (tridiagonal N), u^n = 1..n."""
+    g = _mock_golden()
+    assert tuple(int(v) for v in g["sizes"]) == inputs.MOCK_SIZES
+    ndiag, d = int(g["diagonals"][0]), int(g["d"][0])
+    for n in inputs.MOCK_SIZES[:3]:
+        A = inputs.mock_seven_diagonal(n, seed=n)
+        offs = {j - i for i, j in zip(*np.nonzero(A))}
+        assert offs == set(range(-(ndiag // 2), ndiag // 2 + 1))
+        off = np.abs(A).sum(axis=1) - np.abs(np.diag(A))
+        assert np.all(np.abs(np.diag(A)) > off)            # strictly diagonally dominant
+        # the fitted N has half-width d: tridiagonal storage (n, 2d + 1)
+        rng = np.random.default_rng(n)
+        Px = rng.standard_normal((n, 12))
+        band, _ = mrep.mrep(Px, A @ Px, d)
+        assert band.shape == (n, 2 * d + 1)
+    assert g["rhs"] == ["arange", "1", "n"]

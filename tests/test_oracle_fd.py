@@ -1,10 +1,11 @@
 """Pins for oracle.fd: central finite-difference weights (Eq. 1 discretised, Eq. 2).
 
 Independent checks: textbook stencils (Fornberg, Math. Comp. 51 (1988), Table 1 and
-the standard 2nd-order formulas), symmetry, and the measured convergence order on a
-smooth periodic function.
+the standard 2nd-order formulas; fixture tests/golden/central_fd_weights.txt), symmetry,
+and the measured convergence order on a smooth periodic function.
 """
 import math
+import os
 from fractions import Fraction as F
 
 import numpy as np
@@ -13,19 +14,20 @@ import pytest
 from oracle import fd
 
 
-@pytest.mark.parametrize("k,p,expected", [
-    (1, 2, [F(-1, 2), F(0), F(1, 2)]),
-    (2, 2, [F(1), F(-2), F(1)]),
-    (1, 4, [F(1, 12), F(-2, 3), F(0), F(2, 3), F(-1, 12)]),
-    (2, 4, [F(-1, 12), F(4, 3), F(-5, 2), F(4, 3), F(-1, 12)]),
-    (1, 6, [F(-1, 60), F(3, 20), F(-3, 4), F(0), F(3, 4), F(-3, 20), F(1, 60)]),
-    (2, 6, [F(1, 90), F(-3, 20), F(3, 2), F(-49, 18), F(3, 2), F(-3, 20), F(1, 90)]),
-    (1, 8, [F(1, 280), F(-4, 105), F(1, 5), F(-4, 5), F(0), F(4, 5), F(-1, 5), F(4, 105), F(-1, 280)]),
-    (2, 8, [F(-1, 560), F(8, 315), F(-1, 5), F(8, 5), F(-205, 72), F(8, 5), F(-1, 5), F(8, 315), F(-1, 560)]),
-    (3, 2, [F(-1, 2), F(1), F(0), F(-1), F(1, 2)]),
-    (4, 2, [F(1), F(-4), F(6), F(-4), F(1)]),
-    (4, 4, [F(-1, 6), F(2), F(-13, 2), F(28, 3), F(-13, 2), F(2), F(-1, 6)]),
-])
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "central_fd_weights.txt")
+
+
+def _golden_weights():
+    rows = []
+    with open(GOLDEN) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].split()
+            if line:
+                rows.append((int(line[0]), int(line[1]), [F(t) for t in line[2:]]))
+    return rows
+
+
+@pytest.mark.parametrize("k,p,expected", _golden_weights())
 def test_textbook_weights(k, p, expected):
     assert fd.central_weights_exact(k, p) == expected
 
