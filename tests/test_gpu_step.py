@@ -229,3 +229,18 @@ def test_full_size_2d_step(dev, precision):
     assert info.status == 0
     assert rel(out.cpu().numpy(), ref) <= bound
     s.close()
+
+
+def test_full_size_3d_step(dev):
+    """The 256^3 workload (8th order, radius 5 in every direction, m = 50, b = 3), mixed form,
+    at the launch configuration of the library (z-marching tiled stencil): one step against
+    the exact (Fourier) solve."""
+    w = inputs.c3()
+    op = Operator(w.shape, w.order, w.terms)
+    dt = _dt(w, op)
+    s = _solver(w, precision=1)
+    out, info = s.step(t64(w.u0, dev), dt, 1e-10)
+    ref = exact.solve_fourier(op, w.u0, dt)
+    assert info.status == 0
+    assert rel(out.cpu().numpy(), ref) <= 1e-8
+    s.close()
