@@ -1,7 +1,7 @@
 """Central finite-difference weights for the k-th derivative terms of Eq. 1.
 
 Eq. 1 writes the operator as a sum of alpha_ki * d^k u / dx_i^k; Eq. 2 is its
-discretisation.  The paper only asks for "a suitable discretization"; this oracle uses
+discretisation.  The paper leaves the discretisation method open; this oracle uses
 central differences of even accuracy order p on the half-width
 
     r = floor((k - 1) / 2) + p / 2,

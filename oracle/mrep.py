@@ -6,7 +6,7 @@ is a least-squares fit of P_y(i, :) on rows of P_x:
 * the first d and the last d rows: a simple linear fit (beta_0, beta_1) of P_y(i, :) on
   P_x(i, :); N(i, i) = beta_1 and the intercept beta_0 is discarded;
 * interior rows: the design matrix P_x* stacks a row of ones over P_x(i-d .. i+d, :)
-  ((2d+2) x m, "three regressors, four unknowns" for d = 1), and
+  ((2d+2) x m: for d = 1 three regressor rows plus the intercept, four unknowns), and
   N* = (P_x* P_x*^T)^{-1} P_x* P_y(i, :)^T by the normal equations.  N*(1) is the
   intercept; N*(j) for j >= 2 multiplies P_x(i - d + j - 2, :) and goes to
   N(i, i - d + j - 2).

@@ -2,9 +2,9 @@
 
 Periodic grid with n_i points per direction, h_i = 2 pi / n_i, vectors flattened with
 x fastest.  L u = sum over terms alpha * h_dir^-k * sum_j w_j u(x + j h e_dir) with the
-central weights of ``oracle.fd``.  The matrix-free product (the "residual computation"
-that replaces A x in the matrix-free GMRES of the paper's introduction) uses periodic
-shifts; ``dense_L`` assembles the same operator entry by entry for tiny grids.
+central weights of ``oracle.fd``.  The matrix-free product (a residual evaluation that
+stands in for A x in the paper's matrix-free GMRES) uses periodic shifts; ``dense_L``
+assembles the same operator entry by entry for tiny grids.
 """
 from __future__ import annotations
 

@@ -145,7 +145,7 @@ struct psp_ctx {
   psp_profile prof{};
   double *hostbuf = nullptr;   // pinned staging for psp_step_host
   double *dev_un = nullptr, *dev_unp1 = nullptr;
-  // host waits of psp_step: a stream synchronisation (the driver spins), or with
+  // host waits of psp_step: a stream synchronisation (the CUDA runtime spin-waits), or with
   // blocking_wait a blocking-sync event, on which the thread sleeps -- set by psp_step_batch
   // when it runs more threads than the host has cores
   bool blocking_wait = false;
