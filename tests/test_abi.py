@@ -56,3 +56,15 @@ def test_argument_errors_need_no_gpu(libpsp):
     assert st == psp.PSP_ERR_ARG
     assert b"NULL" in psp.lib().psp_last_error()
     assert psp.lib().psp_step(None, None, None, 0.1, 1e-8, None) == psp.PSP_ERR_ARG
+
+
+def test_opts_layout_matches_the_header(libpsp):
+    """psp_default_opts writes exactly the ctypes psp_opts: a C struct with a field the
+    binding lacks would write past it (guard bytes), and the new options default to off."""
+    from paper_1308_5626_gb300 import psp
+    size = ctypes.sizeof(psp.psp_opts)
+    buf = (ctypes.c_ubyte * (size + 64))(*([0xAB] * (size + 64)))
+    assert psp.lib().psp_default_opts(ctypes.cast(buf, ctypes.POINTER(psp.psp_opts))) == psp.PSP_OK
+    assert all(b == 0xAB for b in bytes(buf)[size:])
+    o = psp.psp_opts.from_buffer_copy(bytes(buf)[:size])
+    assert o.adjoint == 0 and o.cyclic == 0 and o.solver == psp.PSP_SOLVER_GMRES
