@@ -68,3 +68,35 @@ def test_opts_layout_matches_the_header(libpsp):
     assert all(b == 0xAB for b in bytes(buf)[size:])
     o = psp.psp_opts.from_buffer_copy(bytes(buf)[:size])
     assert o.adjoint == 0 and o.cyclic == 0 and o.solver == psp.PSP_SOLVER_GMRES
+
+
+def _create(shape, order=2, b=2, m=8, **opt):
+    from paper_1308_5626_gb300 import psp
+    g = psp.psp_grid()
+    g.ndim = len(shape)
+    for d in range(3):
+        g.n[d] = shape[d] if d < len(shape) else 1
+        g.length[d] = 6.283185307179586
+    t = (psp.psp_term * 1)()
+    t[0].k, t[0].dir, t[0].alpha = 2, 0, 1.0
+    o = psp.psp_default_opts()
+    for k, v in opt.items():
+        setattr(o, k, v)
+    h = ctypes.c_void_p()
+    return psp.lib().psp_create(ctypes.byref(g), order, t, 1, b, m, ctypes.byref(o), None, ctypes.byref(h))
+
+
+@pytest.mark.parametrize("shape,kw,what", [
+    ((1 << 16, 1 << 16), {}, b"2^31"),                                    # 2^32 unknowns
+    ((64, 64), {"cyclic": 1}, b"cyclic"),                                 # cyclic band off a 1D grid
+    ((9,), {"cyclic": 1}, b"cyclic"),                                     # n < 4b + 2
+    ((64,), {"solver": 1, "precision": 1}, b"BiCGSTAB"),                  # BiCGSTAB in the mixed form
+    ((64,), {"solver": 1, "m": 2}, b"BiCGSTAB"),                          # m < 3
+    ((64,), {"solver": 7}, b"solver"),
+    ((64,), {"precision": 5}, b"precision"),
+])
+def test_create_refuses_bad_arguments_without_gpu(libpsp, shape, kw, what):
+    from paper_1308_5626_gb300 import psp
+    m = kw.pop("m", 8)
+    assert _create(shape, m=m, **kw) == psp.PSP_ERR_ARG
+    assert what in psp.lib().psp_last_error()

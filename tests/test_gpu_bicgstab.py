@@ -73,3 +73,24 @@ def test_bicgstab_options(dev):
         psp.Solver((64,), 2, [(2, 0, 1.0)], 2, 8, precision=psp.PSP_MIXED, solver=psp.PSP_SOLVER_BICGSTAB)
     with pytest.raises(RuntimeError):
         psp.Solver((64,), 2, [(2, 0, 1.0)], 2, 2, solver=psp.PSP_SOLVER_BICGSTAB)
+
+
+def test_bicgstab_with_cyclic_band(dev):
+    """BiCGSTAB with the cyclic band on the 1D workload: the fitted N equals A, so after the
+    step that adopts it every FP64 step takes one iteration and matches the exact solve."""
+    import torch
+    from paper_1308_5626_gb300 import psp
+    w = inputs.c1(1024)
+    op = Operator(w.shape, w.order, w.terms)
+    s = psp.Solver(w.shape, w.order, w.terms, w.b, w.m, solver=psp.PSP_SOLVER_BICGSTAB, cyclic=1)
+    u = torch.tensor(w.u0, dtype=torch.float64, device=dev)
+    out = torch.empty_like(u)
+    its = []
+    for _ in range(5):
+        ref = exact.solve_fourier(op, u.cpu().numpy(), w.dt)
+        _, info = s.step(u, w.dt, 1e-12, out=out)
+        assert rel(out.cpu().numpy(), ref) <= 2e-9
+        its.append(int(info.iters))
+        u, out = out, u
+    s.close()
+    assert its[0] > 5 and all(k == 1 for k in its[2:]), its

@@ -244,3 +244,19 @@ def test_full_size_3d_step(dev):
     assert info.status == 0
     assert rel(out.cpu().numpy(), ref) <= 1e-8
     s.close()
+
+
+@pytest.mark.parametrize("precision,solver", [(0, 0), (1, 0), (0, 1)], ids=["gmres-fp64", "gmres-mixed", "bicgstab"])
+def test_zero_right_hand_side(dev, precision, solver):
+    """u^n = 0: the restart finds a zero residual, the step ends without an iteration and
+    u^{n+1} = 0 exactly (GMRES in both forms, BiCGSTAB)."""
+    import torch
+    w = inputs.c2(48, 40)
+    s = _solver(w, precision=precision, solver=solver)
+    u = torch.zeros(w.n, dtype=torch.float64, device=dev)
+    out = torch.full_like(u, 7.0)
+    for _ in range(2):
+        _, info = s.step(u, w.dt, 1e-10, out=out)
+        assert info.status == 0 and info.iters == 0
+        assert torch.count_nonzero(out).item() == 0
+    s.close()
