@@ -94,6 +94,9 @@ def _create(shape, order=2, b=2, m=8, **opt):
     ((64,), {"solver": 1, "m": 2}, b"BiCGSTAB"),                          # m < 3
     ((64,), {"solver": 7}, b"solver"),
     ((64,), {"precision": 5}, b"precision"),
+    ((0,), {}, b"positive"),                                              # empty grid
+    ((4,), {}, b"2b+1"),                                                  # n < 2b + 1
+    ((64,), {"m": 65}, b"restart length"),                                # m above 64
 ])
 def test_create_refuses_bad_arguments_without_gpu(libpsp, shape, kw, what):
     from paper_1308_5626_gb300 import psp

@@ -260,3 +260,34 @@ def test_zero_right_hand_side(dev, precision, solver):
         assert info.status == 0 and info.iters == 0
         assert torch.count_nonzero(out).item() == 0
     s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_max_restart_length(dev, precision):
+    """m = 64, the largest restart length (the scalar engine's largest shared layout and
+    cross-CTA sums over 2(m+1) values): one full cycle's R(m) equals the true residual of the
+    returned X, and a whole step meets the exact solve's bound."""
+    w = inputs.c2(64, 48)
+    op = Operator(w.shape, w.order, w.terms)
+    s_m = psp_solver_m(w, 64, precision, max_restarts=1)
+    out, info = s_m.step(t64(w.u0, dev), w.dt, 1e-30, allow_noconv=True)
+    assert info.cycles == 1
+    if precision == 0:   # the mixed form's cycle may end at its inner tolerance first
+        assert info.iters == 64
+        true_res = np.linalg.norm(w.u0 - op.apply_A(out.cpu().numpy(), w.dt))
+        assert abs(true_res - info.rel_res * np.linalg.norm(w.u0)) <= 1e-9 * np.linalg.norm(w.u0)
+    else:
+        assert 1 <= info.iters <= 64
+    s_m.close()
+    s_m = psp_solver_m(w, 64, precision)
+    tol = 1e-12 if precision == 0 else 1e-10
+    out, info = s_m.step(t64(w.u0, dev), w.dt, tol)
+    ref = exact.solve_fourier(op, w.u0, w.dt)
+    bound = exact.condition_number(op, w.dt) * 2 * tol if precision == 0 else 1e-8
+    assert info.status == 0 and rel(out.cpu().numpy(), ref) <= bound
+    s_m.close()
+
+
+def psp_solver_m(w, m, precision, **kw):
+    from paper_1308_5626_gb300 import psp
+    return psp.Solver(w.shape, w.order, w.terms, w.b, m, precision=precision, **kw)
