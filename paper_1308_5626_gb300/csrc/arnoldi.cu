@@ -526,8 +526,10 @@ __global__ void __launch_bounds__(kDotThreads, 1) k_dcgs_dots(const T *__restric
       VT c0{}, c1{};
       if (i0 < nvg) matvec_vec<T, MV / 8, MV % 8>(xin, s_c, (int)i0, mv.nx, mv.ny, mv.nz, w0, c0);
       if (i1 < nvg) matvec_vec<T, MV / 8, MV % 8>(xin, s_c, (int)i1, mv.nx, mv.ny, mv.nz, w1, c1);
-      if (i0 < nvg) { wout[i0] = w0; if (xcp) xcp[i0] = c0; }
-      if (i1 < nvg) { wout[i1] = w1; if (xcp) xcp[i1] = c1; }
+      // w_j is read again by pass B; the P_x copy only by the next fit: it streams out with
+      // evict_first instead of displacing basis lines pass B re-reads
+      if (i0 < nvg) { wout[i0] = w0; if (xcp) Vec<T>::st(xcp + i0, c0, pol_first); }
+      if (i1 < nvg) { wout[i1] = w1; if (xcp) Vec<T>::st(xcp + i1, c1, pol_first); }
       if (xcp) { v0 = c0; v1 = c1; }
       else {
         if (ok0) v0 = Vec<T>::ldnc(vjp + i0, pol_j);
