@@ -255,11 +255,14 @@ psp_status psp_fit_band_f32(psp_handle h, const float *Px, const float *Py, int6
  * psp_fit_band above).  For callers that cannot allocate device memory -- e.g. code in an
  * allocation-free real-time or graph-driven loop, or a plugin given a fixed memory budget --
  * and so cannot create a handle (psp_create allocates the solver workspace).  Same result
- * as psp_fit_band for a handle with half-width b and the given intercept flag: Px, Py are
- * n x M column-major FP64 device arrays (leading dimension ld >= n), N_band the device
- * output (n x (2b+1) band storage), *singular_rows (host, may be NULL) the count of
- * degenerate rows.  Work is enqueued on cuda_stream (a cudaStream_t, NULL = legacy default)
- * and the call returns after it finished if singular_rows is not NULL.
+ * as psp_fit_band for a handle with half-width b, the given intercept flag and
+ * opts.cyclic = 0: the first and last b rows are Algorithm 2's boundary rows (there is no
+ * cyclic variant).  Px, Py are n x M column-major FP64 device arrays (leading dimension
+ * ld >= n), N_band the device output (n x (2b+1) band storage), *singular_rows (host, may be
+ * NULL) the count of degenerate rows.  Work is enqueued on cuda_stream (a cudaStream_t,
+ * NULL = legacy default) and the call returns after it finished if singular_rows is not
+ * NULL; singular_rows must be NULL while cuda_stream is being captured into a graph
+ * (PSP_ERR_ARG otherwise), because reading the count back synchronises the stream.
  * Scratch: a static device array for at most 65536 rows (10 MiB per GPU that loads the
  * library, kept until exit); larger n returns PSP_ERR_ARG.  The first call on a device
  * looks up that array's device address (do it before any stream capture).  All calls share

@@ -77,6 +77,15 @@ extern "C" psp_status psp_fit_band_static(const double *Px, const double *Py, in
     count = g_singular_ptr[dev];
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  if (singular_rows) {
+    // the count is read back with a copy to host memory and a stream synchronisation, and
+    // neither may be enqueued while the stream is being captured into a graph
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess)
+      return err(PSP_ERR_CUDA, "psp_fit_band_static: cudaStreamIsCapturing failed");
+    if (cs != cudaStreamCaptureStatusNone)
+      return err(PSP_ERR_ARG, "psp_fit_band_static: singular_rows must be NULL while the stream is captured");
+  }
   cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), s);
   if (e != cudaSuccess) return err(PSP_ERR_CUDA, std::string("psp_fit_band_static: ") + cudaGetErrorString(e));
   psp::launch_fit<double>(b, intercept ? 1 : 0, n, M, Px, Py, ld, scratch, N_band, count, s);

@@ -276,12 +276,13 @@ def random_pd_part_band(n: int, b: int, seed: int, skew: float = 3.0) -> np.ndar
     for off in range(1, b + 1):
         w = rng.uniform(0.2, 1.0, n)          # symmetric part: w * (e_i - e_j)(e_i - e_j)^T
         k = rng.uniform(-1.0, 1.0, n) * skew  # skew part
-        for i in range(n - off):
-            j = i + off
-            band[i, b] += w[i]
-            band[j, b] += w[i]
-            band[i, b + off] += -w[i] + k[i]
-            band[j, b - off] += -w[i] - k[i]
+        # pair (i, j = i + off) for i < n - off; row j receives its share before row j's own
+        # pair (j, j + off) adds to it, the order of a loop over i
+        wi, ki = w[:n - off], k[:n - off]
+        band[off:, b] += wi
+        band[:n - off, b] += wi
+        band[:n - off, b + off] += -wi + ki
+        band[off:, b - off] += -wi - ki
     return band
 
 

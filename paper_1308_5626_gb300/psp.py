@@ -113,8 +113,12 @@ def lib() -> ctypes.CDLL:
 
 
 class PspError(RuntimeError):
-    def __init__(self, status: int, where: str):
-        msg = lib().psp_last_error().decode(errors="replace")
+    """A failing call: `status` is the psp_status; the message is the library's
+    psp_last_error() text, or `msg` for a refusal made by this binding before the call."""
+
+    def __init__(self, status: int, where: str, msg: Optional[str] = None):
+        if msg is None:
+            msg = lib().psp_last_error().decode(errors="replace")
         super().__init__("%s: %s (%s)" % (where, STATUS_NAMES.get(status, status), msg))
         self.status = status
 
@@ -234,16 +238,31 @@ def psp_fit_band(h, Px, Py, N_band, ld: Optional[int] = None, M: Optional[int] =
 
 
 def psp_fit_band_static(Px, Py, N_band, b: int, intercept: int = 1, ld: Optional[int] = None,
-                        M: Optional[int] = None, n: Optional[int] = None, stream: int = 0) -> int:
-    """Allocation-free band fit (no handle): Px, Py FP64 tensors shaped (M, ld); returns the
-    number of degenerate rows."""
+                        M: Optional[int] = None, n: Optional[int] = None, stream: int = 0,
+                        want_count: bool = True) -> Optional[int]:
+    """Allocation-free band fit (no handle).  Px, Py: contiguous float64 CUDA tensors shaped
+    (M, ld) (row c = history column c), N_band: contiguous float64 CUDA tensor of at least
+    n (2b+1) values.  Returns the number of degenerate rows, or None with want_count=False
+    (required while the stream is captured into a graph).  Tensors of another dtype, device
+    or shape are refused here, before any pointer reaches the library."""
+    import torch
+    for name, t in (("Px", Px), ("Py", Py), ("N_band", N_band)):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+            raise PspError(PSP_ERR_ARG, "psp_fit_band_static", "%s must be a contiguous float64 CUDA tensor" % name)
+    if Px.dim() != 2 or Py.shape != Px.shape:
+        raise PspError(PSP_ERR_ARG, "psp_fit_band_static", "Px and Py must both be shaped (M, ld)")
     M = int(Px.shape[0]) if M is None else int(M)
     ld = int(Px.shape[1]) if ld is None else int(ld)
     n = ld if n is None else int(n)
+    if not (1 <= M <= Px.shape[0] and n <= ld <= Px.shape[1] and n >= 1 and 1 <= int(b)):
+        raise PspError(PSP_ERR_ARG, "psp_fit_band_static", "need 1 <= M <= rows and n <= ld <= columns of Px")
+    if N_band.numel() < n * (2 * int(b) + 1):
+        raise PspError(PSP_ERR_ARG, "psp_fit_band_static", "N_band holds fewer than n (2b+1) values")
     sing = ctypes.c_int(0)
     _check(lib().psp_fit_band_static(_ptr(Px), _ptr(Py), ld, M, n, int(b), int(intercept), _ptr(N_band),
-                                     ctypes.byref(sing), ctypes.c_void_p(stream)), "psp_fit_band_static")
-    return sing.value
+                                     ctypes.byref(sing) if want_count else None, ctypes.c_void_p(stream)),
+           "psp_fit_band_static")
+    return sing.value if want_count else None
 
 
 def psp_set_band(h, N_band) -> None:

@@ -103,3 +103,17 @@ def test_create_refuses_bad_arguments_without_gpu(libpsp, shape, kw, what):
     m = kw.pop("m", 8)
     assert _create(shape, m=m, **kw) == psp.PSP_ERR_ARG
     assert what in psp.lib().psp_last_error()
+
+
+def test_static_fit_binding_refuses_host_and_fp32_tensors():
+    """The allocation-free fit's binding passes raw pointers to an FP64-only kernel: tensors
+    that are not contiguous float64 CUDA tensors (here CPU and FP32 ones) are refused with
+    PSP_ERR_ARG before the library is called (no GPU needed)."""
+    import torch
+    from paper_1308_5626_gb300 import psp
+    x = torch.zeros((4, 100), dtype=torch.float64)
+    out = torch.zeros((100, 3), dtype=torch.float64)
+    for args in ((x, x, out), (x.float(), x.float(), out)):
+        with pytest.raises(psp.PspError) as e:
+            psp.psp_fit_band_static(*args, 1)
+        assert e.value.status == psp.PSP_ERR_ARG
