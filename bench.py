@@ -1,30 +1,38 @@
 #!/usr/bin/env python
-"""Benchmark: implicit-Euler steps per second of PSP-GMRES on the 2D workload.
+"""Benchmark: implicit-Euler steps per second of PSP-GMRES on the 3D workload.
 
-Workload (inputs.c2): 2D periodic anisotropic advection-diffusion, 6th-order central FD
-(13-point cross), 1024 x 1024 grid (1,048,576 unknowns, x fastest), GMRES restart m = 40,
-band half-width b = 4, CFL 20, relative tolerance 1e-10, u^0 a seeded Gaussian random
-field with k^-2 spectrum.  One benchmark step = one implicit-Euler step: every restart
-cycle of Algorithm 1 (stencil matvecs, preconditioner solves, CGS2 Arnoldi, Givens,
-update), the Algorithm 2 fit of the next preconditioner and its partitioned
-factorisation, continuing the time series u^{n+1} -> next step.
+Workload (inputs.c3): 3D periodic diffusion plus fourth-derivative hyperdiffusion,
+8th-order central FD (31-point cross), 256^3 grid (16,777,216 unknowns, x fastest), GMRES
+restart m = 50, band half-width b = 3, rho(L) dt = 100, relative tolerance 1e-10, u^0 white
+noise low-passed to |k| < 32.  One benchmark step = one implicit-Euler step: every restart
+cycle of Algorithm 1 (stencil matvecs, preconditioner solves, DCGS2 Arnoldi, Givens,
+update), the Algorithm 2 fit of the next candidate preconditioner and its partitioned
+factorisation when the next step tries it, continuing the time series u^{n+1} -> next
+step.  The line reports, beside steps/s, the Arnoldi iterations and restart cycles per
+step, ms per Arnoldi iteration and how many fitted candidates were made, tried and
+adopted in the timed steps, so that the throughput says what it measures.
 
 Arms
 * default (``--impl psp``): the mixed form (FP32 Krylov vectors and kernels, FP64
   Hessenberg, fit, restart residual and update) timed on the GPU; the plain FP64 GPU form
   is timed in the same run and reported under "fp64_form"; ``e2e`` repeats the chosen
-  form through psp_step_host with pinned host buffers; ``cpu_baseline`` times the oracle
+  form through psp_step_host with pinned host buffers; ``c2`` repeats the headline and
+  its FP64 form on the 2D 1024^2 workload (inputs.c2); ``cpu_baseline`` times the oracle
   (numpy FP64) on a bounded sample on the host cores.
-* ``--impl reference``: the oracle, as it stands, on the host cores (rank 0 only).
+* ``--impl reference``: the oracle, as it stands, on the host cores (rank 0 only): each
+  bench step is one Arnoldi iteration of an oracle restart cycle of the same workload
+  (its matvec and modified Gram-Schmidt sweep), timed; the line's value scales the mean
+  iteration time to implicit steps/s by the oracle's own record of iterations and cycles
+  per step of this workload.
 
 Multi-GPU: replicas (the step does not shard; see the design notes).  Every rank runs
 its own copy of the workload; value = total steps of all ranks / max-over-ranks time.
 
 Timing: W untimed warm-up steps, then K steps between CUDA events on the solver's stream,
-bracketed by a barrier and a device synchronise; the working set (Krylov basis 168 MB,
-history ring 688 MB in the mixed form) is larger than the 129 MB L2, so no flush is used.
-Per-kernel device times come from the library's profiling mode (CUDA event records
-captured inside the cycle graphs), switched on for the timed region.
+bracketed by a barrier and a device synchronise; the working set (Krylov basis 3.4 GB,
+history ring 13.7 GB in the mixed form) is far larger than the 129 MB L2, so no flush is
+used.  Per-kernel device times come from the library's profiling mode (CUDA event records
+captured inside the cycle graphs), switched on in a second timed region of the same steps.
 """
 from __future__ import annotations
 
@@ -63,7 +71,10 @@ def _args():
     ap.add_argument("--batch", type=int, default=512, help="instances of the batched line (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--batch-threads", type=int, default=16)
-    ap.add_argument("--nx", type=int, default=1024, help="grid points per direction (default: the full workload)")
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2"], help="headline workload")
+    ap.add_argument("--n3", type=int, default=256, help="3D grid points per direction (default: the full workload)")
+    ap.add_argument("--nx", type=int, default=1024, help="2D grid points per direction (default: the full workload)")
+    ap.add_argument("--no-c2", action="store_true", help="skip the 2D workload's extra line")
     return ap.parse_args()
 
 
@@ -216,7 +227,28 @@ def aggregate_value(steps: int, world: int, max_ms: float) -> float:
 # GPU arm
 # --------------------------------------------------------------------------------------
 
-def _time_form(w, precision, steps, warmup, device, world, profile):
+def library_dt(w) -> float:
+    """The workload's time step: w.dt, or for a spectral-radius rule (rho(L) dt = w.rho_dt)
+    rho = max |lambda| of the library's own stencil of L (psp_get_stencil) over the grid's
+    Fourier modes, lambda(theta) = sum_d sum_j w_dj e^{i j theta_d}."""
+    if w.dt is not None:
+        return float(w.dt)
+    import numpy as np
+    from paper_1308_5626_gb300 import psp
+    s = psp.Solver(w.shape, w.order, w.terms, w.b, 2, max_hist_cols=4)
+    wst, R = psp.psp_get_stencil(s.handle)
+    s.close()
+    lam = np.zeros(tuple(reversed(w.shape)), dtype=np.complex128)
+    for d, nd in enumerate(w.shape):
+        th = 2.0 * np.pi * np.arange(nd) / nd
+        ld = sum(wst[d][j + R] * np.exp(1j * j * th) for j in range(-R, R + 1))
+        shp = [1] * len(w.shape)
+        shp[len(w.shape) - 1 - d] = nd
+        lam = lam + ld.reshape(shp)
+    return float(w.rho_dt / np.abs(lam).max())
+
+
+def _time_form(w, precision, steps, warmup, device, world, profile, dt):
     import torch
     from paper_1308_5626_gb300 import psp
     stream = torch.cuda.Stream(device=device)
@@ -226,7 +258,7 @@ def _time_form(w, precision, steps, warmup, device, world, profile):
         out = torch.empty_like(u)
         infos = []
         for _ in range(warmup):
-            solver.step(u, w.dt, w.tol, out=out)
+            solver.step(u, dt, w.tol, out=out)
             u, out = out, u
         if profile:
             psp.psp_set_profiling(solver.handle, True)
@@ -239,7 +271,7 @@ def _time_form(w, precision, steps, warmup, device, world, profile):
         t_host0 = time.perf_counter()
         e0.record(stream)
         for _ in range(steps):
-            _, info = solver.step(u, w.dt, w.tol, out=out)
+            _, info = solver.step(u, dt, w.tol, out=out)
             infos.append(info)
             u, out = out, u
         e1.record(stream)
@@ -338,8 +370,10 @@ def _standalone(w, device, hbm_peak, fp64_peak_tflops):
         by = 2.0 * es * n3
         out[name]["stencil_256cubed"] = {"us": best * 1e3, "bytes": by, "gbs": by / (best * 1e-3) / 1e9,
                                          "frac_hbm": by / (best * 1e-3) / 1e9 / hbm_peak}
-    out["note"] = ("psp_matvec / psp_fit_band through the C ABI on the %s grid (stencil also on 256^3), CUDA events around each "
-                   "call, minimum of 20 / 3 calls (coefficients uploaded once per dt, outside the timed calls); "
+    out["best_case"] = True
+    out["note"] = ("best case: psp_matvec / psp_fit_band through the C ABI on the %s grid (stencil also on 256^3), CUDA "
+                   "events around each call, minimum of 20 / 3 calls (coefficients uploaded once per dt, outside the timed "
+                   "calls), unlike the event-timed means of the step's kernel classes; "
                    "the fit uses M = 2(m+1) random history columns; FP64 peak %.2f TFLOP/s measured"
                    % ("x".join(str(v) for v in w.shape), fp64_peak_tflops))
     return out
@@ -353,19 +387,7 @@ def _adjoint_line(device):
     from paper_1308_5626_gb300 import autograd, inputs, psp
     w, factors = inputs.c5(512)
     # dt from rho(L) dt = 10, rho(L) the largest |eigenvalue| of the library's own stencil of L
-    # (psp_get_stencil) over the grid's Fourier modes
-    import numpy as np
-    s = psp.Solver(w.shape, w.order, w.terms, w.b, 2, max_hist_cols=4)
-    wst, R = psp.psp_get_stencil(s.handle)
-    s.close()
-    lam = 0.0
-    for d, nd in enumerate(w.shape):
-        th = 2.0 * np.pi * np.arange(nd) / nd
-        ld = sum(wst[d][j + R] * np.exp(1j * j * th) for j in range(-R, R + 1))
-        shp = [1] * len(w.shape)
-        shp[len(w.shape) - 1 - d] = nd
-        lam = lam + ld.reshape(shp)
-    dt = w.rho_dt / float(np.abs(lam).max())
+    dt = library_dt(w)
     alphas = [t.alpha * f for t, f in zip(w.terms, factors)]
     target = torch.zeros(w.n, dtype=torch.float64, device=device)
     out = {"workload": w.name, "steps": w.steps}
@@ -584,7 +606,7 @@ def _batch_line(device, count: int, steps: int, nthreads: int):
                     "host threads; host wall clock"}
 
 
-def _e2e(w, precision, steps, device):
+def _e2e(w, precision, steps, device, dt):
     """Same metric through the C ABI with host buffers: psp_step_host copies u^n from pinned
     host memory to the device and u^{n+1} back every step."""
     import torch
@@ -595,12 +617,12 @@ def _e2e(w, precision, steps, device):
         a = torch.tensor(w.u0, dtype=torch.float64).pin_memory()
         b = torch.empty_like(a).pin_memory()
         for _ in range(2):
-            psp.psp_step_host(solver.handle, a, b, w.dt, w.tol)
+            psp.psp_step_host(solver.handle, a, b, dt, w.tol)
             a, b = b, a
         torch.cuda.synchronize(device)
         t0 = time.perf_counter()
         for _ in range(steps):
-            psp.psp_step_host(solver.handle, a, b, w.dt, w.tol)
+            psp.psp_step_host(solver.handle, a, b, dt, w.tol)
             a, b = b, a
         torch.cuda.synchronize(device)
         dt_s = time.perf_counter() - t0
@@ -615,43 +637,43 @@ def _e2e(w, precision, steps, device):
 # --------------------------------------------------------------------------------------
 
 def _oracle_iterations_per_step(w):
-    """Mean Arnoldi iterations per implicit step of the oracle on this workload, from the
-    committed record written by oracle/record_iterations.py (None if absent)."""
+    """Mean Arnoldi iterations and restart cycles per implicit step of the oracle on this
+    workload, from the committed record written by oracle/record_iterations.py (None if
+    absent), and that record's description."""
     p = os.path.join(ROOT, "oracle", "%s_series.json" % w.name.split("_")[0])
     if not os.path.exists(p):
-        return None, None
+        return None, None, None
     with open(p) as fh:
         d = json.load(fh)
     if d.get("workload") != w.name:
-        return None, None
-    return float(d["mean_iterations"]), float(d["mean_cycles"])
+        return None, None, None
+    what = ("the oracle's first step (N = I), oracle/%s" % os.path.basename(p)) if d.get("first_step_only") else \
+        ("the oracle's %d-step series, oracle/%s" % (len(d["steps"]), os.path.basename(p)))
+    return float(d["mean_iterations"]), float(d["mean_cycles"]), what
 
 
-def _oracle_sample(w, iters_per_step=None, cycles_per_step=None):
-    """Times the oracle on a bounded sample of one implicit step and scales it to steps/s:
-    one restart cycle of Algorithm 1 (m preconditioned matvecs with MGS, N = I) and one
-    Algorithm 2 fit of the full history ring.  Per-step time = time per Arnoldi iteration
-    x iterations per step + time per restart x restarts per step + fit time."""
-    import numpy as np
-    from oracle import gmres, mrep
+def _oracle_cycle(w, dt, iters):
+    """Times one oracle restart cycle of `iters` Arnoldi iterations (Algorithm 1 with N = I,
+    modified Gram-Schmidt, the restart's matvec included) on the workload; returns seconds."""
+    from oracle import gmres
     from oracle.operator import Operator
     op = Operator(w.shape, w.order, w.terms)
-    A = lambda x: op.apply_A(x, w.dt)
+    A = lambda x: op.apply_A(x, dt)
     t0 = time.perf_counter()
-    res = gmres.pspgmres(A, w.u0, None, 0.0, w.m, w.u0, 1)
-    t_cycle = time.perf_counter() - t0
-    cols = min(len(res.Px), 2 * (w.m + 1))
-    Px = np.stack(res.Px[-cols:], axis=1)
-    Py = np.stack(res.Py[-cols:], axis=1)
-    t1 = time.perf_counter()
-    mrep.mrep(Px, Py, w.b, True)
-    t_fit = time.perf_counter() - t1
-    t_iter = t_cycle / res.iterations
-    if iters_per_step is None:
-        iters_per_step, cycles_per_step = float(w.m), 1.0
-    t_step = t_iter * iters_per_step + t_fit
-    return {"t_iter": t_iter, "t_fit": t_fit, "t_step": t_step, "sample_s": t_cycle + t_fit,
-            "iters_per_step": iters_per_step, "cycles_per_step": cycles_per_step}
+    res = gmres.pspgmres(A, w.u0, None, 0.0, iters, w.u0, 1)
+    t = time.perf_counter() - t0
+    assert res.iterations == iters
+    return t
+
+
+def _oracle_step_model(t_cycle, iters_sampled, ips, cps):
+    """Implicit-step time implied by a timed cycle: its time per matvec (iterations plus the
+    restart, each one matvec and one Gram-Schmidt sweep) times the matvecs of a step
+    (iterations plus restarts).  The sweeps of a sampled cycle stop at j = iters_sampled,
+    below the longer cycles of a step, and the Algorithm 2 fit is not counted, so the
+    model is a lower bound on the oracle's step time."""
+    t_mv = t_cycle / (iters_sampled + 1)
+    return t_mv * (ips + cps)
 
 
 def _cores_used():
@@ -661,38 +683,154 @@ def _cores_used():
     return 1
 
 
+def _headline_workload(a):
+    from paper_1308_5626_gb300 import inputs
+    return inputs.c3(a.n3) if a.workload == "c3" else inputs.c2(a.nx)
+
+
+def _oracle_dt(w):
+    """dt of the workload as the oracle sees it (its own spectral radius, for rho(L) dt rules)."""
+    if w.dt is not None:
+        return float(w.dt)
+    from oracle.operator import Operator
+    return float(w.with_dt(Operator(w.shape, w.order, w.terms).spectral_radius()))
+
+
 def run_reference(a):
     world, rank, _ = _dist()
     if rank != 0:
         return
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
-    from paper_1308_5626_gb300 import inputs
-    w = inputs.c2(a.nx)
-    ips, cps = _oracle_iterations_per_step(w)
-    times = []
-    for i in range(a.warmup + a.steps):
-        s = _oracle_sample(w, ips, cps)
-        if i >= a.warmup:
-            times.append(s["t_step"])
-    t = sum(times) / len(times)
-    value = 1.0 / t
-    sample = ("per step: one restart cycle (m=%d Arnoldi iterations, MGS, N=I) and one Algorithm-2 fit timed, "
-              "scaled to %.1f iterations/step from the oracle's own record of this workload" % (w.m, s["iters_per_step"]))
+    w = _headline_workload(a)
+    dt = _oracle_dt(w)
+    ips, cps, what = _oracle_iterations_per_step(w)
+    if ips is None:
+        ips, cps, what = float(w.m), 1.0, "one full restart cycle per step (no oracle record present)"
+    # W warm-up iterations in a cycle of their own, then one cycle of K timed iterations:
+    # each bench step is one Arnoldi iteration (a matvec and an MGS sweep) of the oracle
+    if a.warmup > 0:
+        _oracle_cycle(w, dt, a.warmup)
+    t = _oracle_cycle(w, dt, a.steps)
+    ms_iter = 1000.0 * t / a.steps
+    t_step = _oracle_step_model(t, a.steps, ips, cps)
+    value = 1.0 / t_step
+    sample = ("each bench step is one Arnoldi iteration of an oracle restart cycle on %s (matvec + MGS sweep, "
+              "N = I; W warm-up iterations in a cycle of their own, then one cycle of K = %d timed iterations plus "
+              "its restart matvec, %.1f s); value scales the time per matvec to %.1f iterations + %.1f restarts per "
+              "implicit step from %s; the Algorithm 2 fit is not counted (a lower bound on the oracle's step time)"
+              % (w.name, a.steps, t, ips, cps, what))
     line = {"impl": "reference", "metric": "implicit steps/s", "value": value, "unit": "implicit steps/s",
-            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 * t,
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_iter,
+            "step_unit": "oracle Arnoldi iteration", "implied_ms_per_implicit_step": 1000.0 * t_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": w.name, "grid": list(w.shape), "order": w.order,
-                                            "m": w.m, "b": w.b, "tol": w.tol},
+                                            "m": w.m, "b": w.b, "tol": w.tol, "dt": dt},
             "cpu_baseline": {"value": value, "unit": "implicit steps/s", "cores": _cores_used(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "implicit steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+def _cpu_baseline(w):
+    """The oracle on a bounded sample of the workload (about 10-30 s of one host core):
+    one restart cycle of q Arnoldi iterations, scaled like the reference arm."""
+    dt = _oracle_dt(w)
+    ips, cps, what = _oracle_iterations_per_step(w)
+    if ips is None:
+        ips, cps, what = float(w.m), 1.0, "one full restart cycle per step (no oracle record present)"
+    q = 3 if w.n > 4_000_000 else min(w.m, 20)
+    t = _oracle_cycle(w, dt, q)
+    t_step = _oracle_step_model(t, q, ips, cps)
+    return {"value": 1.0 / t_step, "unit": "implicit steps/s", "cores": _cores_used(), "kind": "oracle",
+            "sample": "one oracle restart cycle of %d Arnoldi iterations (N = I, MGS; %.1f s) on %s, scaled by its "
+                      "time per matvec to %.1f iterations + %.1f restarts per implicit step from %s; the Algorithm 2 "
+                      "fit is not counted (a lower bound on the oracle's step time)" % (q, t, w.name, ips, cps, what)}
+
+
 # --------------------------------------------------------------------------------------
 # main
 # --------------------------------------------------------------------------------------
+
+def _summary(infos, steps):
+    """Per-step averages and the preconditioner decisions of the timed steps."""
+    from paper_1308_5626_gb300 import psp
+    its = sum(i.iters for i in infos)
+    return {"iters_per_step": its / steps,
+            "cycles_per_step": sum(i.cycles for i in infos) / steps,
+            "rel_res_max": max(i.rel_res for i in infos),
+            "candidates": {"fitted": sum(1 for i in infos if i.flags & psp.PSP_FLAG_FITTED),
+                           "tried": sum(1 for i in infos if i.flags & psp.PSP_FLAG_CANDIDATE_TRIED),
+                           "adopted": sum(1 for i in infos if i.flags & psp.PSP_FLAG_CANDIDATE_ACCEPTED)},
+            "iterations_total": its}
+
+
+def _roofline(prof, workload, hbm_peak, peak_kind):
+    """Kernel classes of the profiling mode as GB/s of algorithmic bytes, and the roofline
+    object of the class with the largest device time."""
+    kernels = {}
+    for name, d in prof.items():
+        if d["launches"] > 0 and d["ms"] > 0:
+            kernels[name] = {"ms_per_launch": d["ms"] / d["launches"], "launches": d["launches"],
+                             "bytes_per_launch": d["bytes"] / d["launches"],
+                             "gbs": d["bytes"] / (d["ms"] * 1e-3) / 1e9,
+                             "frac": d["bytes"] / (d["ms"] * 1e-3) / 1e9 / hbm_peak,
+                             "share_of_profiled": 0.0}
+    tot = sum(d["ms"] for d in prof.values()) or 1.0
+    for name in kernels:
+        kernels[name]["share_of_profiled"] = prof[name]["ms"] / tot
+    if not kernels:
+        return None, kernels
+    dom = max(kernels, key=lambda k: prof[k]["ms"])
+    kd = kernels[dom]
+    ent = _traffic_for(dom, workload)
+    # the capture is one launch at one iteration j; traffic scales with the columns
+    # streamed, so it is scaled to the mean launch by its algorithmic bytes
+    traffic = None
+    if ent and ent.get("algorithmic_bytes"):
+        traffic = ent["dram_bytes_per_launch"] / ent["algorithmic_bytes"] * kd["bytes_per_launch"]
+    roof = {"kernel": dom, "bound": "hbm", "achieved": kd["gbs"], "peak": hbm_peak, "unit": "GB/s",
+            "frac": kd["gbs"] / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
+            "bytes_per_launch": kd["bytes_per_launch"], "ms_per_launch": kd["ms_per_launch"]}
+    return roof, kernels
+
+
+def _workload_forms(w, a, device, world, hbm_peak, peak_kind, with_fp64=True, with_profile=True):
+    """The mixed form timed on workload w (no profiling), its kernel classes from a second
+    timed region with the library's event sampling on, and the plain FP64 form."""
+    import torch
+    from paper_1308_5626_gb300 import psp
+    dt = library_dt(w)
+    mixed = _time_form(w, psp.PSP_MIXED, a.steps, a.warmup, device, world, False, dt)
+    ms_max = _max_over_ranks(mixed["ms_total"], world, device)
+    out = {"value": aggregate_value(a.steps, world, ms_max), "ms_per_step": ms_max / a.steps, "dt": dt}
+    out.update(_summary(mixed["infos"], a.steps))
+    out["ms_per_iteration"] = out["ms_per_step"] / max(out["iters_per_step"], 1e-9)
+    out["gpu_launches"] = int(sum(i.launches for i in mixed["infos"]))
+    u_mixed = mixed["u"]
+    mixed["solver"].close()
+    if with_profile:
+        pr = _time_form(w, psp.PSP_MIXED, a.steps, a.warmup, device, world, True, dt)
+        out["ms_per_step_with_events"] = _max_over_ranks(pr["ms_total"], world, device) / a.steps
+        out["roofline"], out["kernels"] = _roofline(pr["prof"], w.name, hbm_peak, peak_kind)
+        pr["solver"].close()
+    if with_fp64:
+        r = _time_form(w, psp.PSP_FP64, a.steps, a.warmup, device, world, False, dt)
+        ms64 = _max_over_ranks(r["ms_total"], world, device)
+        # both forms ran the same warm-up + timed steps from u^0: the relative difference of
+        # their final iterates (each step solved to the relative tolerance)
+        diff = float(torch.linalg.vector_norm(u_mixed - r["u"]) / torch.linalg.vector_norm(r["u"]))
+        f = {"value": aggregate_value(a.steps, world, ms64), "ms_per_step": ms64 / a.steps,
+             "mixed_vs_fp64_rel_diff": diff, "steps_compared": a.warmup + a.steps}
+        f.update(_summary(r["infos"], a.steps))
+        f["ms_per_iteration"] = f["ms_per_step"] / max(f["iters_per_step"], 1e-9)
+        out["fp64_form"] = f
+        out["speedup_vs_fp64_form"] = out["value"] / f["value"]
+        r["solver"].close()
+    del u_mixed
+    torch.cuda.empty_cache()
+    return out
+
 
 def main():
     a = _args()
@@ -714,52 +852,60 @@ def main():
         build.build()
     _barrier(world)
     build.build()
-    w = inputs.c2(a.nx)
+    hbm_peak, peak_kind = _peaks()
+    w = _headline_workload(a)
+    dt = library_dt(w)
 
     clocks = ClockSampler(local)
     clocks.start()
-    mixed = _time_form(w, psp.PSP_MIXED, a.steps, a.warmup, device, world, False)
+    mixed = _time_form(w, psp.PSP_MIXED, a.steps, a.warmup, device, world, False, dt)
     clk = clocks.stop()
     ms_max = _max_over_ranks(mixed["ms_total"], world, device)
     value = aggregate_value(a.steps, world, ms_max)
     infos = mixed["infos"]
     u_mixed = mixed["u"]
     mixed["solver"].close()
+    summ = _summary(infos, a.steps)
     # per-kernel device times come from a second timed region of the same steps with the
     # library's event sampling on: the event records split the cycle graphs and slow the
     # step by several per cent, so the headline value above is taken without them
     prof = None
     prof_ms = None
     if not a.no_profile:
-        pr = _time_form(w, psp.PSP_MIXED, a.steps, a.warmup, device, world, True)
+        pr = _time_form(w, psp.PSP_MIXED, a.steps, a.warmup, device, world, True, dt)
         prof = pr["prof"]
         prof_ms = _max_over_ranks(pr["ms_total"], world, device) / a.steps
         pr["solver"].close()
 
     fp64 = None
     if not a.no_fp64_form:
-        r = _time_form(w, psp.PSP_FP64, a.steps, a.warmup, device, world, False)
+        r = _time_form(w, psp.PSP_FP64, a.steps, a.warmup, device, world, False, dt)
         ms64 = _max_over_ranks(r["ms_total"], world, device)
-        # both forms ran the same warm-up + timed steps from u^0: the relative difference of
-        # their final iterates (each step solved to the relative tolerance)
         diff = float(torch.linalg.vector_norm(u_mixed - r["u"]) / torch.linalg.vector_norm(r["u"]))
         fp64 = {"value": aggregate_value(a.steps, world, ms64), "ms_per_step": ms64 / a.steps,
-                "iters_per_step": sum(i.iters for i in r["infos"]) / a.steps,
-                "cycles_per_step": sum(i.cycles for i in r["infos"]) / a.steps,
                 "mixed_vs_fp64_rel_diff": diff, "steps_compared": a.warmup + a.steps}
+        fp64.update(_summary(r["infos"], a.steps))
+        fp64["ms_per_iteration"] = fp64["ms_per_step"] / max(fp64["iters_per_step"], 1e-9)
         r["solver"].close()
+    del u_mixed
+    torch.cuda.empty_cache()
 
     e2e = None
     if not a.no_e2e:
-        e = _e2e(w, psp.PSP_MIXED, a.steps, device)
+        e = _e2e(w, psp.PSP_MIXED, a.steps, device, dt)
         secs = _max_over_ranks(e.pop("seconds"), world, device)
         e2e = {"value": world * a.steps / secs}
         e2e.update(e)
 
-    hbm_peak, peak_kind = _peaks()
+    w2 = inputs.c2(a.nx)
+    c2 = None
+    if not a.no_c2 and a.workload != "c2":
+        c2 = _workload_forms(w2, a, device, world, hbm_peak, peak_kind, with_fp64=not a.no_fp64_form,
+                             with_profile=not a.no_profile)
+        c2 = dict({"workload": w2.name}, **c2)
     standalone = None
     if not a.no_standalone and rank == 0:
-        standalone = _standalone(w, device, hbm_peak, FP64_PEAK_TFLOPS)
+        standalone = _standalone(w2, device, hbm_peak, FP64_PEAK_TFLOPS)
     adj = None
     if not a.no_adjoint and rank == 0:
         adj = _adjoint_line(device)
@@ -774,75 +920,46 @@ def main():
         cyclic = _cyclic_line(device)
     integ = None
     if not a.no_integrators and rank == 0:
-        integ = _integrators_line(w, device)
+        integ = _integrators_line(w2, device)
     bicg = None
     if not a.no_bicgstab and rank == 0:
-        bicg = _bicgstab_line(w, device)
+        bicg = _bicgstab_line(w2, device)
 
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return
 
-    roofline = None
-    kernels = {}
+    roofline, kernels = (None, {})
     if prof:
-        for name, d in prof.items():
-            if d["launches"] > 0 and d["ms"] > 0:
-                kernels[name] = {"ms_per_launch": d["ms"] / d["launches"], "launches": d["launches"],
-                                 "bytes_per_launch": d["bytes"] / d["launches"],
-                                 "gbs": d["bytes"] / (d["ms"] * 1e-3) / 1e9,
-                                 "frac": d["bytes"] / (d["ms"] * 1e-3) / 1e9 / hbm_peak,
-                                 "share_of_profiled": 0.0}
-        tot = sum(d["ms"] for d in prof.values()) or 1.0
-        for name in kernels:
-            kernels[name]["share_of_profiled"] = prof[name]["ms"] / tot
-        if kernels:
-            dom = max(kernels, key=lambda k: prof[k]["ms"])
-            kd = kernels[dom]
-            ent = _traffic_for(dom, w.name)
-            # the capture is one launch at iteration j; traffic scales with the columns
-            # streamed, so it is scaled to the mean launch by its algorithmic bytes
-            traffic = None
-            if ent and ent.get("algorithmic_bytes"):
-                traffic = ent["dram_bytes_per_launch"] / ent["algorithmic_bytes"] * kd["bytes_per_launch"]
-            roofline = {"kernel": dom, "bound": "hbm", "achieved": kd["gbs"], "peak": hbm_peak,
-                        "unit": "GB/s", "frac": kd["gbs"] / hbm_peak, "traffic": traffic,
-                        "peak_kind": peak_kind, "bytes_per_launch": kd["bytes_per_launch"],
-                        "ms_per_launch": kd["ms_per_launch"]}
+        roofline, kernels = _roofline(prof, w.name, hbm_peak, peak_kind)
 
     cpu = None
     if not a.no_cpu_baseline:
-        ips, cps = _oracle_iterations_per_step(w)
-        if ips is None:
-            ips = sum(i.iters for i in infos) / len(infos)
-            cps = sum(i.cycles for i in infos) / len(infos)
-            src = "the GPU FP64-algorithm count of this run (no oracle record present)"
-        else:
-            src = "the oracle's own record of this workload"
-        s = _oracle_sample(w, ips, cps)
-        cpu = {"value": 1.0 / s["t_step"], "unit": "implicit steps/s", "cores": _cores_used(), "kind": "oracle",
-               "sample": "one restart cycle (m=%d Arnoldi iterations, MGS, N=I) + one Algorithm-2 fit of %d columns "
-                         "timed (%.1f s), scaled to %.1f iterations per step from %s"
-                         % (w.m, min(w.m + 2, 2 * (w.m + 1)), s["sample_s"], ips, src)}
+        cpu = _cpu_baseline(w)
 
+    ms_step = ms_max / a.steps
     line = {
         "metric": "implicit steps/s", "value": value, "unit": "implicit steps/s", "n_gpus": world,
-        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": w.name, "grid": list(w.shape), "order": w.order, "m": w.m, "b": w.b,
-                   "tol": w.tol, "form": "mixed (FP32 Krylov, FP64 Givens/fit/restart residual)",
+                   "tol": w.tol, "dt": dt, "form": "mixed (FP32 Krylov, FP64 Givens/fit/restart residual)",
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "working set > L2 (basis 168 MB + history 688 MB), no flush"},
-        "iters_per_step": sum(i.iters for i in infos) / a.steps,
-        "cycles_per_step": sum(i.cycles for i in infos) / a.steps,
-        "rel_res_max": max(i.rel_res for i in infos),
+                   "l2": "working set > L2 (basis %.0f MB + history %.0f MB), no flush"
+                         % ((w.m + 1) * w.n * 4 / 1e6, 4 * (w.m + 1) * w.n * 4 / 1e6)},
+        "iters_per_step": summ["iters_per_step"],
+        "cycles_per_step": summ["cycles_per_step"],
+        "ms_per_iteration": ms_step / max(summ["iters_per_step"], 1e-9),
+        "candidates": summ["candidates"],
+        "rel_res_max": summ["rel_res_max"],
         "gpu_launches": int(sum(i.launches for i in infos)),
         "fp64_form": fp64, "e2e": e2e, "roofline": roofline, "kernels": kernels,
         "kernel_timing": None if prof is None else
         {"source": "CUDA events recorded by the library around every kernel class of every 4th Arnoldi "
                    "iteration, in a separate timed region of the same %d steps" % a.steps,
          "ms_per_step_with_events": prof_ms},
+        "c2": c2,
         "standalone": standalone,
         "adjoint": adj,
         "mock_test": e1,

@@ -59,6 +59,7 @@ enum { PSP_FP64 = 0, PSP_MIXED = 1 };
 #define PSP_FLAG_CANDIDATE_ACCEPTED 0x4 /* ... and adopted it */
 #define PSP_FLAG_FACTOR_FAILED 0x8      /* a fitted N had a zero pivot and was dropped */
 #define PSP_FLAG_BREAKDOWN 0x10         /* an Arnoldi breakdown ended a cycle */
+#define PSP_FLAG_FITTED 0x20            /* Algorithm 2 fitted a candidate N after this step */
 
 /* Periodic grid of Eq. 1: ndim in {1,2,3}, n[d] points on [0, length[d]), h = length/n. */
 typedef struct {
@@ -271,6 +272,18 @@ psp_status psp_fit_band_f32(psp_handle h, const float *Px, const float *Py, int6
 psp_status psp_fit_band_static(const double *Px, const double *Py, int64_t ld, int M, int64_t n, int b,
                                int intercept, double *N_band, int *singular_rows, void *cuda_stream);
 
+/*
+ * The matvec history of Algorithm 1 that the next Algorithm 2 fit would use: the valid
+ * columns of the handle's history ring (at most max_hist_cols, the most recent pairs
+ * (x, A x) of the steps since the history was last cleared), oldest first, copied to Px, Py
+ * as n x cols column-major FP64 device arrays with leading dimension ld >= n (FP32 history of
+ * the mixed form widened exactly).  *cols (host) receives the number of valid columns; with
+ * Px or Py NULL only that count is returned.  PSP_ERR_ARG if max_cols is smaller than it.
+ * Synchronous.  Diagnostics and checkpoints: with psp_get_band it is the state that
+ * decides the next step's preconditioner.
+ */
+psp_status psp_get_history(psp_handle h, double *Px, double *Py, int64_t ld, int max_cols, int *cols);
+
 /* Factor the device band N_band (half-width b) and adopt it as the preconditioner.
  * Returns PSP_ERR_NUMERIC (and keeps the previous N) if a pivot of the partitioned
  * factorisation is zero or not finite. */
@@ -294,6 +307,24 @@ psp_status psp_apply_precond_f32(psp_handle h, const float *v, float *y, int tra
  * lambda = A^{-T} g, the gradients of a loss with dL/du^{n+1} = g are lambda (u^n),
  * lambda . L u^{n+1} (dt) and dt lambda . D_t u^{n+1} (alpha_t).  Synchronous. */
 psp_status psp_apply_L(psp_handle h, int term, const double *x, double *y);
+
+/* The gradients of a loss through one implicit step with respect to dt and the term
+ * coefficients, from the adjoint state (derivative of Eq. 4, not in the paper): with
+ * u = u^{n+1} = A^{-1} u^n, A = I - dt L, L = sum_t alpha_t D_t and lambda = A^{-T} g for
+ * g = dLoss/du^{n+1},
+ *     grads_host[0]     = dLoss/d dt      = lambda . L u = sum_t alpha_t (lambda . D_t u),
+ *     grads_host[1 + t] = dLoss/d alpha_t = dt (lambda . D_t u),   t < nterms of psp_create.
+ * lam and u are FP64 device arrays of n values; the dot products are made by one kernel per
+ * 16 terms with a fixed-order reduction (deterministic).  Forward PDE handles only
+ * (PSP_ERR_ARG for an adjoint or banded handle).  Synchronous. */
+psp_status psp_adjoint_grads(psp_handle h, const double *lam, const double *u, double dt, double *grads_host);
+
+/* Adopt the preconditioner of handle src (its adopted N, or I if it has none) in handle dst,
+ * transposed (N^T) with transpose = 1: the adjoint system A^T lambda = g is preconditioned by
+ * N^T of the forward handle's N.  Both handles need the same n, b and cyclic option, on the
+ * current device.  dst's own candidate and history are kept.  PSP_ERR_NUMERIC (dst keeps its
+ * N) if the factorisation fails.  Synchronous. */
+psp_status psp_set_band_from(psp_handle dst, psp_handle src, int transpose);
 
 /* Stencil of L without dt: w_host[d*(2R+1) + (j+R)] is the weight of u(x + j h e_d) in
  * (L u)(x) for d < ndim and j in -R..R, R = *radius (host).  w_host holds 3*(2R+1)

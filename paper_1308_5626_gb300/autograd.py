@@ -8,9 +8,10 @@ forward handle's adopted N, and returns
 
     dLoss/du^n = lambda,  dLoss/d(dt) = lambda . L u^{n+1},  dLoss/d(alpha_t) = dt lambda . D_t u^{n+1}
 
-with L u^{n+1} and D_t u^{n+1} from `psp_apply_L` (the derivative of A u^{n+1} = u^n).  All
-arithmetic of the step, the adjoint solve and the stencils runs in the library's kernels;
-this module marshals arguments and forms the three dot products.
+(the derivative of A u^{n+1} = u^n) from one `psp_adjoint_grads` call on the forward
+handle, and N^T reaches the adjoint handle through `psp_set_band_from(adj, fwd, 1)`.  All
+arithmetic of the step, the adjoint solve, the transposed band and the gradient dot products
+runs in the library's kernels; this module only marshals arguments.
 
 `rollout(..., checkpoint=True)` keeps only the input of every step and recomputes the step
 during the backward pass (torch.utils.checkpoint), so a long rollout stores one vector per
@@ -71,19 +72,6 @@ class Problem:
         self._cache.clear()
 
 
-def _transpose_band(band, n: int, b: int):
-    """N^T in band storage: bandT[i][p] = band[i+p-b][2b-p] (zero outside the matrix)."""
-    import torch
-    w = 2 * b + 1
-    B = band.reshape(n, w)
-    out = torch.zeros_like(B)
-    for p in range(w):
-        off = p - b
-        lo, hi = max(0, -off), min(n, n - off)
-        out[lo:hi, p] = B[lo + off:hi + off, 2 * b - p]
-    return out.reshape(-1)
-
-
 class ImplicitStep:
     """torch.autograd.Function wrapper, built lazily so that importing the package does not
     import torch."""
@@ -122,24 +110,15 @@ def _make_function():
             problem = ctx.problem
             e = problem.entry(ctx.alphas)
             fwd, adj = e["fwd"], e["adj"]
-            n = u1.numel()
             if e["nt_stale"]:
-                band = torch.empty(n * (2 * problem.b + 1), dtype=torch.float64, device=u1.device)
-                psp.psp_get_band(fwd.handle, band)
-                psp.psp_set_band(adj.handle, _transpose_band(band, n, problem.b).contiguous())
+                psp.psp_set_band_from(adj.handle, fwd.handle, 1)
                 e["nt_stale"] = False
             lam, _ = adj.step(g.detach().to(torch.float64).contiguous(), ctx.dt, problem.tol)
-            tmp = torch.empty_like(u1)
-            psp.psp_apply_L(fwd.handle, -1, u1, tmp)
-            ddt = torch.dot(lam, tmp)
-            dal = []
-            for t in range(len(problem.kdirs)):
-                psp.psp_apply_L(fwd.handle, t, u1, tmp)
-                dal.append(ctx.dt * torch.dot(lam, tmp))
-            ddt = ddt.to(dtype=ctx.dt_like.dtype, device=ctx.dt_like.device).reshape(ctx.dt_like.shape) \
-                if torch.is_tensor(ctx.dt_like) else None
-            dalpha = torch.stack(dal).to(dtype=ctx.alpha_like.dtype, device=ctx.alpha_like.device) \
-                .reshape(ctx.alpha_like.shape)
+            grads = psp.psp_adjoint_grads(fwd.handle, lam, u1, ctx.dt, len(problem.kdirs))
+            ddt = torch.tensor(grads[0], dtype=ctx.dt_like.dtype, device=ctx.dt_like.device).reshape(
+                ctx.dt_like.shape) if torch.is_tensor(ctx.dt_like) else None
+            dalpha = torch.tensor(grads[1:], dtype=ctx.alpha_like.dtype, device=ctx.alpha_like.device).reshape(
+                ctx.alpha_like.shape)
             return lam, ddt, dalpha, None
 
     return _Step

@@ -20,6 +20,8 @@
 // two-sum, so a moment carries about 48 significant bits -- FP64-grade for sums of a few
 // hundred terms -- at FP32 instruction rates (GB300 runs FP64 at 1/64 of the FP32 rate).
 // An FP64 history is accumulated in FP64.
+#include <algorithm>
+
 #include "psp_kernels.cuh"
 
 namespace psp {
@@ -238,6 +240,34 @@ void launch_fit(int b, int intercept, int64_t n, int M, const TH *Px, const TH *
     default: break;
   }
 }
+
+// The history ring in chronological order: output column c (of `cols`) is ring column
+// (first + c) mod mmax, widened to FP64 (exact for FP32 values).
+template <typename TH>
+__global__ void __launch_bounds__(kThreads) k_history_copy(int64_t n, int cols, int first, int mmax,
+                                                           const TH *__restrict__ Px, const TH *__restrict__ Py,
+                                                           int64_t ld, double *__restrict__ ox,
+                                                           double *__restrict__ oy, int64_t ldo) {
+  const int c = blockIdx.y;
+  const int64_t src = (int64_t)((first + c) % mmax) * ld;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    ox[(int64_t)c * ldo + i] = (double)Px[src + i];
+    oy[(int64_t)c * ldo + i] = (double)Py[src + i];
+  }
+}
+
+template <typename TH>
+void launch_history_copy(int64_t n, int cols, int first, int mmax, const TH *Px, const TH *Py, int64_t ld,
+                         double *ox, double *oy, int64_t ldo, cudaStream_t s) {
+  if (cols <= 0) return;
+  const int gx = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 1024);
+  k_history_copy<TH><<<dim3((unsigned)std::max(gx, 1), (unsigned)cols), kThreads, 0, s>>>(n, cols, first, mmax, Px, Py,
+                                                                                            ld, ox, oy, ldo);
+}
+template void launch_history_copy<float>(int64_t, int, int, int, const float *, const float *, int64_t, double *,
+                                         double *, int64_t, cudaStream_t);
+template void launch_history_copy<double>(int64_t, int, int, int, const double *, const double *, int64_t,
+                                          double *, double *, int64_t, cudaStream_t);
 
 template void launch_fit<float>(int, int, int64_t, int, const float *, const float *, int64_t, double *, double *,
                                 int *, cudaStream_t, int);

@@ -121,6 +121,8 @@ struct psp_ctx {
   int t_version = -1;                // adopted_version that slot 2 (N^T) was factored for
   // per-term stencils of L (unit alpha, h^-k folded in), for psp_apply_L
   std::vector<std::pair<int, std::vector<double>>> term_w;
+  std::vector<double> term_alpha;    // alpha of each term (psp_adjoint_grads)
+  double *grad_dev = nullptr;        // kMaxTerms per-term dot products (psp_adjoint_grads)
   void *apply_mem = nullptr;
   BandSolver bs;
 
@@ -480,7 +482,7 @@ psp_status psp_destroy(psp_handle h) {
         if (e) cudaEventDestroy(e);
   void *dev[] = {h->V, h->Px, h->Py, h->Z, h->X, h->B, h->partial, h->st, h->api_st, h->moments,
                  h->band_adopted, h->band_cand, h->dev_int, h->slot_mem[0], h->slot_mem[1], h->slot_mem[2],
-                 h->band_T, h->Ab, h->Ab32, h->apply_mem,
+                 h->band_T, h->Ab, h->Ab32, h->apply_mem, h->grad_dev,
                  h->dev_un, h->dev_unp1, h->int_rhs, h->int_u1};
   for (void *p : dev)
     if (p) cudaFree(p);
@@ -553,6 +555,7 @@ psp_status psp_create(const psp_grid *grid, int order, const psp_term *terms, in
       tw[kMaxR + j] = hk * w[j + r];
     }
     h->term_w.emplace_back(tm.dir, std::move(tw));
+    h->term_alpha.push_back(tm.alpha);
     R = std::max(R, r);
   }
   if (o.adjoint) {
@@ -596,6 +599,7 @@ psp_status psp_create(const psp_grid *grid, int order, const psp_term *terms, in
   ok = ok && dalloc((void **)&h->band_cand, (size_t)n * (2 * b + 1) * 8);
   ok = ok && dalloc((void **)&h->band_T, (size_t)n * (2 * b + 1) * 8);
   ok = ok && dalloc((void **)&h->dev_int, 64);
+  ok = ok && dalloc((void **)&h->grad_dev, kMaxTerms * sizeof(double));
   if (ok) {
     h->bs.cyclic = o.cyclic != 0;
     h->bs.plan(n, b);
@@ -773,6 +777,7 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
                              : fit_into<double>(h, (const double *)h->Px, (const double *)h->Py, h->ld, hist,
                                                 h->band_cand, &singular);
     if (fs != PSP_OK) return fs;
+    flags |= PSP_FLAG_FITTED;
     if (singular) flags |= PSP_FLAG_SINGULAR_FIT;
     const int slot = (h->adopted == 0) ? 1 : 0;
     launches += 2 + 2 * (int)h->bs.levels.size() - 1;   // fit + factor/assemble per level
@@ -966,6 +971,55 @@ psp_status psp_apply_L(psp_handle h, int term, const double *x, double *y) {
   return PSP_OK;
 }
 
+psp_status psp_adjoint_grads(psp_handle h, const double *lam, const double *u, double dt, double *grads_host) {
+  if (!h || !lam || !u || !grads_host) return fail(PSP_ERR_ARG, "NULL argument");
+  if (h->geo.band_w > 0) return fail(PSP_ERR_ARG, "an explicit banded operator has no L");
+  if (h->opts.adjoint) return fail(PSP_ERR_ARG, "the gradients need the forward handle (opts.adjoint = 0)");
+  const int nt = (int)h->term_w.size();
+  std::vector<double> d(nt, 0.0);
+  for (int t0 = 0; t0 < nt; t0 += kMaxTerms) {
+    TermStencils ts{};
+    ts.nt = std::min(kMaxTerms, nt - t0);
+    ts.R = h->geo.R;
+    for (int t = 0; t < ts.nt; ++t) {
+      ts.dir[t] = h->term_w[t0 + t].first;
+      for (int j = 0; j < 2 * kMaxR + 1; ++j) ts.w[t][j] = h->term_w[t0 + t].second[j];
+    }
+    launch_term_dots(h->geo, lam, u, ts, h->partial, &h->api_st->counter[2], h->grad_dev, h->stream);
+    PSP_CUDA(cudaGetLastError());
+    PSP_CUDA(cudaMemcpyAsync(d.data() + t0, h->grad_dev, ts.nt * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    PSP_CUDA(cudaStreamSynchronize(h->stream));
+  }
+  double dl = 0.0;
+  for (int t = 0; t < nt; ++t) dl += h->term_alpha[t] * d[t];
+  grads_host[0] = dl;
+  for (int t = 0; t < nt; ++t) grads_host[1 + t] = dt * d[t];
+  return PSP_OK;
+}
+
+psp_status psp_set_band_from(psp_handle dst, psp_handle src, int transpose) {
+  if (!dst || !src) return fail(PSP_ERR_ARG, "NULL argument");
+  if (dst->geo.n != src->geo.n || dst->b != src->b || dst->bs.cyclic != src->bs.cyclic)
+    return fail(PSP_ERR_ARG, "the handles need the same n, band half-width and cyclic option");
+  const int64_t n = src->geo.n;
+  const int W = 2 * src->b + 1;
+  PSP_CUDA(cudaStreamSynchronize(src->stream));
+  if (src->adopted < 0) {   // N = I (its own transpose)
+    std::vector<double> id((size_t)n * W, 0.0);
+    for (int64_t i = 0; i < n; ++i) id[(size_t)i * W + src->b] = 1.0;
+    PSP_CUDA(cudaMemcpy(dst->band_T, id.data(), id.size() * 8, cudaMemcpyHostToDevice));
+  } else if (transpose) {
+    launch_transpose_band(src->band_adopted, dst->band_T, n, src->b, dst->stream, dst->bs.cyclic);
+    PSP_CUDA(cudaGetLastError());
+  } else {
+    PSP_CUDA(cudaMemcpyAsync(dst->band_T, src->band_adopted, (size_t)n * W * 8, cudaMemcpyDeviceToDevice,
+                             dst->stream));
+  }
+  // band_T is dst's scratch for its own N^T: the adoption below bumps adopted_version, so
+  // that N^T is made afresh before dst's next transposed solve
+  return psp_set_band(dst, dst->band_T);
+}
+
 psp_status psp_fit_band(psp_handle h, const double *Px, const double *Py, int64_t ld, int M, double *N_band,
                         int *singular_rows) {
   if (!h || !Px || !Py || !N_band) return fail(PSP_ERR_ARG, "NULL argument");
@@ -978,6 +1032,27 @@ psp_status psp_fit_band_f32(psp_handle h, const float *Px, const float *Py, int6
   if (!h || !Px || !Py || !N_band) return fail(PSP_ERR_ARG, "NULL argument");
   if (M < 1 || ld < h->geo.n) return fail(PSP_ERR_ARG, "need M >= 1 and ld >= n");
   return fit_into<float>(h, Px, Py, ld, M, N_band, singular_rows);
+}
+
+psp_status psp_get_history(psp_handle h, double *Px, double *Py, int64_t ld, int max_cols, int *cols) {
+  if (!h || !cols) return fail(PSP_ERR_ARG, "NULL argument");
+  PSP_CUDA(cudaMemcpyAsync(h->int_host + 4, &h->st->hist_count, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  PSP_CUDA(cudaStreamSynchronize(h->stream));
+  const int count = h->int_host[4];
+  const int c = std::min(count, h->mmax);
+  *cols = c;
+  if (!Px || !Py) return PSP_OK;   // query only
+  if (ld < h->geo.n || max_cols < c) return fail(PSP_ERR_ARG, "need ld >= n and max_cols >= the valid columns");
+  const int first = ((count - c) % h->mmax + h->mmax) % h->mmax;
+  if (h->mixed)
+    launch_history_copy<float>(h->geo.n, c, first, h->mmax, (const float *)h->Px, (const float *)h->Py, h->ld, Px, Py,
+                               ld, h->stream);
+  else
+    launch_history_copy<double>(h->geo.n, c, first, h->mmax, (const double *)h->Px, (const double *)h->Py, h->ld, Px,
+                                Py, ld, h->stream);
+  PSP_CUDA(cudaGetLastError());
+  PSP_CUDA(cudaStreamSynchronize(h->stream));
+  return PSP_OK;
 }
 
 psp_status psp_set_band(psp_handle h, const double *N_band) {

@@ -88,6 +88,19 @@ struct TileMatvec {
   int nx, ny, nz, ndim, R;
 };
 
+// Unit-coefficient 1D stencils of the operator's terms (for the adjoint gradients).
+constexpr int kMaxTerms = 16;
+struct TermStencils {
+  int nt;                              // terms (<= kMaxTerms)
+  int R;                               // widest radius
+  int dir[kMaxTerms];
+  double w[kMaxTerms][2 * kMaxR + 1];  // w[t][kMaxR + j]: weight of u(x + j h e_dir)
+};
+// out[t] = lambda . (D_t u), t < ts.nt; per-CTA sums in partial (rows of kMaxCta), one
+// last-block counter
+void launch_term_dots(const Geometry &g, const double *lam, const double *u, const TermStencils &ts, double *partial,
+                      unsigned int *counter, double *out, cudaStream_t s);
+
 // stencil.cu
 template <typename TI, typename TO, typename TC>
 void launch_stencil(const Geometry &g, InRef<TI> x, OutRef<TO> y, const DevState *st, const int *active,
@@ -132,6 +145,10 @@ void launch_bi_omega(int64_t n, const double *V, int64_t ldv, InRef<double> t, D
 void launch_bi_xr(int j, int m, int64_t n, double *X, double *V, int64_t ldv, InRef<double> p, InRef<double> sx,
                   InRef<double> t, DevState *st, double *partial, cudaStream_t s);
 
+// band_fit.cu: the history ring in chronological order, widened to FP64 (psp_get_history)
+template <typename TH>
+void launch_history_copy(int64_t n, int cols, int first, int mmax, const TH *Px, const TH *Py, int64_t ld,
+                         double *ox, double *oy, int64_t ldo, cudaStream_t s);
 // band_fit.cu (cyclic: every row regresses on its neighbours modulo n)
 template <typename TH>
 void launch_fit(int b, int intercept, int64_t n, int M, const TH *Px, const TH *Py, int64_t ld,

@@ -205,6 +205,18 @@ def c4_instance(i: int, e_range: Tuple[int, int] = (10, 18)) -> Workload:
     order = int(rng.choice([2, 4, 6, 8]))
     b = int(rng.integers(1, 5))
     cfl = float(rng.uniform(1.0, 20.0))
+    return _c4_build(rng, "c4_%d" % i, two_d, e, order, b, cfl, 4 + i)
+
+
+def c4_spec(two_d: bool, e: int, order: int, b: int, cfl: float, seed: int) -> Workload:
+    """A batched-workload instance with its size, order, band and CFL chosen by the caller
+    (the coefficients and u^0 drawn as in c4_instance from the given seed): the parity tests
+    pick instances that span the batch's ranges."""
+    rng = np.random.default_rng(seed)
+    return _c4_build(rng, "c4s%d" % seed, bool(two_d), int(e), int(order), int(b), float(cfl), seed)
+
+
+def _c4_build(rng, tag, two_d, e, order, b, cfl, seed) -> Workload:
     if two_d:
         nx, ny = 2 ** ((e + 1) // 2), 2 ** (e // 2)
         a = rng.uniform(0.5, 2.0, 2)
@@ -218,8 +230,8 @@ def c4_instance(i: int, e_range: Tuple[int, int] = (10, 18)) -> Workload:
         terms = [Term(1, 0, 1.0), Term(2, 0, 0.01)]
         u0 = sines_1d(n, 16, rng)
         shape, dt = (n,), cfl * (TWO_PI / n)
-    return Workload("c4_%d_%s" % (i, "x".join(str(s) for s in shape)), shape, order, terms, b=b, m=30,
-                    steps=10, tol=1e-8, dt=dt, rho_dt=None, u0=u0, seed=4 + i)
+    return Workload("%s_%s" % (tag, "x".join(str(s) for s in shape)), shape, order, terms, b=b, m=30,
+                    steps=10, tol=1e-8, dt=dt, rho_dt=None, u0=u0, seed=seed)
 
 
 WORKLOADS = {"c1": c1, "c2": c2, "c3": c3}

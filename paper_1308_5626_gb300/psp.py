@@ -25,6 +25,7 @@ PSP_FLAG_CANDIDATE_TRIED = 0x2
 PSP_FLAG_CANDIDATE_ACCEPTED = 0x4
 PSP_FLAG_FACTOR_FAILED = 0x8
 PSP_FLAG_BREAKDOWN = 0x10
+PSP_FLAG_FITTED = 0x20
 
 STATUS_NAMES = {0: "PSP_OK", 1: "PSP_ERR_ARG", 2: "PSP_ERR_CUDA", 3: "PSP_ERR_OOM", 4: "PSP_ERR_NOCONV",
                 5: "PSP_ERR_NUMERIC", 6: "PSP_ERR_DEVICE"}
@@ -79,7 +80,10 @@ _SIGS = {
                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)],
     "psp_fit_band": [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_int)],
     "psp_fit_band_f32": [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_int)],
+    "psp_get_history": [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "psp_set_band": [_VP, _VP],
+    "psp_set_band_from": [_VP, _VP, ctypes.c_int],
+    "psp_adjoint_grads": [_VP, _VP, _VP, ctypes.c_double, _VP],
     "psp_get_band": [_VP, _VP],
     "psp_apply_precond": [_VP, _VP, _VP, ctypes.c_int],
     "psp_apply_precond_f32": [_VP, _VP, _VP, ctypes.c_int],
@@ -265,8 +269,33 @@ def psp_fit_band_static(Px, Py, N_band, b: int, intercept: int = 1, ld: Optional
     return sing.value if want_count else None
 
 
+def psp_get_history(h, n: int):
+    """The handle's matvec history, oldest pair first: (Px, Py) float64 CUDA tensors shaped
+    (cols, n) (row c = history column c)."""
+    import torch
+    c = ctypes.c_int(0)
+    _check(lib().psp_get_history(h, None, None, int(n), 0, ctypes.byref(c)), "psp_get_history")
+    Px = torch.empty((max(c.value, 1), n), dtype=torch.float64, device="cuda")
+    Py = torch.empty_like(Px)
+    _check(lib().psp_get_history(h, _ptr(Px), _ptr(Py), int(n), c.value, ctypes.byref(c)), "psp_get_history")
+    return Px[:c.value], Py[:c.value]
+
+
 def psp_set_band(h, N_band) -> None:
     _check(lib().psp_set_band(h, _ptr(N_band)), "psp_set_band")
+
+
+def psp_set_band_from(dst, src, transpose: int = 1) -> None:
+    """Adopt src's preconditioner (transposed with transpose=1) in dst."""
+    _check(lib().psp_set_band_from(dst, src, int(transpose)), "psp_set_band_from")
+
+
+def psp_adjoint_grads(h, lam, u, dt: float, nterms: int):
+    """[dLoss/d dt, dLoss/d alpha_0, ...] of one implicit step from the adjoint state lam and
+    u^{n+1} (FP64 device tensors); a list of 1 + nterms floats."""
+    g = (ctypes.c_double * (1 + int(nterms)))()
+    _check(lib().psp_adjoint_grads(h, _ptr(lam), _ptr(u), float(dt), g), "psp_adjoint_grads")
+    return list(g)
 
 
 def psp_get_band(h, N_band) -> None:

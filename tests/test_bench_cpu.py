@@ -67,13 +67,21 @@ def test_clock_summary():
     assert s["sm_mhz"] == 2000 and s["sm_max_mhz"] == 2070 and s["reasons"] == ["sw_power_cap"]
 
 
-def test_reference_arm_line_on_a_small_grid():
+@pytest.mark.parametrize("args", [["--n3", "32"], ["--workload", "c2", "--nx", "64"]], ids=["c3", "c2"])
+def test_reference_arm_line_on_a_small_grid(args):
+    """The reference arm's line: the oracle timed on K Arnoldi iterations; its bookkeeping
+    (steps x ms_per_step) is the timed work actually run, and value is the implied
+    implicit-step rate, which the sample's description states."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0", "--nx", "64"], capture_output=True, text=True, env=env, timeout=300)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "3",
+                        "--warmup", "1"] + args, capture_output=True, text=True, env=env, timeout=300)
     assert r.returncode == 0, r.stderr
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["unit"] == "implicit steps/s" and line["higher_is_better"] is True
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+    assert line["steps"] == 3 and line["step_unit"] == "oracle Arnoldi iteration"
+    # the implied step is longer than one sampled iteration
+    assert line["implied_ms_per_implicit_step"] > line["ms_per_step"]
+    assert line["value"] == pytest.approx(1000.0 / line["implied_ms_per_implicit_step"])

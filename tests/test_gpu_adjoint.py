@@ -171,3 +171,71 @@ def adjoint_target(op, u0, dt, steps):
     for _ in range(steps):
         u = exact.solve_fourier(op, u, dt)
     return u
+
+
+@pytest.mark.parametrize("shape,order,terms", [
+    ((300,), 4, [(1, 0, 1.0), (2, 0, 0.01)]),
+    ((40, 36), 6, [(1, 0, 0.8), (1, 1, -1.3), (2, 0, 1e-3), (2, 1, 2e-3)]),
+    ((16, 12, 20), 8, [(2, 0, 0.7), (2, 1, 1.1), (2, 2, 1.9), (4, 0, -1e-3), (4, 1, -1e-3), (4, 2, -2e-3)]),
+])
+def test_adjoint_grads_match_the_oracle_terms(dev, shape, order, terms):
+    """psp_adjoint_grads: dLoss/d dt = lambda . L u and dLoss/d alpha_t = dt lambda . D_t u,
+    against the oracle's stencils (each term applied alone with unit alpha), 1e-12 of the
+    products' rounding scale sum|lambda| |D_t| |u|."""
+    from paper_1308_5626_gb300 import psp
+    op = Operator(shape, order, terms)
+    rng = np.random.default_rng(11)
+    lam, u = rng.standard_normal(op.n), rng.standard_normal(op.n)
+    dt = 0.3 * min(op.h)
+    s = psp.Solver(shape, order, terms, 2, 8)
+    g = psp.psp_adjoint_grads(s.handle, t64(lam, dev), t64(u, dev), dt, len(terms))
+    s.close()
+    d = []
+    for (k, dd, a) in terms:
+        d.append(float(lam @ Operator(shape, order, [(k, dd, 1.0)]).apply_L(u)))
+    scale = [float(np.abs(lam) @ np.abs(Operator(shape, order, [(k, dd, 1.0)]).apply_L(u))) + 1.0
+             for (k, dd, a) in terms]
+    for t, (k, dd, a) in enumerate(terms):
+        assert abs(g[1 + t] - dt * d[t]) <= 1e-12 * dt * scale[t] * 100
+    ref0 = sum(a * dv for (k, dd, a), dv in zip(terms, d))
+    assert abs(g[0] - ref0) <= 1e-12 * sum(abs(a) * sc for (k, dd, a), sc in zip(terms, scale)) * 100
+
+
+def test_adjoint_grads_refuse_adjoint_and_banded_handles(dev):
+    import torch
+    from paper_1308_5626_gb300 import psp
+    x = torch.zeros(64, dtype=torch.float64, device=dev)
+    Ab = t64(inputs.dense_to_band(np.eye(64) * 2.0, 1), dev).reshape(-1)
+    for s in (psp.Solver((64,), 2, [(2, 0, 1.0)], 2, 8, adjoint=1), psp.Solver.banded(Ab, 1, 1, 8)):
+        with pytest.raises(psp.PspError) as e:
+            psp.psp_adjoint_grads(s.handle, x, x, 0.1, 1)
+        assert e.value.status == psp.PSP_ERR_ARG
+        s.close()
+
+
+@pytest.mark.parametrize("cyclic", [0, 1])
+def test_set_band_from_hands_over_the_transpose(dev, cyclic):
+    """psp_set_band_from(dst, src, 1): dst adopts N^T of src's adopted N (the oracle's
+    transpose_band of the same band, cyclic too); with transpose = 0, N itself; from a handle
+    with no adopted N, the identity."""
+    import torch
+    from paper_1308_5626_gb300 import psp
+    n, b = 257, 3
+    band = inputs.random_cyclic_band(n, b, seed=5) if cyclic else inputs.random_band(n, b, seed=5)
+    src = psp.Solver((n,), 4, [(2, 0, 1.0)], b, 8, cyclic=cyclic)
+    dst = psp.Solver((n,), 4, [(2, 0, 1.0)], b, 8, cyclic=cyclic, adjoint=1)
+    out = torch.empty((n, 2 * b + 1), dtype=torch.float64, device=dev)
+    psp.psp_set_band_from(dst.handle, src.handle, 1)
+    psp.psp_get_band(dst.handle, out)
+    ident = np.zeros((n, 2 * b + 1))
+    ident[:, b] = 1.0
+    np.testing.assert_array_equal(out.cpu().numpy(), ident)
+    psp.psp_set_band(src.handle, t64(band, dev))
+    psp.psp_set_band_from(dst.handle, src.handle, 1)
+    psp.psp_get_band(dst.handle, out)
+    np.testing.assert_array_equal(out.cpu().numpy(), banded.transpose_band(band, b, cyclic=bool(cyclic)))
+    psp.psp_set_band_from(dst.handle, src.handle, 0)
+    psp.psp_get_band(dst.handle, out)
+    np.testing.assert_array_equal(out.cpu().numpy(), band)
+    src.close()
+    dst.close()

@@ -13,7 +13,7 @@
 import numpy as np
 import pytest
 
-from gpu_common import rel, t64, torch_dev
+from gpu_common import elementwise_bound, inv_inf_norm, rel, rel_max, t64, torch_dev
 from oracle import exact
 from oracle.operator import Operator
 from oracle.step import Stepper
@@ -228,6 +228,7 @@ def test_full_size_2d_step(dev, precision):
     bound = exact.condition_number(op, w.dt) * 2 * tol if precision == 0 else 1e-8
     assert info.status == 0
     assert rel(out.cpu().numpy(), ref) <= bound
+    assert rel_max(out.cpu().numpy(), ref) <= elementwise_bound(inv_inf_norm(op, w.dt), tol, w.u0, ref)
     s.close()
 
 
@@ -243,6 +244,7 @@ def test_full_size_3d_step(dev):
     ref = exact.solve_fourier(op, w.u0, dt)
     assert info.status == 0
     assert rel(out.cpu().numpy(), ref) <= 1e-8
+    assert rel_max(out.cpu().numpy(), ref) <= elementwise_bound(inv_inf_norm(op, dt), 1e-10, w.u0, ref)
     s.close()
 
 
