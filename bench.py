@@ -186,10 +186,10 @@ def _traffic_for(kernel: str, workload: str):
         return None
     with open(p) as fh:
         d = json.load(fh)
-    if d.get("source_hash") != _kernel_source_hash():
+    wl = d.get("kernels", {}).get(workload, {})
+    if wl.get("source_hash", d.get("source_hash")) != _kernel_source_hash():
         return None
-    ent = d.get("kernels", {}).get(workload, {}).get(kernel)
-    return ent
+    return wl.get(kernel)
 
 
 def _dist():
