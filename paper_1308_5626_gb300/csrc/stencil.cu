@@ -410,17 +410,20 @@ static int stencil_grid(int64_t n) {
   }
 
 // 3D vectorised stencil with z-marching (2.5D blocking): a CTA owns a tile of kTileXV
-// x-vectors by kTileY rows and walks a range of planes.  Each thread keeps the 2R+1 planes
-// of its own vector in a register queue (the z terms), loaded R planes ahead.  The tile of
-// each plane, with an x halo of whole vectors and a y halo of R rows on each side (no
-// corners), is staged in a ring of kStage3 shared-memory slots by 16-byte asynchronous
-// copies (cp.async) issued kAhead3 planes ahead, so the halo latency overlaps the work of
-// the planes before it.  A point is read from HBM about once; the halos come from L2.
-// Needs nx / W and ny to be multiples of the tile (the periodic wrap is then tile-exact).
+// x-vectors by kTileY rows and walks a range of planes.  Each thread keeps the planes
+// z-R .. z+R of its own vector in a register queue (the z terms), loaded kPre3 planes ahead
+// of their first use.  The plane loop is unrolled by the queue length, so the queue index of
+// every plane is a compile-time constant and nothing is moved between planes.  The tile of
+// the current plane, with an x halo of whole vectors and a y halo of R rows on each side (no
+// corners: the stencil is a cross), sits in one of two shared-memory slots: each thread
+// writes its own vector there from the queue, and the halo vectors of the next plane are
+// copied by 16-byte asynchronous copies (cp.async, every thread taking the same one or two
+// halo positions on every plane) while the current plane is computed.  One barrier per plane.
+// A point is read from HBM about once; the halos come from L2.  Needs nx / W and ny to be
+// multiples of the tile (the periodic wrap is then tile-exact).
 constexpr int kTileXV = 32;
 constexpr int kTileY = 8;
-constexpr int kAhead3 = 4;
-constexpr int kStage3 = kAhead3 + 1;
+constexpr int kPre3 = 2;   // planes of look-ahead of the queue loads
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
@@ -436,6 +439,28 @@ __host__ __device__ constexpr int tile3d_slot_vecs() {
   return (kTileY + 2 * R) * (kTileXV + 2 * ((R + SVec<T>::W - 1) / SVec<T>::W));
 }
 
+// Coefficients of the three directions: in registers for FP32 (the kernel is then bound by
+// memory and instruction issue), read from shared memory for FP64 (bound by the FP64 pipe).
+template <typename T, int R, bool REG>
+struct Coef3;
+template <typename T, int R>
+struct Coef3<T, R, true> {
+  T c[3][2 * R + 1];
+  __device__ __forceinline__ void load(const T (*s)[2 * R + 1]) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int j = 0; j < 2 * R + 1; ++j) c[d][j] = s[d][j];
+  }
+  __device__ __forceinline__ T operator()(int d, int j) const { return c[d][j]; }
+};
+template <typename T, int R>
+struct Coef3<T, R, false> {
+  const T (*c)[2 * R + 1];
+  __device__ __forceinline__ void load(const T (*s)[2 * R + 1]) { c = s; }
+  __device__ __forceinline__ T operator()(int d, int j) const { return c[d][j]; }
+};
+
 template <typename T, int R>
 __global__ void __launch_bounds__(kTileXV * kTileY, 2) k_stencil_3d(InRef<T> xref, OutRef<T> yref, OutRef<T> xcopy,
                                                                    const double *scale, const DevState *__restrict__ st,
@@ -445,6 +470,9 @@ __global__ void __launch_bounds__(kTileXV * kTileY, 2) k_stencil_3d(InRef<T> xre
   constexpr int NH = (R + W - 1) / W;
   constexpr int SX = kTileXV + 2 * NH;
   constexpr int SLOT = tile3d_slot_vecs<T, R>();
+  constexpr int QL = 2 * R + 1 + kPre3;               // queue length: planes z-R .. z+R+kPre3
+  constexpr int NHALO = 2 * R * kTileXV + 2 * NH * kTileY;
+  constexpr int NT = kTileXV * kTileY;
   if (active && *active == 0) return;
   extern __shared__ __align__(16) unsigned char smem3[];
   VT *ring = reinterpret_cast<VT *>(smem3);
@@ -461,98 +489,109 @@ __global__ void __launch_bounds__(kTileXV * kTileY, 2) k_stencil_3d(InRef<T> xre
   const int64_t plane = (int64_t)nx * ny;
   const int tx = threadIdx.x % kTileXV, ty = threadIdx.x / kTileXV;
   const int xv0 = blockIdx.x * kTileXV, y0 = blockIdx.y * kTileY;
-  const int xv = xv0 + tx, iy = y0 + ty;
+  const int64_t own = (int64_t)(y0 + ty) * nx + (int64_t)(xv0 + tx) * W;   // offset inside a plane
   const int z0 = blockIdx.z * tz;
   const int z1 = min(z0 + tz, nz);
   auto wrapz = [&](int z) { return z < 0 ? z + nz : (z >= nz ? z - nz : z); };
-  auto gptr = [&](int vx, int vy, int vz) -> const VT * {
-    return reinterpret_cast<const VT *>(x + (int64_t)vz * plane + (int64_t)vy * nx + (int64_t)vx * W);
-  };
-  // the copies of one plane's tile into ring slot `slot`: centre rows (own vector), x halo
-  // of the centre rows, y halo rows (centre columns only)
-  auto stage = [&](int z, int slot) {
-    VT *t = ring + slot * SLOT;
-    cp_async16(t + (ty + R) * SX + tx + NH, gptr(xv, iy, z));
-    if (tx < NH) {
-      int v = xv0 - NH + tx;
-      v += (v < 0) ? nxv : 0;
-      cp_async16(t + (ty + R) * SX + tx, gptr(v, iy, z));
-    } else if (tx >= kTileXV - NH) {
-      const int u = tx - (kTileXV - NH);
-      int v = xv0 + kTileXV + u;
-      v -= (v >= nxv) ? nxv : 0;
-      cp_async16(t + (ty + R) * SX + kTileXV + NH + u, gptr(v, iy, z));
-    }
-    for (int e = threadIdx.x; e < 2 * R * kTileXV; e += blockDim.x) {
+  auto ldv = [&](int z) { return __ldg(reinterpret_cast<const VT *>(x + (int64_t)wrapz(z) * plane + own)); };
+  // this thread's halo positions (the same on every plane): e = threadIdx.x and e + NT of
+  // the list [y halo rows (2R x kTileXV), x halo vectors of the tile rows (kTileY x 2NH)]
+  int h_s[2];
+  int64_t h_g[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int e = threadIdx.x + k * NT;
+    h_s[k] = -1;
+    h_g[k] = 0;
+    if (e < 2 * R * kTileXV) {
       const int hr = e / kTileXV, hx = e % kTileXV;
       int row = (hr < R) ? y0 - R + hr : y0 + kTileY + (hr - R);
       row += (row < 0) ? ny : 0;
       row -= (row >= ny) ? ny : 0;
-      cp_async16(t + ((hr < R) ? hr : kTileY + hr) * SX + hx + NH, gptr(xv0 + hx, row, z));
+      h_s[k] = ((hr < R) ? hr : kTileY + hr) * SX + hx + NH;
+      h_g[k] = (int64_t)row * nx + (int64_t)(xv0 + hx) * W;
+    } else if (e < NHALO) {
+      const int f = e - 2 * R * kTileXV;
+      const int r = f / (2 * NH), c = f % (2 * NH);
+      int v = (c < NH) ? xv0 - NH + c : xv0 + kTileXV + (c - NH);
+      v += (v < 0) ? nxv : 0;
+      v -= (v >= nxv) ? nxv : 0;
+      h_s[k] = (r + R) * SX + ((c < NH) ? c : kTileXV + c);
+      h_g[k] = (int64_t)(y0 + r) * nx + (int64_t)v * W;
     }
-  };
-  VT q[2 * R + 1];
-#pragma unroll
-  for (int k = 0; k < 2 * R; ++k) q[k] = *gptr(xv, iy, wrapz(z0 - R + k));
-#pragma unroll
-  for (int a = 0; a < kAhead3; ++a) {
-    if (z0 + a < z1) stage(z0 + a, a);
-    cp_async_commit();   // one group per plane slot, empty past the range
   }
-  for (int z = z0; z < z1; ++z) {
-    q[2 * R] = *gptr(xv, iy, wrapz(z + R));
-    {
-      const int za = z + kAhead3;
-      if (za < z1) stage(za, (za - z0) % kStage3);
+  auto stage_halo = [&](int z, VT *slot) {
+    const T *pz = x + (int64_t)wrapz(z) * plane;
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+      if (h_s[k] >= 0) cp_async16(slot + h_s[k], pz + h_g[k]);
+  };
+  // queue: plane z0 - R + i in q[i] for i < 2R + kPre3; the halos of plane z0 into slot 0
+  VT q[QL];
+#pragma unroll
+  for (int i = 0; i < 2 * R + kPre3; ++i) q[i] = (z0 - R + i < z1 + R) ? ldv(z0 - R + i) : VT{};
+  stage_halo(z0, ring);
+  cp_async_commit();
+  __syncthreads();   // s_c
+  Coef3<T, R, sizeof(T) == 4> c;
+  c.load(s_c);
+  for (int zb = z0; zb < z1; zb += QL) {
+#pragma unroll
+    for (int u = 0; u < QL; ++u) {
+      const int z = zb + u;
+      if (z >= z1) break;
+      // plane z + k sits in q[(u + k + R) % QL]; the load kPre3 planes ahead takes the slot
+      // of plane z - R - 1, which the previous plane used last
+      if (z + R + kPre3 < z1 + R) q[(u + 2 * R + kPre3) % QL] = ldv(z + R + kPre3);
+      VT *slot = ring + ((z - z0) & 1) * SLOT;
+      slot[(ty + R) * SX + tx + NH] = q[(u + R) % QL];
+      cp_async_wait<0>();   // this thread's halo copies of plane z have landed
+      __syncthreads();      // ... and every thread's, with the centre vectors
+      if (z + 1 < z1) stage_halo(z + 1, ring + ((z + 1 - z0) & 1) * SLOT);
       cp_async_commit();
+      T win[(2 * NH + 1) * W];
+#pragma unroll
+      for (int hh = 0; hh <= 2 * NH; ++hh) {
+        const VT v = slot[(ty + R) * SX + tx + hh];
+        const T *ve = reinterpret_cast<const T *>(&v);
+#pragma unroll
+        for (int i = 0; i < W; ++i) win[hh * W + i] = ve[i];
+      }
+      T acc[W];
+#pragma unroll
+      for (int i = 0; i < W; ++i) {
+        T a = c(0, R) * win[NH * W + i];
+#pragma unroll
+        for (int j = 1; j <= R; ++j) a += c(0, R - j) * win[NH * W + i - j] + c(0, R + j) * win[NH * W + i + j];
+        acc[i] = a;
+      }
+#pragma unroll
+      for (int j = 1; j <= R; ++j) {
+        const VT tm = slot[(ty + R - j) * SX + tx + NH], tp = slot[(ty + R + j) * SX + tx + NH];
+        const T *me = reinterpret_cast<const T *>(&tm), *pe = reinterpret_cast<const T *>(&tp);
+#pragma unroll
+        for (int i = 0; i < W; ++i) acc[i] += c(1, R - j) * me[i] + c(1, R + j) * pe[i];
+      }
+#pragma unroll
+      for (int j = 1; j <= R; ++j) {
+        const T *me = reinterpret_cast<const T *>(&q[(u + R - j + QL) % QL]);
+        const T *pe = reinterpret_cast<const T *>(&q[(u + R + j) % QL]);
+#pragma unroll
+        for (int i = 0; i < W; ++i) acc[i] += c(2, R - j) * me[i] + c(2, R + j) * pe[i];
+      }
+      VT out;
+      T *oe = reinterpret_cast<T *>(&out);
+#pragma unroll
+      for (int i = 0; i < W; ++i) oe[i] = sc * acc[i];
+      const int64_t o = (int64_t)z * plane + own;
+      *reinterpret_cast<VT *>(y + o) = out;
+      if (xc) {
+        const T *ce = reinterpret_cast<const T *>(&q[(u + R) % QL]);
+#pragma unroll
+        for (int i = 0; i < W; ++i) oe[i] = sc * ce[i];
+        *reinterpret_cast<VT *>(xc + o) = out;
+      }
     }
-    cp_async_wait<kAhead3>();   // this thread's copies of plane z have landed
-    __syncthreads();            // ... and every other thread's
-    const VT *t = ring + ((z - z0) % kStage3) * SLOT;
-    T win[(2 * NH + 1) * W];
-#pragma unroll
-    for (int h = 0; h <= 2 * NH; ++h) {
-      const VT v = t[(ty + R) * SX + tx + h];
-      const T *ve = reinterpret_cast<const T *>(&v);
-#pragma unroll
-      for (int i = 0; i < W; ++i) win[h * W + i] = ve[i];
-    }
-    T acc[W];
-#pragma unroll
-    for (int i = 0; i < W; ++i) {
-      T a = s_c[0][R] * win[NH * W + i];
-#pragma unroll
-      for (int j = 1; j <= R; ++j) a += s_c[0][R - j] * win[NH * W + i - j] + s_c[0][R + j] * win[NH * W + i + j];
-      acc[i] = a;
-    }
-#pragma unroll
-    for (int j = 1; j <= R; ++j) {
-      const VT tm = t[(ty + R - j) * SX + tx + NH], tp = t[(ty + R + j) * SX + tx + NH];
-      const T *me = reinterpret_cast<const T *>(&tm), *pe = reinterpret_cast<const T *>(&tp);
-#pragma unroll
-      for (int i = 0; i < W; ++i) acc[i] += s_c[1][R - j] * me[i] + s_c[1][R + j] * pe[i];
-    }
-#pragma unroll
-    for (int j = 1; j <= R; ++j) {
-      const T *me = reinterpret_cast<const T *>(&q[R - j]), *pe = reinterpret_cast<const T *>(&q[R + j]);
-#pragma unroll
-      for (int i = 0; i < W; ++i) acc[i] += s_c[2][R - j] * me[i] + s_c[2][R + j] * pe[i];
-    }
-    VT out;
-    T *oe = reinterpret_cast<T *>(&out);
-#pragma unroll
-    for (int i = 0; i < W; ++i) oe[i] = sc * acc[i];
-    const int64_t o = (int64_t)z * plane + (int64_t)iy * nx + (int64_t)xv * W;
-    *reinterpret_cast<VT *>(y + o) = out;
-    if (xc) {
-      const T *ce = reinterpret_cast<const T *>(&q[R]);
-#pragma unroll
-      for (int i = 0; i < W; ++i) oe[i] = sc * ce[i];
-      *reinterpret_cast<VT *>(xc + o) = out;
-    }
-#pragma unroll
-    for (int k = 0; k < 2 * R; ++k) q[k] = q[k + 1];
-    __syncthreads();   // the slot of plane z is refilled by the next step's copies
   }
   cp_async_wait<0>();
 }
@@ -564,7 +603,7 @@ static int tile3d_tz(int gx, int gy, int nz) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int bytes = kStage3 * tile3d_slot_vecs<T, R>() * 16;
+    const int bytes = 2 * tile3d_slot_vecs<T, R>() * 16;
     cudaFuncSetAttribute(k_stencil_3d<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_stencil_3d<T, R>, kTileXV * kTileY, bytes);
     return std::max(1, sms) * std::max(1, per);
@@ -640,7 +679,7 @@ void launch_stencil(const Geometry &g, InRef<TI> x, OutRef<TO> y, const DevState
       PSP_DISPATCH_R(g.R, {
         const int tz = tile3d_tz<TI, RR>(gx, gy, g.nz);
         const dim3 grid3(gx, gy, (g.nz + tz - 1) / tz);
-        const int bytes = kStage3 * tile3d_slot_vecs<TI, RR>() * 16;
+        const int bytes = 2 * tile3d_slot_vecs<TI, RR>() * 16;
         k_stencil_3d<TI, RR><<<grid3, kTileXV * kTileY, bytes, s>>>(x, y, xcopy, scale, st, g.nx, g.ny, g.nz, tz, active);
       });
       return;
