@@ -457,13 +457,14 @@ def _cyclic_line(device, steps: int = 10):
     import torch
     from paper_1308_5626_gb300 import inputs, psp
     rows = []
-    for n in (1024, 1 << 20):
+    for n, onchip in ((1024, 1), (1024, 0), (1 << 20, 0)):
         w = inputs.c1(n)
         for prec in (psp.PSP_FP64, psp.PSP_MIXED):
             for cyc in (0, 1):
                 stream = torch.cuda.Stream(device=device)
                 with torch.cuda.stream(stream):
-                    s = psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=prec, stream=stream, cyclic=cyc)
+                    s = psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=prec, stream=stream, cyclic=cyc,
+                                   onchip=onchip)
                     u = torch.tensor(w.u0, dtype=torch.float64, device=device)
                     out = torch.empty_like(u)
                     warm_its = []
@@ -483,7 +484,8 @@ def _cyclic_line(device, steps: int = 10):
                     torch.cuda.synchronize(device)
                     ms = e0.elapsed_time(e1) / steps
                     s.close()
-                rows.append({"n": n, "form": "fp64" if prec == psp.PSP_FP64 else "mixed",
+                rows.append({"n": n, "path": "onchip" if onchip else "cycle graphs",
+                             "form": "fp64" if prec == psp.PSP_FP64 else "mixed",
                              "band": "cyclic" if cyc else "paper boundary rows",
                              "warmup_iters": warm_its, "iters_per_step": its / steps, "ms_per_step": ms,
                              "steps_per_s": 1e3 / ms})
@@ -563,7 +565,7 @@ def _bicgstab_line(w, device, steps: int = 3):
     return {"workload": w.name, "form": "fp64", "rows": rows}
 
 
-def _batch_line(device, count: int, steps: int, nthreads: int):
+def _batch_line(device, count: int, steps: int, nthreads: int, onchip: int = 1):
     """The batched workload: `count` independent instances (inputs.c4_instance: 1D/2D, n from
     2^10 to 2^18, orders 2-8, b 1-4, CFL 1-20, mixed form, tol 1e-8), each on its own stream,
     stepped together by psp_step_batch with `nthreads` host threads.  One untimed step
@@ -577,7 +579,8 @@ def _batch_line(device, count: int, steps: int, nthreads: int):
     solvers, us, outs = [], [], []
     for w in ws:
         s = torch.cuda.Stream(device=device)
-        solvers.append(psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=psp.PSP_MIXED, stream=s))
+        solvers.append(psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=psp.PSP_MIXED, stream=s,
+                                  onchip=onchip))
         us.append(torch.tensor(w.u0, dtype=torch.float64, device=device))
         outs.append(torch.empty(w.n, dtype=torch.float64, device=device))
     t_create = time.perf_counter() - t0
@@ -597,13 +600,18 @@ def _batch_line(device, count: int, steps: int, nthreads: int):
     for s in solvers:
         s.close()
     per.sort()
-    return {"instances": count, "steps": steps, "host_threads": nthreads,
+    its = sum(i.iters for i in infos)
+    return {"instances": count, "steps": steps, "host_threads": nthreads, "onchip": onchip,
             "unknowns_total": int(sum(w.n for w in ws)),
             "value": count * steps / wall, "unit": "implicit steps/s (all instances)",
             "p50_ms": 1e3 * per[len(per) // 2], "p99_ms": 1e3 * per[min(len(per) - 1, int(0.99 * len(per)))],
+            "iters_per_instance_step": its / count,
             "create_s": t_create,
-            "note": "concurrent per-instance cycle graphs on per-instance streams, driven by psp_step_batch's "
-                    "host threads; host wall clock"}
+            "note": ("the cycles of all instances in shared persistent launches (one CTA per system); per-instance "
+                     "time = its device time in those launches (globaltimer) + the host time of its fit and "
+                     "factorisation; aggregate from the host wall clock") if onchip else
+                    ("concurrent per-instance cycle graphs on per-instance streams, driven by psp_step_batch's "
+                     "host threads; host wall clock")}
 
 
 def _e2e(w, precision, steps, device, dt):
@@ -914,7 +922,8 @@ def main():
         e1 = _e1_line(device)
     batch = None
     if a.batch > 0 and rank == 0:
-        batch = _batch_line(device, a.batch, a.batch_steps, a.batch_threads)
+        batch = _batch_line(device, a.batch, a.batch_steps, a.batch_threads, onchip=1)
+        batch["cycle_graphs"] = _batch_line(device, a.batch, a.batch_steps, a.batch_threads, onchip=0)
     cyclic = None
     if not a.no_cyclic and rank == 0:
         cyclic = _cyclic_line(device)

@@ -114,6 +114,15 @@ typedef struct {
                         the fit, the acceptance rule and the preconditioner are unchanged.
                         PSP_FP64 and m >= 3 only (else PSP_ERR_ARG); the profiling mode
                         times GMRES cycles only.  Not in the paper. */
+  int onchip;        /* -1 (default): the on-chip path for systems of at most 32768 unknowns;
+                        1: for systems of at most 262144 unknowns; 0: never.  On the on-chip
+                        path one CTA runs every restart cycle of a step (restart, band solve,
+                        matvec, Gram-Schmidt, Givens, update) with the cycle loop on the device,
+                        so the host waits once per step instead of once per cycle, and
+                        psp_step_batch runs all its handles' cycles in shared launches (one
+                        CTA per system).  Its Gram-Schmidt is classical applied twice (CGS2).
+                        GMRES only (BiCGSTAB handles take the cycle graphs); the profiling mode
+                        does not time it. */
 } psp_opts;
 
 typedef struct {

@@ -14,12 +14,14 @@
 #include <cstring>
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <chrono>
 #include <string>
 #include <thread>
 #include <vector>
 
 #include "band_solve.cuh"
+#include "onchip.cuh"
 
 namespace {
 
@@ -154,6 +156,13 @@ struct psp_ctx {
   cudaEvent_t wait_ev = nullptr;
   // integrators (psp_step_bdf2, psp_step_sdirk2): right-hand side and first-stage vectors
   double *int_rhs = nullptr, *int_u1 = nullptr;
+  int hist_count_host = 0;   // history columns at the end of the last step (0 after a clear)
+  // on-chip path (one CTA runs all cycles of a step): its descriptor and result
+  bool onchip = false;
+  int oc_threads = 256;        // CTA size of this system's on-chip launches
+  int oc_ctas_per_sm = 2;      // resident CTAs per SM of a batched launch
+  OnChipDesc *oc_desc = nullptr, *oc_desc_host = nullptr;
+  OnChipResult *oc_res = nullptr, *oc_res_host = nullptr;
 };
 
 namespace {
@@ -424,6 +433,7 @@ psp_status psp_default_opts(psp_opts *o) {
   o->adjoint = 0;
   o->cyclic = 0;
   o->solver = PSP_SOLVER_GMRES;
+  o->onchip = -1;
   return PSP_OK;
 }
 
@@ -483,9 +493,11 @@ psp_status psp_destroy(psp_handle h) {
   void *dev[] = {h->V, h->Px, h->Py, h->Z, h->X, h->B, h->partial, h->st, h->api_st, h->moments,
                  h->band_adopted, h->band_cand, h->dev_int, h->slot_mem[0], h->slot_mem[1], h->slot_mem[2],
                  h->band_T, h->Ab, h->Ab32, h->apply_mem, h->grad_dev,
-                 h->dev_un, h->dev_unp1, h->int_rhs, h->int_u1};
+                 h->dev_un, h->dev_unp1, h->int_rhs, h->int_u1, h->oc_desc, h->oc_res};
   for (void *p : dev)
     if (p) cudaFree(p);
+  if (h->oc_desc_host) cudaFreeHost(h->oc_desc_host);
+  if (h->oc_res_host) cudaFreeHost(h->oc_res_host);
   if (h->sum_host) cudaFreeHost(h->sum_host);
   if (h->st_host) cudaFreeHost(h->st_host);
   if (h->int_host) cudaFreeHost(h->int_host);
@@ -574,6 +586,11 @@ psp_status psp_create(const psp_grid *grid, int order, const psp_term *terms, in
   h->geo.n = n;
   h->geo.R = R;
   h->fused = o.fuse_matvec != 0 && fused_matvec_ok(h->geo, h->mixed ? 4 : 8);
+  // the on-chip path: one CTA runs all the cycles of a step (GMRES only); by default for the
+  // systems small enough that launch latency, not bandwidth, bounds the cycle graphs
+  h->onchip = o.solver == PSP_SOLVER_GMRES && n <= kOnChipMaxN &&
+              (o.onchip > 0 || (o.onchip < 0 && n <= kOnChipAutoN));
+  h->oc_threads = onchip_threads_for(n);
   h->ld = round_up(n, 512);   // every column starts on a 2 KB boundary (16-byte vector loads)
   h->mmax = o.max_hist_cols > 0 ? o.max_hist_cols : 2 * (m + 1);
   if (h->mmax < m + 1) h->mmax = m + 1;
@@ -600,6 +617,10 @@ psp_status psp_create(const psp_grid *grid, int order, const psp_term *terms, in
   ok = ok && dalloc((void **)&h->band_T, (size_t)n * (2 * b + 1) * 8);
   ok = ok && dalloc((void **)&h->dev_int, 64);
   ok = ok && dalloc((void **)&h->grad_dev, kMaxTerms * sizeof(double));
+  ok = ok && dalloc((void **)&h->oc_desc, sizeof(OnChipDesc));
+  ok = ok && dalloc((void **)&h->oc_res, sizeof(OnChipResult));
+  ok = ok && cudaMallocHost((void **)&h->oc_desc_host, sizeof(OnChipDesc)) == cudaSuccess;
+  ok = ok && cudaMallocHost((void **)&h->oc_res_host, sizeof(OnChipResult)) == cudaSuccess;
   if (ok) {
     h->bs.cyclic = o.cyclic != 0;
     h->bs.plan(n, b);
@@ -633,20 +654,50 @@ psp_status psp_create(const psp_grid *grid, int order, const psp_term *terms, in
   return PSP_OK;
 }
 
-psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, double tol, psp_step_info *info) {
-  if (!h || !u_n || !u_np1) return fail(PSP_ERR_ARG, "NULL argument");
-  if (!(tol > 0.0) || !std::isfinite(dt)) return fail(PSP_ERR_ARG, "tol must be > 0 and dt finite");
-  const int64_t n = h->geo.n;
-  if ((u_n < u_np1 + n) && (u_np1 < u_n + n)) return fail(PSP_ERR_ARG, "u_n and u_np1 overlap");
-  cudaStream_t s = h->stream;
+}  // extern "C"
 
-  // parameters of this step
+namespace {
+
+// One launch's worth of restart cycles (one cycle graph, or an on-chip launch of up to
+// max_cycles cycles) as the step's host logic sees it.
+struct Segment {
+  int cycles = 0, iters = 0, k_last = 0, status = 0, error = 0;
+  double beta_first = 0.0, beta_last = 0.0, R_last = 0.0, bnorm = 0.0;
+};
+
+// The host state of one psp_step between its segments.
+struct StepRun {
+  const double *u_n = nullptr;
+  double *u_np1 = nullptr;
+  double dt = 0.0, tol = 0.0;
+  int iters = 0, cycles = 0, flags = 0, launches = 0, c = 0;
+  bool converged = false, numeric = false, done = false;
+  double last_R = 0.0, bnorm = 0.0;
+  bool try_cand = false;
+  int cur = -1;
+  double trial_beta = -1.0, trial_R = 0.0, main_beta = -1.0, main_R = 0.0;
+  int trial_iters = 0, main_iters = 0;
+  int hist_before_trial = 0, prev_adopted = -1;
+  bool adopted_now = false;
+  psp_status status = PSP_OK;
+};
+
+// Parameters of the step, the back-off bookkeeping and the choice of the first cycle's N.
+psp_status step_begin(psp_ctx *h, StepRun &r, const double *u_n, double *u_np1, double dt, double tol) {
+  const int64_t n = h->geo.n;
+  cudaStream_t s = h->stream;
+  r = StepRun{};
+  r.u_n = u_n;
+  r.u_np1 = u_np1;
+  r.dt = dt;
+  r.tol = tol;
   if (!(h->hist_dt == dt)) {   // A changed: the history no longer describes it
     h->hist_dt = dt;
     h->cand = -1;
     h->rate_ref = -1.0;
     h->wait = 0;
     h->wait_len = 1;
+    h->hist_count_host = 0;
     PSP_CUDA(cudaMemsetAsync(&h->st->hist_count, 0, sizeof(int), s));
   }
   set_coef(h, dt, h->st_host->coef);
@@ -657,113 +708,128 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
   PSP_CUDA(cudaMemcpyAsync(&h->st->first, &h->st_host->first, sizeof(int), cudaMemcpyHostToDevice, s));
   PSP_CUDA(cudaMemcpyAsync(h->B, u_n, n * 8, cudaMemcpyDeviceToDevice, s));
   PSP_CUDA(cudaMemcpyAsync(h->X, u_n, n * 8, cudaMemcpyDeviceToDevice, s));
-
-  int iters = 0, cycles = 0, flags = 0, launches = 0;
-  bool converged = false, numeric = false;
-  double last_R = 0.0, bnorm = 0.0;
   // the first cycle may try the candidate (acceptance rule: see the design notes)
-  const bool try_cand = (h->cand >= 0 && h->wait == 0);
-  if (!try_cand && h->wait > 0) h->wait -= 1;
-  int cur = try_cand ? h->cand : h->adopted;
-  double trial_beta = -1.0, trial_R = 0.0, main_beta = -1.0, main_R = 0.0;
-  int trial_iters = 0, main_iters = 0;
-  int hist_before_trial = 0;
-  const int prev_adopted = h->adopted;
-  bool adopted_now = false;   // the candidate was adopted in this step (band copied at its end)
-  if (try_cand) {   // the history length to restore if the trial cycle breaks down
-    PSP_CUDA(cudaMemcpyAsync(h->int_host + 3, &h->st->hist_count, sizeof(int), cudaMemcpyDeviceToHost, s));
-    PSP_CUDA(host_wait(h, s));
-    hist_before_trial = h->int_host[3];
+  r.try_cand = (h->cand >= 0 && h->wait == 0);
+  if (!r.try_cand && h->wait > 0) h->wait -= 1;
+  r.cur = r.try_cand ? h->cand : h->adopted;
+  r.prev_adopted = h->adopted;
+  r.hist_before_trial = h->hist_count_host;   // the history length to restore if the trial breaks
+  return PSP_OK;
+}
+
+// Cycles the next segment may run: the candidate's trial cycle alone, else the rest.
+int step_next_cycles(const psp_ctx *h, const StepRun &r) {
+  return (r.c == 0 && r.try_cand) ? 1 : std::max(1, h->opts.max_restarts - r.c);
+}
+
+// Which cycle graph / factor slot the next segment uses (0: N = I, 1 + slot).
+int step_which(const StepRun &r) { return r.cur < 0 ? 0 : r.cur + 1; }
+
+// The host logic after a segment (Algorithm 1's restart loop with the acceptance rule).
+psp_status step_after_segment(psp_ctx *h, StepRun &r, const Segment &sg, int launches) {
+  const int64_t n = h->geo.n;
+  cudaStream_t s = h->stream;
+  const bool trial_now = (r.c == 0 && r.try_cand);
+  r.cycles += sg.cycles;
+  r.iters += sg.iters;
+  r.launches += launches;
+  r.c += sg.cycles;
+  r.bnorm = sg.bnorm;
+  if (sg.error) {
+    r.done = true;
+    return fail(PSP_ERR_DEVICE, "device error flag " + std::to_string(sg.error) +
+                                    " (a bounded wait expired or a launch was misconfigured)");
   }
-  for (int c = 0; c < h->opts.max_restarts; ++c) {
-    const int which = cur < 0 ? 0 : cur + 1;
-    psp_status ps = ensure_graph(h, which);
-    if (ps != PSP_OK) return ps;
-    PSP_CUDA(cudaGraphLaunch(h->graph[which], s));
+  const bool broken = (sg.status & kStNumeric) || !std::isfinite(sg.R_last) || !std::isfinite(sg.beta_last);
+  if (broken && (trial_now || r.adopted_now)) {
+    // the fresh candidate broke a cycle of this step (in the mixed form an ill-conditioned
+    // N can overflow the FP32 solve): it is rejected like a slow one and the step restarts
+    // from u^n with the previous N -- X back to u^n, the pairs of the cycles run with the
+    // candidate dropped from the history
+    r.flags |= PSP_FLAG_CANDIDATE_TRIED;
+    r.flags &= ~PSP_FLAG_CANDIDATE_ACCEPTED;
+    PSP_CUDA(cudaMemcpyAsync(h->X, r.u_n, n * 8, cudaMemcpyDeviceToDevice, s));
+    h->int_host[3] = r.hist_before_trial;
+    PSP_CUDA(cudaMemcpyAsync(&h->st->hist_count, h->int_host + 3, sizeof(int), cudaMemcpyHostToDevice, s));
     PSP_CUDA(host_wait(h, s));
-    const CycleSummary sm = *h->sum_host;
-    cycles += 1;
-    iters += sm.k_end;
-    launches += h->graph_kernels[which];
-    if (h->profiling && h->opts.solver == PSP_SOLVER_GMRES) accumulate_profile(h, which, sm.k_end);
-    bnorm = sm.bnorm;
-    if (sm.error) return fail(PSP_ERR_DEVICE, "device error flag " + std::to_string(sm.error) +
-                                                  " (a bounded wait expired or a launch was misconfigured)");
-    const bool broken = (sm.status & kStNumeric) || !std::isfinite(sm.R_end) || !std::isfinite(sm.beta);
-    if (broken && ((c == 0 && try_cand) || adopted_now)) {
-      // the fresh candidate broke a cycle of this step (in the mixed form an ill-conditioned
-      // N can overflow the FP32 solve): it is rejected like a slow one and the step restarts
-      // from u^n with the previous N -- X back to u^n, the pairs of the cycles run with the
-      // candidate dropped from the history
-      flags |= PSP_FLAG_CANDIDATE_TRIED;
-      flags &= ~PSP_FLAG_CANDIDATE_ACCEPTED;
-      PSP_CUDA(cudaMemcpyAsync(h->X, u_n, n * 8, cudaMemcpyDeviceToDevice, s));
-      h->int_host[3] = hist_before_trial;
-      PSP_CUDA(cudaMemcpyAsync(&h->st->hist_count, h->int_host + 3, sizeof(int), cudaMemcpyHostToDevice, s));
-      PSP_CUDA(host_wait(h, s));
-      if (adopted_now) {
-        h->adopted = prev_adopted;
-        h->adopted_version += 1;
-        adopted_now = false;
-        h->wait_len = std::max(h->wait_len, 1);
-      }
+    if (r.adopted_now) {
+      h->adopted = r.prev_adopted;
+      h->adopted_version += 1;
+      r.adopted_now = false;
+      h->wait_len = std::max(h->wait_len, 1);
+    }
+    h->wait = h->wait_len;
+    h->wait_len *= 2;
+    r.cur = h->adopted;
+    h->cand = -1;
+    r.main_beta = -1.0;
+    r.main_iters = 0;
+    if (r.c == 0) r.c = 1;   // the trial's cycle counts against max_restarts
+    r.try_cand = false;
+    r.done = r.c >= h->opts.max_restarts;
+    return PSP_OK;
+  }
+  if (sg.status & kStNumeric) {
+    r.numeric = true;
+    r.done = true;
+    return PSP_OK;
+  }
+  if (sg.status & kStBreakdown) r.flags |= PSP_FLAG_BREAKDOWN;
+  // residual at the end of the segment: the FP64 true residual of a converged restart
+  // (mixed form) or the Givens estimate R(k_end)
+  const double R_now = (h->mixed && sg.k_last == 0) ? sg.beta_last : sg.R_last;
+  r.last_R = h->mixed ? sg.beta_last : sg.R_last;
+  if (sg.status & kStConverged) r.converged = true;
+  if (trial_now) {
+    r.trial_beta = sg.beta_first;
+    r.trial_iters = sg.iters;
+    r.trial_R = R_now;
+    r.flags |= PSP_FLAG_CANDIDATE_TRIED;
+    const double r1 = rate_of(sg.R_last, sg.beta_first, sg.iters);
+    const bool cycle_done = r.converged || (sg.R_last <= r.tol * sg.bnorm);
+    if (!h->opts.accept_rule || cycle_done || h->rate_ref < 0.0 || r1 <= h->rate_ref) {
+      h->adopted = h->cand;
+      h->adopted_version += 1;
+      h->wait_len = 1;
+      r.flags |= PSP_FLAG_CANDIDATE_ACCEPTED;
+      r.adopted_now = true;
+    } else {
       h->wait = h->wait_len;
       h->wait_len *= 2;
-      cur = h->adopted;
-      h->cand = -1;
-      main_beta = -1.0;
-      main_iters = 0;
-      continue;
     }
-    if (sm.status & kStNumeric) { numeric = true; break; }
-    if (sm.status & kStBreakdown) flags |= PSP_FLAG_BREAKDOWN;
-    // residual at the end of the cycle: the FP64 true residual of a converged restart
-    // (mixed form) or the Givens estimate R(k_end)
-    const double R_now = (h->mixed && sm.k_end == 0) ? sm.beta : sm.R_end;
-    last_R = h->mixed ? sm.beta : sm.R_end;
-    if (sm.status & kStConverged) converged = true;
-    if (c == 0 && try_cand) {
-      trial_beta = sm.beta;
-      trial_iters = sm.k_end;
-      trial_R = R_now;
-      flags |= PSP_FLAG_CANDIDATE_TRIED;
-      const double r1 = rate_of(sm.R_end, sm.beta, sm.k_end);
-      const bool cycle_done = converged || (sm.R_end <= tol * sm.bnorm);
-      if (!h->opts.accept_rule || cycle_done || h->rate_ref < 0.0 || r1 <= h->rate_ref) {
-        h->adopted = h->cand;
-        h->adopted_version += 1;
-        h->wait_len = 1;
-        flags |= PSP_FLAG_CANDIDATE_ACCEPTED;
-        adopted_now = true;
-      } else {
-        h->wait = h->wait_len;
-        h->wait_len *= 2;
-      }
-      cur = h->adopted;
-      h->cand = -1;
-    } else {
-      if (main_beta < 0.0) main_beta = sm.beta;
-      main_iters += sm.k_end;
-      main_R = R_now;
-    }
-    if (converged) break;
+    r.cur = h->adopted;
+    h->cand = -1;
+  } else {
+    if (r.main_beta < 0.0) r.main_beta = sg.beta_first;
+    r.main_iters += sg.iters;
+    r.main_R = R_now;
   }
-  if (main_iters > 0 && main_beta > 0.0) h->rate_ref = rate_of(main_R, main_beta, main_iters);
-  else if (trial_iters > 0 && trial_beta > 0.0) h->rate_ref = rate_of(trial_R, trial_beta, trial_iters);
+  r.done = r.converged || r.c >= h->opts.max_restarts;
+  return PSP_OK;
+}
 
-  if (adopted_now)
+// After the last segment: the reference rate, the adopted band, u^{n+1}, and the
+// Algorithm 2 fit of the next candidate (when the next step tries one).
+psp_status step_finish(psp_ctx *h, StepRun &r, psp_step_info *info) {
+  const int64_t n = h->geo.n;
+  cudaStream_t s = h->stream;
+  if (r.main_iters > 0 && r.main_beta > 0.0) h->rate_ref = rate_of(r.main_R, r.main_beta, r.main_iters);
+  else if (r.trial_iters > 0 && r.trial_beta > 0.0) h->rate_ref = rate_of(r.trial_R, r.trial_beta, r.trial_iters);
+
+  if (r.adopted_now)
     PSP_CUDA(cudaMemcpyAsync(h->band_adopted, h->band_cand, (size_t)n * (2 * h->b + 1) * 8,
                              cudaMemcpyDeviceToDevice, s));
   psp_status result = PSP_OK;
-  if (numeric) result = fail(PSP_ERR_NUMERIC, "non-finite residual");
-  else if (!converged) result = fail(PSP_ERR_NOCONV, "max_restarts reached");
-  PSP_CUDA(cudaMemcpyAsync(u_np1, h->X, n * 8, cudaMemcpyDeviceToDevice, s));
+  if (r.numeric) result = fail(PSP_ERR_NUMERIC, "non-finite residual");
+  else if (!r.converged) result = fail(PSP_ERR_NOCONV, "max_restarts reached");
+  PSP_CUDA(cudaMemcpyAsync(r.u_np1, h->X, n * 8, cudaMemcpyDeviceToDevice, s));
 
   // progressive fit of the candidate for the next step (Algorithm 2)
   int hist = 0;
   {
     PSP_CUDA(cudaMemcpyAsync(h->int_host + 2, &h->st->hist_count, sizeof(int), cudaMemcpyDeviceToHost, s));
     PSP_CUDA(host_wait(h, s));
+    h->hist_count_host = h->int_host[2];
     hist = std::min(h->int_host[2], h->mmax);
   }
   const int need = 2 * h->b + (h->opts.intercept ? 2 : 1);
@@ -771,33 +837,295 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
   // a fit is only worth making when the next step tries it: while the acceptance rule's
   // back-off still runs (wait > 0) the next step keeps the adopted N, and the step after
   // it fits afresh from the longer history, so the skipped fit could never be used
-  if (!numeric && hist >= need && h->wait == 0) {
+  if (!r.numeric && hist >= need && h->wait == 0) {
     psp_status fs = h->mixed ? fit_into<float>(h, (const float *)h->Px, (const float *)h->Py, h->ld, hist,
                                                h->band_cand, &singular)
                              : fit_into<double>(h, (const double *)h->Px, (const double *)h->Py, h->ld, hist,
                                                 h->band_cand, &singular);
     if (fs != PSP_OK) return fs;
-    flags |= PSP_FLAG_FITTED;
-    if (singular) flags |= PSP_FLAG_SINGULAR_FIT;
+    r.flags |= PSP_FLAG_FITTED;
+    if (singular) r.flags |= PSP_FLAG_SINGULAR_FIT;
     const int slot = (h->adopted == 0) ? 1 : 0;
-    launches += 2 + 2 * (int)h->bs.levels.size() - 1;   // fit + factor/assemble per level
+    r.launches += 2 + 2 * (int)h->bs.levels.size() - 1;   // fit + factor/assemble per level
     psp_status f2 = factor_into(h, slot, h->band_cand);
     if (f2 == PSP_OK) h->cand = slot;
-    else if (f2 == PSP_ERR_NUMERIC) { flags |= PSP_FLAG_FACTOR_FAILED; h->cand = -1; }
+    else if (f2 == PSP_ERR_NUMERIC) { r.flags |= PSP_FLAG_FACTOR_FAILED; h->cand = -1; }
     else return f2;
   }
   h->last_singular = singular;
   if (info) {
-    info->iters = iters;
-    info->cycles = cycles;
+    info->iters = r.iters;
+    info->cycles = r.cycles;
     info->status = result;
-    info->flags = flags;
-    info->rel_res = bnorm > 0.0 ? last_R / bnorm : 0.0;
+    info->flags = r.flags;
+    info->rel_res = r.bnorm > 0.0 ? r.last_R / r.bnorm : 0.0;
     info->hist_cols = hist;
     info->singular_rows = singular;
-    info->launches = launches;
+    info->launches = r.launches;
   }
   return result;
+}
+
+// The on-chip descriptor of handle h for a segment with slot `which` and max_cycles cycles.
+OnChipDesc onchip_desc(psp_ctx *h, int which, int max_cycles, OnChipResult *res_dev) {
+  OnChipDesc d{};
+  const Geometry &g = h->geo;
+  d.ndim = g.ndim;
+  d.nx = g.nx;
+  d.ny = g.ny;
+  d.nz = g.nz;
+  d.R = g.R;
+  d.n = (int)g.n;
+  d.band_w = g.band_w;
+  d.b = h->b;
+  d.Ab = g.Ab;
+  d.Ab32 = g.Ab32;
+  d.X = h->X;
+  d.Bv = h->B;
+  d.V = h->V;
+  d.Px = h->Px;
+  d.Py = h->Py;
+  d.Z = h->Z;
+  d.ld = h->ld;
+  d.m = h->m;
+  d.mmax = h->mmax;
+  d.st = h->st;
+  const int slot = which - 1;
+  if (slot >= 0) {
+    d.lev = h->mixed ? (const void *)h->bs.dev_app32[slot] : (const void *)h->bs.dev_app64[slot];
+    d.nlev = (int)h->bs.levels.size();
+    d.cyclic = h->bs.cyclic ? 1 : 0;
+    if (d.cyclic) {
+      const BandSolver::Slot &S = h->bs.slots[slot];
+      d.smwZ = h->mixed ? (const void *)S.Z32 : (const void *)S.Z64;
+      d.smwK = h->mixed ? (const void *)S.K32 : (const void *)S.K64;
+      d.tmp = h->bs.cyc_y;
+    }
+  }
+  d.max_cycles = max_cycles;
+  d.res = res_dev;
+  return d;
+}
+
+Segment segment_of(const OnChipResult &o) {
+  Segment sg;
+  sg.cycles = o.cycles;
+  sg.iters = o.iters;
+  sg.k_last = o.k_last;
+  sg.status = o.status;
+  sg.error = o.error;
+  sg.beta_first = o.first_beta;
+  sg.beta_last = o.last_beta;
+  sg.R_last = o.last_R;
+  sg.bnorm = o.bnorm;
+  return sg;
+}
+
+// One segment of handle h's step with slot `which`: one captured cycle graph, or an on-chip
+// launch of up to max_cycles cycles.  Returns the kernels launched in *launches.
+psp_status run_segment(psp_ctx *h, int which, int max_cycles, Segment *out, int *launches) {
+  cudaStream_t s = h->stream;
+  if (h->onchip) {
+    *h->oc_desc_host = onchip_desc(h, which, max_cycles, h->oc_res);
+    PSP_CUDA(cudaMemcpyAsync(h->oc_desc, h->oc_desc_host, sizeof(OnChipDesc), cudaMemcpyHostToDevice, s));
+    if (h->mixed) launch_onchip<float>(h->oc_desc, 1, h->dev_int + 8, h->oc_threads, 1, s);
+    else launch_onchip<double>(h->oc_desc, 1, h->dev_int + 8, h->oc_threads, 1, s);
+    PSP_CUDA(cudaGetLastError());
+    PSP_CUDA(cudaMemcpyAsync(h->oc_res_host, h->oc_res, sizeof(OnChipResult), cudaMemcpyDeviceToHost, s));
+    PSP_CUDA(host_wait(h, s));
+    *out = segment_of(*h->oc_res_host);
+    *launches = 1;
+    return PSP_OK;
+  }
+  psp_status ps = ensure_graph(h, which);
+  if (ps != PSP_OK) return ps;
+  PSP_CUDA(cudaGraphLaunch(h->graph[which], s));
+  PSP_CUDA(host_wait(h, s));
+  const CycleSummary sm = *h->sum_host;
+  if (h->profiling && h->opts.solver == PSP_SOLVER_GMRES) accumulate_profile(h, which, sm.k_end);
+  Segment sg;
+  sg.cycles = 1;
+  sg.iters = sm.k_end;
+  sg.k_last = sm.k_end;
+  sg.status = sm.status;
+  sg.error = sm.error;
+  sg.beta_first = sg.beta_last = sm.beta;
+  sg.R_last = sm.R_end;
+  sg.bnorm = sm.bnorm;
+  *out = sg;
+  *launches = h->graph_kernels[which];
+  return PSP_OK;
+}
+
+// Device and pinned buffers of the batched on-chip launches, made on the first batched call
+// (and grown when a larger batch comes); one set per process, used under a mutex.
+struct BatchBuffers {
+  int cap = 0;
+  OnChipDesc *desc = nullptr, *desc_host = nullptr;
+  OnChipResult *res = nullptr, *res_host = nullptr;
+  int *counter = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  int sms = 0;
+};
+std::mutex g_batch_mu;
+BatchBuffers g_batch;
+
+psp_status batch_buffers(int count) {
+  BatchBuffers &b = g_batch;
+  if (!b.stream) {
+    PSP_CUDA(cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking));
+    PSP_CUDA(cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming));
+    PSP_CUDA(cudaMalloc((void **)&b.counter, 256));
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b.sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  if (count > b.cap) {
+    if (b.desc) cudaFree(b.desc);
+    if (b.res) cudaFree(b.res);
+    if (b.desc_host) cudaFreeHost(b.desc_host);
+    if (b.res_host) cudaFreeHost(b.res_host);
+    b.desc = nullptr; b.res = nullptr; b.desc_host = nullptr; b.res_host = nullptr; b.cap = 0;
+    const int cap = std::max(count, 64);
+    if (cudaMalloc((void **)&b.desc, cap * sizeof(OnChipDesc)) != cudaSuccess ||
+        cudaMalloc((void **)&b.res, cap * sizeof(OnChipResult)) != cudaSuccess ||
+        cudaMallocHost((void **)&b.desc_host, cap * sizeof(OnChipDesc)) != cudaSuccess ||
+        cudaMallocHost((void **)&b.res_host, cap * sizeof(OnChipResult)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PSP_ERR_OOM, "batch buffers");
+    }
+    b.cap = cap;
+  }
+  return PSP_OK;
+}
+
+// The batched form on the on-chip path: the segments of every instance's step run in shared
+// persistent launches (one CTA per system at a time, systems taken largest first from a
+// counter), the host logic between them per instance; the fits and factorisations that end
+// the steps run from nthreads host threads, each instance on its own stream.
+psp_status step_batch_onchip(psp_ctx **hs, int count, const double *const *u_n, double *const *u_np1, const double *dt,
+                             double tol, int nthreads, psp_step_info *infos, double *seconds, psp_status *statuses) {
+  std::lock_guard<std::mutex> lock(g_batch_mu);
+  psp_status bs = batch_buffers(count);
+  if (bs != PSP_OK) return bs;
+  BatchBuffers &B = g_batch;
+  const auto t0 = std::chrono::steady_clock::now();
+  std::vector<StepRun> runs(count);
+  std::vector<double> dev_ns(count, 0.0);
+  for (int i = 0; i < count; ++i) {
+    psp_ctx *h = hs[i];
+    const int64_t n = h->geo.n;
+    if ((u_n[i] < u_np1[i] + n) && (u_np1[i] < u_n[i] + n)) return fail(PSP_ERR_ARG, "u_n and u_np1 overlap");
+    if (!std::isfinite(dt[i])) return fail(PSP_ERR_ARG, "dt must be finite");
+    psp_status st = step_begin(h, runs[i], u_n[i], u_np1[i], dt[i], tol);
+    if (st != PSP_OK) return st;
+    PSP_CUDA(cudaEventRecord(B.ev, h->stream));
+    PSP_CUDA(cudaStreamWaitEvent(B.stream, B.ev, 0));
+  }
+  // largest systems first: they bound the launch, the small ones fill the SMs behind them
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hs[a]->geo.n > hs[b]->geo.n; });
+  const bool mixed = hs[0]->mixed;
+  for (int round = 0;; ++round) {
+    // systems still stepping, grouped by CTA size (a system's CTA size is fixed at create, so
+    // its arithmetic, reductions included, is the same batched or alone); one persistent
+    // launch per group, back to back on the batch stream
+    std::vector<int> live;
+    for (int i : order)
+      if (!runs[i].done) live.push_back(i);
+    if (live.empty()) break;
+    std::stable_sort(live.begin(), live.end(), [&](int a, int b) { return hs[a]->oc_threads > hs[b]->oc_threads; });
+    for (size_t k = 0; k < live.size(); ++k) {
+      const int i = live[k];
+      B.desc_host[k] = onchip_desc(hs[i], step_which(runs[i]), step_next_cycles(hs[i], runs[i]), B.res + k);
+    }
+    const int cnt = (int)live.size();
+    PSP_CUDA(cudaMemcpyAsync(B.desc, B.desc_host, cnt * sizeof(OnChipDesc), cudaMemcpyHostToDevice, B.stream));
+    for (int k0 = 0, grp = 0; k0 < cnt; ++grp) {
+      const int threads = hs[live[k0]]->oc_threads;
+      int k1 = k0;
+      while (k1 < cnt && hs[live[k1]]->oc_threads == threads) ++k1;
+      const int per_sm = std::max(1, hs[live[k0]]->oc_ctas_per_sm);
+      const int grid = std::min(k1 - k0, std::max(1, B.sms) * per_sm);
+      if (mixed) launch_onchip<float>(B.desc + k0, k1 - k0, B.counter + grp, threads, grid, B.stream);
+      else launch_onchip<double>(B.desc + k0, k1 - k0, B.counter + grp, threads, grid, B.stream);
+      PSP_CUDA(cudaGetLastError());
+      k0 = k1;
+    }
+    PSP_CUDA(cudaMemcpyAsync(B.res_host, B.res, cnt * sizeof(OnChipResult), cudaMemcpyDeviceToHost, B.stream));
+    PSP_CUDA(cudaStreamSynchronize(B.stream));
+    for (int k = 0; k < cnt; ++k) {
+      const int i = live[k];
+      dev_ns[i] += (double)(B.res_host[k].t_end - B.res_host[k].t_begin);
+      psp_status st = step_after_segment(hs[i], runs[i], segment_of(B.res_host[k]), 1);
+      if (st != PSP_OK) {
+        runs[i].done = true;
+        runs[i].status = st;
+      }
+    }
+  }
+  const double t_cycles = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  (void)t_cycles;
+  // the ends of the steps (u^{n+1}, fits, factorisations) from a pool of host threads
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int nt = std::max(1, std::min(nthreads < 1 ? 1 : nthreads, count));
+  std::atomic<int> next{0};
+  std::atomic<int> first_err{(int)PSP_OK};
+  std::atomic<bool> noconv{false};
+  auto work = [&]() {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= count) break;
+      const auto tf = std::chrono::steady_clock::now();
+      psp_step_info info{};
+      psp_status st = runs[i].status;
+      if (st == PSP_OK) st = step_finish(hs[i], runs[i], &info);
+      const double fin = std::chrono::duration<double>(std::chrono::steady_clock::now() - tf).count();
+      if (infos) infos[i] = info;
+      if (seconds) seconds[i] = dev_ns[i] * 1e-9 + fin;
+      if (statuses) statuses[i] = st;
+      if (st == PSP_ERR_NOCONV) {
+        noconv = true;
+      } else if (st != PSP_OK) {
+        int expected = (int)PSP_OK;
+        first_err.compare_exchange_strong(expected, (int)st);
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+  work();
+  for (auto &th : pool) th.join();
+  if (first_err.load() != (int)PSP_OK)
+    return fail((psp_status)first_err.load(), "at least one instance of the batch failed (see statuses)");
+  return noconv.load() ? fail(PSP_ERR_NOCONV, "an instance reached max_restarts") : PSP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, double tol, psp_step_info *info) {
+  if (!h || !u_n || !u_np1) return fail(PSP_ERR_ARG, "NULL argument");
+  if (!(tol > 0.0) || !std::isfinite(dt)) return fail(PSP_ERR_ARG, "tol must be > 0 and dt finite");
+  const int64_t n = h->geo.n;
+  if ((u_n < u_np1 + n) && (u_np1 < u_n + n)) return fail(PSP_ERR_ARG, "u_n and u_np1 overlap");
+  StepRun r;
+  psp_status st = step_begin(h, r, u_n, u_np1, dt, tol);
+  if (st != PSP_OK) return st;
+  while (!r.done) {
+    Segment sg;
+    int launches = 0;
+    st = run_segment(h, step_which(r), step_next_cycles(h, r), &sg, &launches);
+    if (st != PSP_OK) return st;
+    st = step_after_segment(h, r, sg, launches);
+    if (st != PSP_OK) return st;
+  }
+  return step_finish(h, r, info);
 }
 
 psp_status psp_step_batch(psp_handle *hs, int count, const double *const *u_n, double *const *u_np1,
@@ -813,6 +1141,10 @@ psp_status psp_step_batch(psp_handle *hs, int count, const double *const *u_n, d
     if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
       return fail(PSP_ERR_ARG, "a handle appears twice in the batch");
   }
+  if (count == 0) return PSP_OK;
+  bool all_onchip = true;
+  for (int i = 0; i < count; ++i) all_onchip = all_onchip && hs[i]->onchip && hs[i]->mixed == hs[0]->mixed;
+  if (all_onchip) return step_batch_onchip(hs, count, u_n, u_np1, dt, tol, nthreads, infos, seconds, statuses);
   int dev = 0;
   cudaGetDevice(&dev);
   const int nt = std::max(1, std::min(nthreads < 1 ? 1 : nthreads, std::max(count, 1)));
@@ -1172,6 +1504,7 @@ psp_status psp_reset(psp_handle h) {
   h->wait = 0;
   h->wait_len = 1;
   h->hist_dt = NAN;
+  h->hist_count_host = 0;
   PSP_CUDA(cudaMemsetAsync(&h->st->hist_count, 0, sizeof(int), h->stream));
   PSP_CUDA(cudaStreamSynchronize(h->stream));
   return PSP_OK;

@@ -23,14 +23,19 @@ def dev():
     return torch_dev()
 
 
-def test_batch_matches_exact_and_single(dev):
+@pytest.mark.parametrize("onchip", [0, 1], ids=["graphs", "onchip"])
+def test_batch_matches_exact_and_single(dev, onchip):
+    """onchip = 0: the instances' cycle graphs driven by host threads; onchip = 1: the
+    persistent launches of the on-chip path (one CTA per system) run every instance's cycles.
+    Either way every instance equals its exact solve within cond(A) 2 tol and the same
+    instance stepped alone (the same arithmetic) to rounding."""
     import torch
     from paper_1308_5626_gb300 import psp
     ws = [inputs.c4_instance(i, e_range=(8, 12)) for i in range(12)]
 
     def make(w):
         s = torch.cuda.Stream(device=dev)
-        return psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=psp.PSP_MIXED, stream=s)
+        return psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=psp.PSP_MIXED, stream=s, onchip=onchip)
 
     batch = [make(w) for w in ws]
     twins = [make(w) for w in ws]

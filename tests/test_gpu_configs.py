@@ -41,15 +41,16 @@ def _check_step(op, dt, tol, un, got, kappa, inv_inf, what):
     assert rel_max(got, ref) <= eb, (what, "elementwise", rel_max(got, ref), eb)
 
 
+@pytest.mark.parametrize("onchip", [0, 1], ids=["graphs", "onchip"])
 @pytest.mark.parametrize("cyclic", [0, 1], ids=["paper-boundary-rows", "cyclic-band"])
-def test_1d_workload_as_configured(dev, cyclic):
+def test_1d_workload_as_configured(dev, cyclic, onchip):
     from paper_1308_5626_gb300 import psp
     w = inputs.c1()
     assert (w.n, w.order, w.m, w.b, w.tol, w.steps) == (1024, 4, 30, 2, 1e-10, 20)
     op = Operator(w.shape, w.order, w.terms)
     kappa = exact.condition_number(op, w.dt)
     inv_inf = inv_inf_norm(op, w.dt)
-    s = psp.Solver(w.shape, w.order, w.terms, w.b, w.m, cyclic=cyclic)
+    s = psp.Solver(w.shape, w.order, w.terms, w.b, w.m, cyclic=cyclic, onchip=onchip)
     u = t64(w.u0, dev)
     un = w.u0
     for step in range(w.steps):

@@ -74,8 +74,9 @@ def test_cyclic_fit(dev, n, b, M, intercept):
     s.close()
 
 
+@pytest.mark.parametrize("onchip", [0, 1], ids=["graphs", "onchip"])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_cyclic_steps_one_iteration(dev, precision):
+def test_cyclic_steps_one_iteration(dev, precision, onchip):
     import torch
     from paper_1308_5626_gb300 import psp
     w = inputs.c1(1024)
@@ -83,7 +84,7 @@ def test_cyclic_steps_one_iteration(dev, precision):
     tol = 1e-10
     its = {}
     for cyc in (0, 1):
-        s = psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=precision, cyclic=cyc)
+        s = psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=precision, cyclic=cyc, onchip=onchip)
         u = torch.tensor(w.u0, dtype=torch.float64, device=dev)
         out = torch.empty_like(u)
         seq = []

@@ -39,15 +39,16 @@ def test_banded_matvec_and_adjoint(dev):
         s.close()
 
 
+@pytest.mark.parametrize("onchip", [0, 1], ids=["graphs", "onchip"])
 @pytest.mark.parametrize("n", inputs.MOCK_SIZES)
-def test_mock_steps_follow_the_oracle(dev, n):
+def test_mock_steps_follow_the_oracle(dev, n, onchip):
     from paper_1308_5626_gb300 import psp
     A = inputs.mock_seven_diagonal(n, seed=n)
     u = np.arange(1.0, n + 1.0)
     ref = np.linalg.solve(A, u)
     kappa = np.linalg.cond(A)
     tol = 1e-10
-    s = psp.Solver.banded(t64(inputs.dense_to_band(A, 3).reshape(-1), dev), 3, 1, 10)
+    s = psp.Solver.banded(t64(inputs.dense_to_band(A, 3).reshape(-1), dev), 3, 1, 10, onchip=onchip)
     st = Stepper(MatrixOperator(A), b=1, m=10)
     for step in range(3):
         x_o, oinfo = st.step(u, 1.0, tol)

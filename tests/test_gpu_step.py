@@ -9,6 +9,8 @@
   step by step (CGS2 on the GPU vs MGS in the oracle: equal in exact arithmetic; counts
   within max(2, 10%) because restarts amplify rounding differences).
 * A short cycle (m <= 8) matches the oracle's R(m) and X to rounding.
+* Small systems run both ways: through the captured cycle graphs (onchip = 0) and on the
+  on-chip path (onchip = 1: one CTA runs every cycle of the step, CGS2).
 """
 import numpy as np
 import pytest
@@ -39,12 +41,16 @@ def _dt(w, op):
 SMALL = [inputs.c1(1000), inputs.c2(48, 40), inputs.c3(16, kmax=4)]
 
 
+PATHS = pytest.mark.parametrize("onchip", [0, 1], ids=["graphs", "onchip"])
+
+
+@PATHS
 @pytest.mark.parametrize("w", SMALL, ids=lambda w: w.name)
-def test_fp64_steps_match_exact(dev, w):
+def test_fp64_steps_match_exact(dev, w, onchip):
     op = Operator(w.shape, w.order, w.terms)
     dt = _dt(w, op)
     kappa = exact.condition_number(op, dt)
-    s = _solver(w)
+    s = _solver(w, onchip=onchip)
     u = t64(w.u0, dev)
     un = w.u0
     for step in range(4):
@@ -57,12 +63,13 @@ def test_fp64_steps_match_exact(dev, w):
     s.close()
 
 
+@PATHS
 @pytest.mark.parametrize("w", SMALL, ids=lambda w: w.name)
-def test_mixed_steps_match_exact(dev, w):
+def test_mixed_steps_match_exact(dev, w, onchip):
     from paper_1308_5626_gb300 import psp
     op = Operator(w.shape, w.order, w.terms)
     dt = _dt(w, op)
-    s = _solver(w, precision=psp.PSP_MIXED)
+    s = _solver(w, precision=psp.PSP_MIXED, onchip=onchip)
     u = t64(w.u0, dev)
     un = w.u0
     for step in range(4):
@@ -87,7 +94,7 @@ def test_matvec_placement(dev, w, precision, fuse):
     dt = _dt(w, op)
     tol = 1e-12 if precision == 0 else 1e-10
     bound = exact.condition_number(op, dt) * 2 * tol if precision == 0 else 1e-8
-    s = _solver(w, precision=precision, fuse_matvec=fuse)
+    s = _solver(w, precision=precision, fuse_matvec=fuse, onchip=0)
     u = t64(w.u0, dev)
     un = w.u0
     for step in range(3):
@@ -112,14 +119,15 @@ def _box3d():
     return dataclasses.replace(base, name="c3_box_128x16x12", shape=shape, u0=u0, m=30)
 
 
+@PATHS
 @pytest.mark.parametrize("precision", [0, 1])
-def test_3d_tiled_stencil_steps(dev, precision):
+def test_3d_tiled_stencil_steps(dev, precision, onchip):
     w = _box3d()
     op = Operator(w.shape, w.order, w.terms)
     dt = _dt(w, op)
     tol = 1e-12 if precision == 0 else 1e-10
     bound = exact.condition_number(op, dt) * 2 * tol if precision == 0 else 1e-8
-    s = _solver(w, precision=precision)
+    s = _solver(w, precision=precision, onchip=onchip)
     u = t64(w.u0, dev)
     un = w.u0
     for step in range(2):
@@ -132,13 +140,14 @@ def test_3d_tiled_stencil_steps(dev, precision):
     s.close()
 
 
+@PATHS
 @pytest.mark.parametrize("w", [inputs.c1(1000), inputs.c3(12, kmax=3)], ids=lambda w: w.name)
-def test_iterations_follow_the_oracle(dev, w):
+def test_iterations_follow_the_oracle(dev, w, onchip):
     from paper_1308_5626_gb300 import psp
     op = Operator(w.shape, w.order, w.terms)
     dt = _dt(w, op)
     st = Stepper(op, b=w.b, m=w.m)
-    s = _solver(w)
+    s = _solver(w, onchip=onchip)
     u = t64(w.u0, dev)
     un = w.u0
     for step in range(6):
@@ -156,8 +165,9 @@ def test_iterations_follow_the_oracle(dev, w):
     s.close()
 
 
+@PATHS
 @pytest.mark.parametrize("m", [3, 5])
-def test_one_short_cycle_matches_oracle(dev, m):
+def test_one_short_cycle_matches_oracle(dev, m, onchip):
     """N = I, one restart cycle of m iterations: every R(k) and X equal the oracle's to
     rounding.
 
@@ -169,7 +179,7 @@ def test_one_short_cycle_matches_oracle(dev, m):
     from paper_1308_5626_gb300 import psp
     w = inputs.c1(512)
     op = Operator(w.shape, w.order, w.terms)
-    s = psp.Solver(w.shape, w.order, w.terms, w.b, m, max_restarts=1)
+    s = psp.Solver(w.shape, w.order, w.terms, w.b, m, max_restarts=1, onchip=onchip)
     out, info = s.step(t64(w.u0, dev), w.dt, 1e-30, allow_noconv=True)
     R_gpu = psp.psp_last_cycle_residuals(s.handle)
     res = gmres.pspgmres(lambda x: op.apply_A(x, w.dt), w.u0, None, 1e-30, m, w.u0, 1, gs="cgs2")
@@ -181,14 +191,15 @@ def test_one_short_cycle_matches_oracle(dev, m):
     s.close()
 
 
-def test_long_cycle_invariants(dev):
+@PATHS
+def test_long_cycle_invariants(dev, onchip):
     """One cycle of m = 30: the GPU's R(m) is a valid GMRES residual (it equals the true
     residual of the returned X) and lies within 1e-3 of the oracle's."""
     from oracle import gmres
     from paper_1308_5626_gb300 import psp
     w = inputs.c1(512)
     op = Operator(w.shape, w.order, w.terms)
-    s = psp.Solver(w.shape, w.order, w.terms, w.b, w.m, max_restarts=1)
+    s = psp.Solver(w.shape, w.order, w.terms, w.b, w.m, max_restarts=1, onchip=onchip)
     out, info = s.step(t64(w.u0, dev), w.dt, 1e-30, allow_noconv=True)
     x = out.cpu().numpy()
     true_res = np.linalg.norm(w.u0 - op.apply_A(x, w.dt))
@@ -199,9 +210,10 @@ def test_long_cycle_invariants(dev):
     s.close()
 
 
-def test_history_and_dt_change(dev):
+@PATHS
+def test_history_and_dt_change(dev, onchip):
     w = inputs.c1(256)
-    s = _solver(w)
+    s = _solver(w, onchip=onchip)
     u = t64(w.u0, dev)
     # every cycle stores its restart pair and one pair per matvec; the delayed
     # re-orthogonalisation makes one matvec more than the Arnoldi columns in a cycle that
@@ -248,13 +260,14 @@ def test_full_size_3d_step(dev):
     s.close()
 
 
+@PATHS
 @pytest.mark.parametrize("precision,solver", [(0, 0), (1, 0), (0, 1)], ids=["gmres-fp64", "gmres-mixed", "bicgstab"])
-def test_zero_right_hand_side(dev, precision, solver):
+def test_zero_right_hand_side(dev, precision, solver, onchip):
     """u^n = 0: the restart finds a zero residual, the step ends without an iteration and
     u^{n+1} = 0 exactly (GMRES in both forms, BiCGSTAB)."""
     import torch
     w = inputs.c2(48, 40)
-    s = _solver(w, precision=precision, solver=solver)
+    s = _solver(w, precision=precision, solver=solver, onchip=onchip)
     u = torch.zeros(w.n, dtype=torch.float64, device=dev)
     out = torch.full_like(u, 7.0)
     for _ in range(2):
@@ -264,14 +277,15 @@ def test_zero_right_hand_side(dev, precision, solver):
     s.close()
 
 
+@PATHS
 @pytest.mark.parametrize("precision", [0, 1])
-def test_max_restart_length(dev, precision):
+def test_max_restart_length(dev, precision, onchip):
     """m = 64, the largest restart length (the scalar engine's largest shared layout and
     cross-CTA sums over 2(m+1) values): one full cycle's R(m) equals the true residual of the
     returned X, and a whole step meets the exact solve's bound."""
     w = inputs.c2(64, 48)
     op = Operator(w.shape, w.order, w.terms)
-    s_m = psp_solver_m(w, 64, precision, max_restarts=1)
+    s_m = psp_solver_m(w, 64, precision, max_restarts=1, onchip=onchip)
     out, info = s_m.step(t64(w.u0, dev), w.dt, 1e-30, allow_noconv=True)
     assert info.cycles == 1
     if precision == 0:   # the mixed form's cycle may end at its inner tolerance first
@@ -281,7 +295,7 @@ def test_max_restart_length(dev, precision):
     else:
         assert 1 <= info.iters <= 64
     s_m.close()
-    s_m = psp_solver_m(w, 64, precision)
+    s_m = psp_solver_m(w, 64, precision, onchip=onchip)
     tol = 1e-12 if precision == 0 else 1e-10
     out, info = s_m.step(t64(w.u0, dev), w.dt, tol)
     ref = exact.solve_fourier(op, w.u0, w.dt)
