@@ -565,7 +565,7 @@ def _bicgstab_line(w, device, steps: int = 3):
     return {"workload": w.name, "form": "fp64", "rows": rows}
 
 
-def _batch_line(device, count: int, steps: int, nthreads: int, onchip: int = 1):
+def _batch_line(device, count: int, steps: int, nthreads: int, onchip: int = -1, tune: bool = False):
     """The batched workload: `count` independent instances (inputs.c4_instance: 1D/2D, n from
     2^10 to 2^18, orders 2-8, b 1-4, CFL 1-20, mixed form, tol 1e-8), each on its own stream,
     stepped together by psp_step_batch with `nthreads` host threads.  One untimed step
@@ -586,8 +586,13 @@ def _batch_line(device, count: int, steps: int, nthreads: int, onchip: int = 1):
     t_create = time.perf_counter() - t0
     hs = [s.handle for s in solvers]
     dts = [w.dt for w in ws]
-    psp.psp_step_batch(hs, us, outs, dts, 1e-8, nthreads=nthreads, allow_noconv=True)
-    us, outs = outs, us
+    # untimed: one step (graph captures, the first fits), and with the autotuner on, one step per
+    # candidate it measures for every size class
+    psp.psp_batch_tuner(1 if tune else 0)
+    for _ in range(1 + (4 if tune else 0)):
+        psp.psp_step_batch(hs, us, outs, dts, 1e-8, nthreads=nthreads, allow_noconv=True)
+        us, outs = outs, us
+    table = psp.psp_batch_tuner(-1) if tune else None
     torch.cuda.synchronize(device)
     per = []
     t0 = time.perf_counter()
@@ -601,15 +606,17 @@ def _batch_line(device, count: int, steps: int, nthreads: int, onchip: int = 1):
         s.close()
     per.sort()
     its = sum(i.iters for i in infos)
-    return {"instances": count, "steps": steps, "host_threads": nthreads, "onchip": onchip,
+    psp.psp_batch_tuner(0)
+    return {"instances": count, "steps": steps, "host_threads": nthreads, "onchip": onchip, "autotuner": table,
             "unknowns_total": int(sum(w.n for w in ws)),
             "value": count * steps / wall, "unit": "implicit steps/s (all instances)",
             "p50_ms": 1e3 * per[len(per) // 2], "p99_ms": 1e3 * per[min(len(per) - 1, int(0.99 * len(per)))],
             "iters_per_instance_step": its / count,
             "create_s": t_create,
-            "note": ("the cycles of all instances in shared persistent launches (one CTA per system); per-instance "
-                     "time = its device time in those launches (globaltimer) + the host time of its fit and "
-                     "factorisation; aggregate from the host wall clock") if onchip else
+            "note": ("each size class on the execution the batch autotuner measured fastest (cycle graphs, or the "
+                     "on-chip path's shared persistent launches with one CTA per system); per-instance time = host "
+                     "wall time of its step (graphs) or device time of its cycles plus host time of its fit "
+                     "(on-chip); aggregate from the host wall clock") if tune else
                     ("concurrent per-instance cycle graphs on per-instance streams, driven by psp_step_batch's "
                      "host threads; host wall clock")}
 
@@ -922,7 +929,7 @@ def main():
         e1 = _e1_line(device)
     batch = None
     if a.batch > 0 and rank == 0:
-        batch = _batch_line(device, a.batch, a.batch_steps, a.batch_threads, onchip=1)
+        batch = _batch_line(device, a.batch, a.batch_steps, a.batch_threads, onchip=-1, tune=True)
         batch["cycle_graphs"] = _batch_line(device, a.batch, a.batch_steps, a.batch_threads, onchip=0)
     cyclic = None
     if not a.no_cyclic and rank == 0:

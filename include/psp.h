@@ -205,17 +205,42 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
 /*
  * One implicit step of many independent handles (the batched form of the blueprint's
  * configuration 4): handle i steps u_n[i] -> u_np1[i] with dt[i] and the common tolerance
- * tol, exactly as psp_step would.  nthreads host threads take the instances in order, each
- * stepping one handle at a time on that handle's stream, so up to nthreads instances' cycle
- * graphs run on the GPU concurrently; handles should therefore be created with distinct
- * streams.  infos, seconds (host wall time of each instance's step) and statuses are
- * host arrays of count entries or NULL.  Returns PSP_OK, PSP_ERR_NOCONV if an instance
+ * tol, exactly as psp_step would.  The handles on the on-chip path (opts.onchip; those of the
+ * first one's precision) run the restart cycles of all their steps in shared persistent
+ * launches, one CTA per system taken from a work counter, largest first, one launch per CTA
+ * size and per round of the acceptance rule's decisions; the other handles are stepped
+ * concurrently by nthreads host threads, each stepping one handle at a time on that handle's
+ * stream, so up to nthreads instances' cycle graphs run on the GPU concurrently; handles
+ * should therefore be created with distinct streams.  The batched launches take device and
+ * pinned buffers made on the first such call (and grown for a larger batch).  infos, seconds
+ * and statuses are host arrays of count entries or NULL; seconds is each instance's time:
+ * host wall time of its step on the graph path, device time of its cycles (the GPU clock) plus
+ * host time of its fit on the on-chip path.  Returns PSP_OK, PSP_ERR_NOCONV if an instance
  * reached max_restarts, or the first other error status of an instance (all instances are
- * attempted).  A handle must not appear twice.
+ * attempted).  A handle must not appear twice.  See psp_batch_tuner.
  */
 psp_status psp_step_batch(psp_handle *handles, int count, const double *const *u_n, double *const *u_np1,
                           const double *dt, double tol, int nthreads, psp_step_info *infos, double *seconds,
                           psp_status *statuses);
+
+/* The batch autotuner of psp_step_batch (not in the paper).  mode 1 switches it on and
+ * forgets what it measured, 0 switches it off (the handles keep the execution it last gave
+ * them), -1 only reports.  While on, psp_step_batch runs every instance of a size class
+ * (floor(log2 n)) the same way on a call: through the captured cycle graphs, or (for classes
+ * up to 2^16 unknowns) on the on-chip path with CTAs of 128, 256 or 512 threads -- one
+ * candidate per call until each was
+ * measured, then the one with the least time per Arnoldi iteration (an instance's device time
+ * on the on-chip path, its host wall time on the graph path), and it sets the handles'
+ * opts.onchip and CTA size accordingly (later psp_step calls on them run the same way).
+ * classes (host, max_classes entries, may be NULL) receives one entry per size class seen;
+ * *nclasses (may be NULL) their number. */
+typedef struct {
+  int log2_n;            /* size class: floor(log2 n) */
+  int choice;            /* -1: not decided; 0: cycle graphs; 128, 256, 512: on-chip CTA size */
+  int samples[4];        /* measured instance steps: graphs, on-chip 128, 256, 512 */
+  double us_per_iter[4]; /* mean time per Arnoldi iteration (microseconds) of each candidate */
+} psp_tuning_class;
+psp_status psp_batch_tuner(int mode, psp_tuning_class *classes, int max_classes, int *nclasses);
 
 /* Second-order implicit integrators on the step (not in the paper): each solves with the
  * same matrix-free PSP-GMRES and progressive preconditioner as psp_step, on another

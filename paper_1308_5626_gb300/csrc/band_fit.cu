@@ -21,6 +21,7 @@
 // hundred terms -- at FP32 instruction rates (GB300 runs FP64 at 1/64 of the FP32 rate).
 // An FP64 history is accumulated in FP64.
 #include <algorithm>
+#include <type_traits>
 
 #include "psp_kernels.cuh"
 
@@ -109,8 +110,194 @@ __global__ void __launch_bounds__(kFitRows) k_fit_moments(int64_t n, int M, cons
   }
 }
 
-// Cholesky solve of a Q x Q SPD system in registers (one square root and one division per
-// pivot; the substitutions multiply by the pivot's reciprocal).  Returns false if degenerate.
+// FP32 history, the fast form of the moments: every thread owns two consecutive rows (i,
+// i+1), and each of its moments is a pair (row i, row i+1) of double-float accumulators held
+// in packed FP32x2 registers, so one packed instruction advances both rows (the error-free
+// product a b = p + e by a multiply and an FMA, the error-free sum by Knuth's two-sum, as in
+// AccF2).  The history is staged in shared memory column chunk by column chunk with 16-byte
+// asynchronous copies, two chunks in flight, so the copies of the next chunk overlap the
+// arithmetic of this one.  Row windows: P_x rows i-B .. i+1+2B, P_y rows i, i+1.
+constexpr int kFm2Threads = 256;
+constexpr int kFm2Rows = 2 * kFm2Threads;        // rows per CTA
+constexpr int kFm2Cols = 8;                      // history columns per staged chunk
+constexpr int kFm2Lead = 4;                      // staged rows before the CTA's first row (>= B, 16-byte aligned)
+constexpr int kFm2Span = kFm2Rows + 12;          // staged P_x rows: r0-4 .. r0+kFm2Rows+7 (covers i+1+2B for B <= 4)
+
+__device__ __forceinline__ uint64_t f2pack(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2unpack(uint64_t v, float &a, float &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2add(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2sub(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2neg(uint64_t a) { return a ^ 0x8000000080000000ull; }
+
+// A pair of double-float accumulators (hi, lo packed per row).
+struct Acc2 {
+  uint64_t hi = 0, lo = 0;
+  // += a b, with na = -a: p = fl(a b), p - a b = fma(na, b, p) = -e exactly
+  __device__ __forceinline__ void fma(uint64_t a, uint64_t na, uint64_t b) {
+    const uint64_t p = f2mul(a, b);
+    const uint64_t ne = f2fma(na, b, p);
+    sum2(p, ne);
+  }
+  __device__ __forceinline__ void add(uint64_t v) { sum2(v, 0ull); }
+  // hi + lo += p - ne (two-sum of hi and p; the rounding error and -ne go to lo)
+  __device__ __forceinline__ void sum2(uint64_t p, uint64_t ne) {
+    const uint64_t s = f2add(hi, p);
+    const uint64_t bb = f2sub(s, hi);
+    const uint64_t err = f2add(f2sub(hi, f2sub(s, bb)), f2sub(p, bb));
+    hi = s;
+    lo = f2add(lo, f2sub(err, ne));
+  }
+  __device__ __forceinline__ void get(double &r0, double &r1) const {
+    float h0, h1, l0, l1;
+    f2unpack(hi, h0, h1);
+    f2unpack(lo, l0, l1);
+    r0 = (double)h0 + (double)l0;
+    r1 = (double)h1 + (double)l1;
+  }
+};
+
+template <int B>
+__global__ void __launch_bounds__(kFm2Threads) k_fit_moments_f32(int64_t n, int M, const float *__restrict__ Px,
+                                                                 const float *__restrict__ Py, int64_t ld,
+                                                                 double *__restrict__ mom, int cyclic, int vec) {
+  constexpr int NM = 4 * B + 4;
+  extern __shared__ __align__(16) float fm2[];
+  float *sx = fm2;                                   // [2][kFm2Cols][kFm2Span]
+  float *sy = fm2 + 2 * kFm2Cols * kFm2Span;         // [2][kFm2Cols][kFm2Rows]
+  const int64_t r0 = (int64_t)blockIdx.x * kFm2Rows;
+  const int tid = threadIdx.x;
+  // the 16-byte path: every staged row inside [0, n) and every column 16-byte aligned
+  const bool fast = vec && r0 - kFm2Lead >= 0 && r0 - kFm2Lead + kFm2Span <= n;
+  auto stage = [&](int c0, int buf) {
+    const int nc = min(kFm2Cols, M - c0);
+    float *bx = sx + buf * kFm2Cols * kFm2Span;
+    float *by = sy + buf * kFm2Cols * kFm2Rows;
+    if (fast) {
+      constexpr int CX = kFm2Span / 4, CY = kFm2Rows / 4;
+      for (int e = tid; e < kFm2Cols * (CX + CY); e += kFm2Threads) {
+        const int cc = e / (CX + CY), k = e % (CX + CY);
+        if (cc >= nc) continue;
+        if (k < CX) {
+          const float *src = Px + (int64_t)(c0 + cc) * ld + r0 - kFm2Lead + 4 * k;
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                           static_cast<uint32_t>(__cvta_generic_to_shared(bx + cc * kFm2Span + 4 * k))),
+                       "l"(src)
+                       : "memory");
+        } else {
+          const int kk = k - CX;
+          const float *src = Py + (int64_t)(c0 + cc) * ld + r0 + 4 * kk;
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                           static_cast<uint32_t>(__cvta_generic_to_shared(by + cc * kFm2Rows + 4 * kk))),
+                       "l"(src)
+                       : "memory");
+        }
+      }
+    } else {
+      for (int e = tid; e < kFm2Cols * kFm2Span; e += kFm2Threads) {
+        const int cc = e / kFm2Span, k = e % kFm2Span;
+        int64_t row = r0 - kFm2Lead + k;
+        if (cyclic) row = (row < 0) ? row + n : (row >= n ? row - n : row);   // B <= 4 < n: one wrap
+        bx[cc * kFm2Span + k] = (cc < nc && row >= 0 && row < n) ? Px[(int64_t)(c0 + cc) * ld + row] : 0.0f;
+      }
+      for (int e = tid; e < kFm2Cols * kFm2Rows; e += kFm2Threads) {
+        const int cc = e / kFm2Rows, k = e % kFm2Rows;
+        const int64_t row = r0 + k;
+        by[cc * kFm2Rows + k] = (cc < nc && row < n) ? Py[(int64_t)(c0 + cc) * ld + row] : 0.0f;
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  Acc2 S[2 * B + 1], Rp[2 * B + 1], ssx, ssy;
+  const int nch = (M + kFm2Cols - 1) / kFm2Cols;
+  stage(0, 0);
+  for (int ch = 0; ch < nch; ++ch) {
+    if (ch + 1 < nch) {
+      stage((ch + 1) * kFm2Cols, (ch + 1) & 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    const int buf = ch & 1;
+    const int nc = min(kFm2Cols, M - ch * kFm2Cols);
+    const float *bx = sx + buf * kFm2Cols * kFm2Span;
+    const float *by = sy + buf * kFm2Cols * kFm2Rows;
+    for (int cc = 0; cc < nc; ++cc) {
+      // x[k] = P_x(i - kFm2Lead + k) with i = r0 + 2 tid, k = 0 .. kFm2Lead + 2B + 1
+      const float *xw = bx + cc * kFm2Span + 2 * tid;
+      constexpr int NW = (kFm2Lead + 2 * B + 2 + 1) / 2;   // aligned pairs of the window
+      uint64_t pr[NW];
+#pragma unroll
+      for (int q = 0; q < NW; ++q) pr[q] = *reinterpret_cast<const uint64_t *>(xw + 2 * q);
+      // the pair (P_x(i + o), P_x(i + 1 + o)) for offset o (from the aligned pairs)
+      auto pair_at = [&](int o) -> uint64_t {
+        const int k = kFm2Lead + o;
+        if ((k & 1) == 0) return pr[k / 2];
+        float a0, a1, b0, b1;
+        f2unpack(pr[k / 2], a0, a1);
+        f2unpack(pr[k / 2 + 1], b0, b1);
+        return f2pack(a1, b0);
+      };
+      const uint64_t x0 = pr[kFm2Lead / 2];
+      const uint64_t nx0 = f2neg(x0);
+      const uint64_t y = *reinterpret_cast<const uint64_t *>(by + cc * kFm2Rows + 2 * tid);
+      const uint64_t ny = f2neg(y);
+#pragma unroll
+      for (int l = 0; l <= 2 * B; ++l) S[l].fma(x0, nx0, pair_at(l));
+#pragma unroll
+      for (int p = 0; p <= 2 * B; ++p) Rp[p].fma(y, ny, pair_at(p - B));
+      ssx.add(x0);
+      ssy.add(y);
+    }
+    __syncthreads();   // the buffer is refilled by the stage issued in the next round
+  }
+  const int64_t row = r0 + 2 * tid;
+  double v0, v1;
+#pragma unroll
+  for (int l = 0; l <= 2 * B; ++l) {
+    S[l].get(v0, v1);
+    if (row < n) mom[row * NM + l] = v0;
+    if (row + 1 < n) mom[(row + 1) * NM + l] = v1;
+    Rp[l].get(v0, v1);
+    if (row < n) mom[row * NM + 2 * B + 1 + l] = v0;
+    if (row + 1 < n) mom[(row + 1) * NM + 2 * B + 1 + l] = v1;
+  }
+  ssx.get(v0, v1);
+  if (row < n) mom[row * NM + 4 * B + 2] = v0;
+  if (row + 1 < n) mom[(row + 1) * NM + 4 * B + 2] = v1;
+  ssy.get(v0, v1);
+  if (row < n) mom[row * NM + 4 * B + 3] = v0;
+  if (row + 1 < n) mom[(row + 1) * NM + 4 * B + 3] = v1;
+}
+
+constexpr size_t kFm2Smem = (size_t)2 * kFm2Cols * (kFm2Span + kFm2Rows) * sizeof(float);
+
+// Cholesky solve of a Q x Q SPD system in registers (one reciprocal square root per pivot,
+// L_jj = d rsqrt(d); the substitutions multiply by rsqrt(d)).  Returns false if degenerate.
 template <int Q>
 __device__ __forceinline__ bool chol_solve(double (&G)[Q][Q], double (&rhs)[Q], int q) {
   double L[Q][Q], rd[Q];
@@ -121,8 +308,8 @@ __device__ __forceinline__ bool chol_solve(double (&G)[Q][Q], double (&rhs)[Q], 
 #pragma unroll
     for (int l = 0; l < Q; ++l) if (l < j) d -= L[j][l] * L[j][l];
     if (!(G[j][j] > 0.0) || !(d > kRelPivot * G[j][j])) return false;
-    const double ljj = sqrt(d);
-    const double r = 1.0 / ljj;
+    const double r = rsqrt(d);
+    const double ljj = d * r;
     L[j][j] = ljj;
     rd[j] = r;
 #pragma unroll
@@ -157,10 +344,10 @@ __device__ __forceinline__ bool chol_solve(double (&G)[Q][Q], double (&rhs)[Q], 
   return true;
 }
 
-template <int B>
-__global__ void __launch_bounds__(128) k_fit_solve(int64_t n, int M, int intercept,
-                                                   const double *__restrict__ mom, double *__restrict__ band,
-                                                   int *singular_count, int cyclic) {
+template <int B, int INTERCEPT>
+__global__ void __launch_bounds__(128) k_fit_solve(int64_t n, int M, const double *__restrict__ mom,
+                                                   double *__restrict__ band, int *singular_count, int cyclic) {
+  constexpr int intercept = INTERCEPT;
   constexpr int NM = 4 * B + 4;
   constexpr int W = 2 * B + 1;
   constexpr int Q = 2 * B + 2;
@@ -228,12 +415,25 @@ template <typename TH>
 void launch_fit(int b, int intercept, int64_t n, int M, const TH *Px, const TH *Py, int64_t ld, double *moments,
                 double *band, int *singular_count, cudaStream_t s, int cyclic) {
   const int g1 = (int)((n + kFitRows - 1) / kFitRows);
+  const int g1f = (int)((n + kFm2Rows - 1) / kFm2Rows);
   const int g2 = (int)((n + 127) / 128);
+  // 16-byte staging needs 16-byte aligned columns
+  const int vec = ((reinterpret_cast<uintptr_t>(Px) | reinterpret_cast<uintptr_t>(Py)) % 16 == 0) && (ld % 4 == 0);
   switch (b) {
 #define PSP_FIT(B_)                                                                              \
   case B_:                                                                                       \
-    k_fit_moments<TH, B_><<<g1, kFitRows, 0, s>>>(n, M, Px, Py, ld, moments, cyclic);            \
-    k_fit_solve<B_><<<g2, 128, 0, s>>>(n, M, intercept, moments, band, singular_count, cyclic);  \
+    if constexpr (std::is_same<TH, float>::value) {                                              \
+      static const bool attr_ = [] {                                                             \
+        return cudaFuncSetAttribute(k_fit_moments_f32<B_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                    (int)kFm2Smem) == cudaSuccess;                               \
+      }();                                                                                       \
+      (void)attr_;                                                                               \
+      k_fit_moments_f32<B_><<<g1f, kFm2Threads, kFm2Smem, s>>>(n, M, Px, Py, ld, moments, cyclic, vec); \
+    } else {                                                                                     \
+      k_fit_moments<TH, B_><<<g1, kFitRows, 0, s>>>(n, M, Px, Py, ld, moments, cyclic);          \
+    }                                                                                            \
+    if (intercept) k_fit_solve<B_, 1><<<g2, 128, 0, s>>>(n, M, moments, band, singular_count, cyclic); \
+    else k_fit_solve<B_, 0><<<g2, 128, 0, s>>>(n, M, moments, band, singular_count, cyclic);           \
     break;
     PSP_FIT(1) PSP_FIT(2) PSP_FIT(3) PSP_FIT(4)
 #undef PSP_FIT

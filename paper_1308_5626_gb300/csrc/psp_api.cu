@@ -957,6 +957,39 @@ psp_status run_segment(psp_ctx *h, int which, int max_cycles, Segment *out, int 
   return PSP_OK;
 }
 
+// The batch autotuner (psp_batch_tuner): per size class (floor(log2 n)) it tries, on the
+// first calls of psp_step_batch, every execution of a step -- the captured cycle graphs, and
+// the on-chip path with CTAs of 128, 256 and 512 threads (tile shapes of 4 rows per thread
+// at these sizes and up) -- one candidate per call for all instances of the class, and keeps
+// the one with the least measured time per Arnoldi iteration (each instance's time: its
+// device time on the on-chip path, its host wall time on the graph path).
+constexpr int kTuneCands = 4;                      // graphs, on-chip 128 / 256 / 512
+constexpr int kTuneThreads[kTuneCands] = {0, 128, 256, 512};
+struct TuneClass {
+  double t[kTuneCands] = {0, 0, 0, 0};   // summed seconds
+  double it[kTuneCands] = {0, 0, 0, 0};  // summed iterations
+  int cnt[kTuneCands] = {0, 0, 0, 0};
+  int choice = -1;                       // decided candidate
+};
+struct BatchTuner {
+  bool on = false;
+  int calls = 0;
+  TuneClass cls[32];
+};
+std::mutex g_tune_mu;
+BatchTuner g_tune;
+
+int size_class(int64_t n) {
+  int c = 0;
+  while (c < 31 && ((int64_t)1 << (c + 1)) <= n) ++c;
+  return c;
+}
+// The tuner tries the on-chip path up to 2^16 unknowns: one CTA streams a system's Krylov
+// basis at a fraction of the bandwidth the grid-wide passes reach, so larger systems take the
+// cycle graphs without being tried.
+constexpr int64_t kTuneOnChipMaxN = (int64_t)1 << 16;
+bool onchip_capable(const psp_ctx *h) { return h->opts.solver == PSP_SOLVER_GMRES && h->geo.n <= kTuneOnChipMaxN; }
+
 // Device and pinned buffers of the batched on-chip launches, made on the first batched call
 // (and grown when a larger batch comes); one set per process, used under a mutex.
 struct BatchBuffers {
@@ -1128,46 +1161,40 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
   return step_finish(h, r, info);
 }
 
-psp_status psp_step_batch(psp_handle *hs, int count, const double *const *u_n, double *const *u_np1,
-                          const double *dt, double tol, int nthreads, psp_step_info *infos, double *seconds,
-                          psp_status *statuses) {
-  if (!hs || !u_n || !u_np1 || !dt || count < 0) return fail(PSP_ERR_ARG, "NULL argument or negative count");
-  if (!(tol > 0.0)) return fail(PSP_ERR_ARG, "tol must be > 0");
-  for (int i = 0; i < count; ++i)
-    if (!hs[i]) return fail(PSP_ERR_ARG, "NULL handle in the batch");
-  {  // two threads must never step one handle (its stream and workspace are not shared)
-    std::vector<psp_handle> sorted(hs, hs + count);
-    std::sort(sorted.begin(), sorted.end());
-    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
-      return fail(PSP_ERR_ARG, "a handle appears twice in the batch");
-  }
-  if (count == 0) return PSP_OK;
-  bool all_onchip = true;
-  for (int i = 0; i < count; ++i) all_onchip = all_onchip && hs[i]->onchip && hs[i]->mixed == hs[0]->mixed;
-  if (all_onchip) return step_batch_onchip(hs, count, u_n, u_np1, dt, tol, nthreads, infos, seconds, statuses);
+}  // extern "C"
+
+namespace {
+
+// The graph-path instances of a batch: nthreads host threads take them in order, each stepping
+// one handle at a time on that handle's own stream, so the GPU runs nthreads instances' cycle
+// graphs concurrently while each thread waits for its instance's cycle summaries.
+void step_batch_graphs(psp_ctx **hs, const std::vector<int> &idx, const double *const *u_n, double *const *u_np1,
+                       const double *dt, double tol, int nthreads, psp_step_info *infos, double *seconds,
+                       psp_status *statuses, std::atomic<int> &first_err, std::atomic<bool> &noconv) {
+  const int count = (int)idx.size();
+  if (count == 0) return;
   int dev = 0;
   cudaGetDevice(&dev);
-  const int nt = std::max(1, std::min(nthreads < 1 ? 1 : nthreads, std::max(count, 1)));
+  const int nt = std::max(1, std::min(nthreads < 1 ? 1 : nthreads, count));
   // more threads than cores: the threads wait on blocking-sync events instead of spinning
   const unsigned cores = std::thread::hardware_concurrency();
   const bool block = cores > 0 && (unsigned)nt > cores;
-  for (int i = 0; i < count; ++i) {
+  for (int i : idx) {
     if (block && !hs[i]->wait_ev &&
-        cudaEventCreateWithFlags(&hs[i]->wait_ev, cudaEventBlockingSync | cudaEventDisableTiming) != cudaSuccess)
-      return fail(PSP_ERR_CUDA, "blocking-sync event");
+        cudaEventCreateWithFlags(&hs[i]->wait_ev, cudaEventBlockingSync | cudaEventDisableTiming) != cudaSuccess) {
+      int expected = (int)PSP_OK;
+      first_err.compare_exchange_strong(expected, (int)PSP_ERR_CUDA);
+      return;
+    }
     hs[i]->blocking_wait = block;
   }
-  // instances are taken from a shared counter in order; every worker thread steps one
-  // handle at a time on that handle's own stream, so the GPU runs nt instances' cycle
-  // graphs concurrently while each thread waits for its instance's cycle summaries
   std::atomic<int> next{0};
-  std::atomic<int> first_err{(int)PSP_OK};   // first status other than OK and NOCONV
-  std::atomic<bool> noconv{false};
   auto work = [&]() {
     cudaSetDevice(dev);
     for (;;) {
-      const int i = next.fetch_add(1);
-      if (i >= count) break;
+      const int k = next.fetch_add(1);
+      if (k >= count) break;
+      const int i = idx[k];
       const auto t0 = std::chrono::steady_clock::now();
       psp_step_info info{};
       const psp_status st = psp_step(hs[i], u_n[i], u_np1[i], dt[i], tol, &info);
@@ -1187,10 +1214,171 @@ psp_status psp_step_batch(psp_handle *hs, int count, const double *const *u_n, d
   for (int t = 1; t < nt; ++t) pool.emplace_back(work);
   work();
   for (auto &th : pool) th.join();
-  for (int i = 0; i < count; ++i) hs[i]->blocking_wait = false;
+  for (int i : idx) hs[i]->blocking_wait = false;
+}
+
+}  // namespace
+
+extern "C" {
+
+psp_status psp_step_batch(psp_handle *hs, int count, const double *const *u_n, double *const *u_np1,
+                          const double *dt, double tol, int nthreads, psp_step_info *infos, double *seconds,
+                          psp_status *statuses) {
+  if (!hs || !u_n || !u_np1 || !dt || count < 0) return fail(PSP_ERR_ARG, "NULL argument or negative count");
+  if (!(tol > 0.0)) return fail(PSP_ERR_ARG, "tol must be > 0");
+  for (int i = 0; i < count; ++i)
+    if (!hs[i]) return fail(PSP_ERR_ARG, "NULL handle in the batch");
+  {  // two threads must never step one handle (its stream and workspace are not shared)
+    std::vector<psp_handle> sorted(hs, hs + count);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+      return fail(PSP_ERR_ARG, "a handle appears twice in the batch");
+  }
+  if (count == 0) return PSP_OK;
+  // per-instance times and iterations are needed by the tuner even when the caller does not
+  // ask for them
+  std::vector<double> secs(count, 0.0);
+  std::vector<psp_step_info> inf(count);
+  std::vector<psp_status> sts(count, PSP_OK);
+  // the tuner's plan for this call: every instance of a size class runs the class's candidate
+  std::vector<int> cand(count, -1);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    if (g_tune.on) {
+      for (int i = 0; i < count; ++i) {
+        TuneClass &tc = g_tune.cls[size_class(hs[i]->geo.n)];
+        int c = tc.choice;
+        if (c < 0) c = g_tune.calls % kTuneCands;
+        if (c > 0 && !onchip_capable(hs[i])) c = 0;
+        cand[i] = c;
+        hs[i]->onchip = c > 0;
+        if (c > 0) hs[i]->oc_threads = kTuneThreads[c];
+      }
+    }
+  }
+  // the on-chip group (one precision) runs in shared persistent launches driven by one host
+  // thread, concurrently with the graph group's host threads
+  std::vector<int> oc, gr;
+  int oc_mixed = -1;
+  for (int i = 0; i < count; ++i) {
+    if (hs[i]->onchip && (oc_mixed < 0 || (int)hs[i]->mixed == oc_mixed)) {
+      oc_mixed = hs[i]->mixed ? 1 : 0;
+      oc.push_back(i);
+    } else {
+      gr.push_back(i);
+    }
+  }
+  std::atomic<int> first_err{(int)PSP_OK};
+  std::atomic<bool> noconv{false};
+  psp_status oc_status = PSP_OK;
+  std::string oc_msg;
+  std::thread oc_thread;
+  if (!oc.empty()) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int fin_threads = gr.empty() ? nthreads : std::max(1, nthreads / 4);
+    oc_thread = std::thread([&, dev, fin_threads]() {
+      cudaSetDevice(dev);
+      std::vector<psp_ctx *> hv;
+      std::vector<const double *> ui;
+      std::vector<double *> uo;
+      std::vector<double> dv;
+      for (int i : oc) {
+        hv.push_back(hs[i]);
+        ui.push_back(u_n[i]);
+        uo.push_back(u_np1[i]);
+        dv.push_back(dt[i]);
+      }
+      const int k = (int)oc.size();
+      std::vector<psp_step_info> oi(k);
+      std::vector<double> os(k);
+      std::vector<psp_status> ost(k, PSP_OK);
+      oc_status = step_batch_onchip(hv.data(), k, ui.data(), uo.data(), dv.data(), tol, fin_threads, oi.data(),
+                                    os.data(), ost.data());
+      if (oc_status != PSP_OK && oc_status != PSP_ERR_NOCONV) oc_msg = g_last_error;
+      for (int j = 0; j < k; ++j) {
+        inf[oc[j]] = oi[j];
+        secs[oc[j]] = os[j];
+        sts[oc[j]] = ost[j];
+      }
+    });
+  }
+  step_batch_graphs(hs, gr, u_n, u_np1, dt, tol, nthreads, inf.data(), secs.data(), sts.data(), first_err, noconv);
+  if (oc_thread.joinable()) oc_thread.join();
+  if (oc_status == PSP_ERR_NOCONV) noconv = true;
+  else if (oc_status != PSP_OK) {
+    int expected = (int)PSP_OK;
+    first_err.compare_exchange_strong(expected, (int)oc_status);
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    if (g_tune.on) {
+      for (int i = 0; i < count; ++i) {
+        if (cand[i] < 0 || sts[i] != PSP_OK) continue;
+        TuneClass &tc = g_tune.cls[size_class(hs[i]->geo.n)];
+        tc.t[cand[i]] += secs[i];
+        tc.it[cand[i]] += std::max(1, inf[i].iters);
+        tc.cnt[cand[i]] += 1;
+      }
+      g_tune.calls += 1;
+      for (int c = 0; c < 32; ++c) {   // decide the classes whose every possible candidate was measured
+        TuneClass &tc = g_tune.cls[c];
+        if (tc.choice >= 0 || tc.cnt[0] == 0) continue;
+        const bool oc_ok = ((int64_t)1 << c) <= kTuneOnChipMaxN;
+        bool all = true;
+        for (int k = 1; k < kTuneCands && oc_ok; ++k) all = all && tc.cnt[k] > 0;
+        if (!all && g_tune.calls < 2 * kTuneCands) continue;
+        int best = -1;
+        double bv = 0.0;
+        for (int k = 0; k < kTuneCands; ++k) {
+          if (tc.cnt[k] == 0) continue;
+          const double v = tc.t[k] / tc.it[k];
+          if (best < 0 || v < bv) { best = k; bv = v; }
+        }
+        tc.choice = best;
+      }
+    }
+  }
+  for (int i = 0; i < count; ++i) {
+    if (infos) infos[i] = inf[i];
+    if (seconds) seconds[i] = secs[i];
+    if (statuses) statuses[i] = sts[i];
+  }
   if (first_err.load() != (int)PSP_OK)
-    return fail((psp_status)first_err.load(), "at least one instance of the batch failed (see statuses)");
+    return fail((psp_status)first_err.load(),
+                oc_msg.empty() ? "at least one instance of the batch failed (see statuses)" : oc_msg);
   return noconv.load() ? fail(PSP_ERR_NOCONV, "an instance reached max_restarts") : PSP_OK;
+}
+
+psp_status psp_batch_tuner(int mode, psp_tuning_class *classes, int max_classes, int *nclasses) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  if (mode == 1) {
+    g_tune = BatchTuner{};
+    g_tune.on = true;
+  } else if (mode == 0) {
+    g_tune.on = false;
+  } else if (mode != -1) {
+    return fail(PSP_ERR_ARG, "mode must be 1, 0 or -1");
+  }
+  int k = 0;
+  for (int c = 0; c < 32; ++c) {
+    const TuneClass &tc = g_tune.cls[c];
+    bool seen = false;
+    for (int j = 0; j < kTuneCands; ++j) seen = seen || tc.cnt[j] > 0;
+    if (!seen) continue;
+    if (classes && k < max_classes) {
+      psp_tuning_class &o = classes[k];
+      o.log2_n = c;
+      o.choice = tc.choice < 0 ? -1 : kTuneThreads[tc.choice];
+      for (int j = 0; j < kTuneCands; ++j) {
+        o.samples[j] = tc.cnt[j];
+        o.us_per_iter[j] = tc.cnt[j] > 0 ? 1e6 * tc.t[j] / tc.it[j] : 0.0;
+      }
+    }
+    ++k;
+  }
+  if (nclasses) *nclasses = k;
+  return PSP_OK;
 }
 
 namespace {

@@ -55,6 +55,11 @@ class psp_step_info(ctypes.Structure):
 PSP_K_NAMES = ["precond", "stencil", "orth_dots", "unused", "orth_update"]
 
 
+class psp_tuning_class(ctypes.Structure):
+    _fields_ = [("log2_n", ctypes.c_int), ("choice", ctypes.c_int), ("samples", ctypes.c_int * 4),
+                ("us_per_iter", ctypes.c_double * 4)]
+
+
 class psp_profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 5), ("bytes", ctypes.c_double * 5), ("launches", ctypes.c_int64 * 5)]
 
@@ -92,6 +97,7 @@ _SIGS = {
     "psp_set_profiling": [_VP, ctypes.c_int],
     "psp_get_profile": [_VP, ctypes.POINTER(psp_profile), ctypes.c_int],
     "psp_last_cycle_residuals": [_VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+    "psp_batch_tuner": [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "psp_fit_band_static": [_VP, _VP, ctypes.c_int64, ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _VP,
                             ctypes.POINTER(ctypes.c_int), _VP],
 }
@@ -224,6 +230,21 @@ def psp_step_batch(handles, u_n, u_np1, dt, tol: float, nthreads: int = 8, allow
     if st != PSP_OK and not (allow_noconv and st == PSP_ERR_NOCONV):
         _check(st, "psp_step_batch")
     return list(infos), list(secs), list(sts)
+
+
+def psp_batch_tuner(mode: int = -1):
+    """Switch the batch autotuner on (1: and forget its measurements) or off (0), or only
+    query it (-1); returns its table: one dict per size class seen."""
+    arr = (psp_tuning_class * 32)()
+    k = ctypes.c_int(0)
+    _check(lib().psp_batch_tuner(int(mode), ctypes.cast(arr, ctypes.c_void_p), 32, ctypes.byref(k)), "psp_batch_tuner")
+    names = ["graphs", "onchip128", "onchip256", "onchip512"]
+    out = []
+    for c in arr[:k.value]:
+        out.append({"log2_n": c.log2_n, "choice": {-1: None, 0: "graphs"}.get(c.choice, "onchip%d" % c.choice),
+                    "samples": dict(zip(names, list(c.samples))),
+                    "us_per_iter": dict(zip(names, [round(v, 3) for v in c.us_per_iter]))})
+    return out
 
 
 def psp_apply_L(h, term: int, x, y) -> None:

@@ -75,3 +75,41 @@ def test_batch_refuses_a_repeated_handle(dev):
     with pytest.raises(RuntimeError):
         psp.psp_step_batch([s.handle, s.handle], u, out, [w.dt, w.dt], 1e-8, nthreads=2)
     s.close()
+
+
+def test_batch_tuner_measures_every_candidate_and_keeps_exact_steps(dev):
+    """psp_batch_tuner(1): the first calls run each size class on one candidate per call (cycle
+    graphs, on-chip CTAs of 128 / 256 / 512), every step still equal to the exact solve within
+    cond(A) 2 tol; afterwards every class has a decision and its instances keep it."""
+    import torch
+    from paper_1308_5626_gb300 import psp
+    ws = [inputs.c4_spec(k % 2 == 1, 10 + 2 * (k % 3), 2 + 2 * (k % 4), 1 + k % 4, 5.0 + k, seed=700 + k)
+          for k in range(8)]
+    solvers = [psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=psp.PSP_MIXED,
+                          stream=torch.cuda.Stream(device=dev)) for w in ws]
+    us = [t64(w.u0, dev) for w in ws]
+    outs = [torch.empty_like(u) for u in us]
+    refs = [w.u0 for w in ws]
+    ops = [Operator(w.shape, w.order, w.terms) for w in ws]
+    psp.psp_batch_tuner(1)
+    try:
+        for call in range(6):
+            infos, secs, sts = psp.psp_step_batch([s.handle for s in solvers], us, outs, [w.dt for w in ws], 1e-8,
+                                                  nthreads=4)
+            torch.cuda.synchronize()
+            for i, w in enumerate(ws):
+                assert sts[i] == 0, (call, i)
+                got = outs[i].cpu().numpy()
+                ref = exact.solve_fourier(ops[i], refs[i], w.dt)
+                assert rel(got, ref) <= exact.condition_number(ops[i], w.dt) * 2 * 1e-8, (call, i)
+                refs[i] = got
+            us, outs = outs, us
+        table = psp.psp_batch_tuner(-1)
+        assert {c["log2_n"] for c in table} == {10, 12, 14}
+        for c in table:
+            assert c["choice"] is not None, c
+            assert all(v >= 1 for v in c["samples"].values()), c
+    finally:
+        psp.psp_batch_tuner(0)
+        for s in solvers:
+            s.close()
