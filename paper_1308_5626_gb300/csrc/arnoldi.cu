@@ -447,20 +447,23 @@ __device__ __forceinline__ void matvec_vec(const T *__restrict__ x, const T (*c)
   for (int i = 0; i < W; ++i) {
     T s = c[0][kMaxR] * wn[NH * W + i];
 #pragma unroll
-    for (int jj = 1; jj <= R; ++jj) s += c[0][kMaxR - jj] * wn[NH * W + i - jj] + c[0][kMaxR + jj] * wn[NH * W + i + jj];
+    for (int jj = 1; jj <= R; ++jj) {
+      s = fma(c[0][kMaxR - jj], wn[NH * W + i - jj], s);
+      s = fma(c[0][kMaxR + jj], wn[NH * W + i + jj], s);
+    }
     acc[i] = s;
   }
 #pragma unroll
   for (int jj = 1; jj <= NY; ++jj) {
     const T *me = reinterpret_cast<const T *>(&ym[jj - 1]), *pe = reinterpret_cast<const T *>(&yp[jj - 1]);
 #pragma unroll
-    for (int i = 0; i < W; ++i) acc[i] += c[1][kMaxR - jj] * me[i] + c[1][kMaxR + jj] * pe[i];
+    for (int i = 0; i < W; ++i) acc[i] = fma(c[1][kMaxR + jj], pe[i], fma(c[1][kMaxR - jj], me[i], acc[i]));
   }
 #pragma unroll
   for (int jj = 1; jj <= NZ; ++jj) {
     const T *me = reinterpret_cast<const T *>(&zm[jj - 1]), *pe = reinterpret_cast<const T *>(&zp[jj - 1]);
 #pragma unroll
-    for (int i = 0; i < W; ++i) acc[i] += c[2][kMaxR - jj] * me[i] + c[2][kMaxR + jj] * pe[i];
+    for (int i = 0; i < W; ++i) acc[i] = fma(c[2][kMaxR + jj], pe[i], fma(c[2][kMaxR - jj], me[i], acc[i]));
   }
   T *oe = reinterpret_cast<T *>(&wout);
 #pragma unroll

@@ -99,8 +99,8 @@ __device__ __forceinline__ TC oc_apply_A(const OnChipDesc &d, const OcShared &sh
       qm += (qm < 0) ? len : 0;
       int qp = c + j;
       qp -= (qp >= len) ? len : 0;
-      acc += coef_of<TC>(sh, dd, kMaxR - j) * (TC)x[base + qm * stride] +
-             coef_of<TC>(sh, dd, kMaxR + j) * (TC)x[base + qp * stride];
+      acc = fma(coef_of<TC>(sh, dd, kMaxR - j), (TC)x[base + qm * stride], acc);
+      acc = fma(coef_of<TC>(sh, dd, kMaxR + j), (TC)x[base + qp * stride], acc);
     }
   }
   return acc;

@@ -25,7 +25,8 @@ __device__ __forceinline__ TC stencil_point(const TI *__restrict__ x, const TC (
   for (int j = 1; j <= R; ++j) {
     int xm = ix - j; xm += (xm < 0) ? nx : 0;
     int xp = ix + j; xp -= (xp >= nx) ? nx : 0;
-    acc += c[0][R - j] * (TC)__ldg(x + base + xm) + c[0][R + j] * (TC)__ldg(x + base + xp);
+    acc = fma(c[0][R - j], (TC)__ldg(x + base + xm), acc);
+    acc = fma(c[0][R + j], (TC)__ldg(x + base + xp), acc);
   }
   if (NDIM >= 2) {
     const int64_t rowx = (int64_t)iz * plane + ix;
@@ -33,8 +34,8 @@ __device__ __forceinline__ TC stencil_point(const TI *__restrict__ x, const TC (
     for (int j = 1; j <= R; ++j) {
       int ym = iy - j; ym += (ym < 0) ? ny : 0;
       int yp = iy + j; yp -= (yp >= ny) ? ny : 0;
-      acc += c[1][R - j] * (TC)__ldg(x + rowx + (int64_t)ym * nx) +
-             c[1][R + j] * (TC)__ldg(x + rowx + (int64_t)yp * nx);
+      acc = fma(c[1][R - j], (TC)__ldg(x + rowx + (int64_t)ym * nx), acc);
+      acc = fma(c[1][R + j], (TC)__ldg(x + rowx + (int64_t)yp * nx), acc);
     }
   }
   if (NDIM >= 3) {
@@ -43,8 +44,8 @@ __device__ __forceinline__ TC stencil_point(const TI *__restrict__ x, const TC (
     for (int j = 1; j <= R; ++j) {
       int zm = iz - j; zm += (zm < 0) ? nz : 0;
       int zp = iz + j; zp -= (zp >= nz) ? nz : 0;
-      acc += c[2][R - j] * (TC)__ldg(x + colx + (int64_t)zm * plane) +
-             c[2][R + j] * (TC)__ldg(x + colx + (int64_t)zp * plane);
+      acc = fma(c[2][R - j], (TC)__ldg(x + colx + (int64_t)zm * plane), acc);
+      acc = fma(c[2][R + j], (TC)__ldg(x + colx + (int64_t)zp * plane), acc);
     }
   }
   return acc;
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(kThreads) k_stencil_vec(InRef<T> xref, OutRef<
     for (int i = 0; i < W; ++i) {
       T a = c[0][R] * win[NH * W + i];
 #pragma unroll
-      for (int j = 1; j <= R; ++j) a += c[0][R - j] * win[NH * W + i - j] + c[0][R + j] * win[NH * W + i + j];
+      for (int j = 1; j <= R; ++j) a = fma(c[0][R + j], win[NH * W + i + j], fma(c[0][R - j], win[NH * W + i - j], a));
       acc[i] = a;
     }
     if (NDIM >= 2) {
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(kThreads) k_stencil_vec(InRef<T> xref, OutRef<
         vload<T, W>(x + iz * plane + ym * nx + xv * W, tm);
         vload<T, W>(x + iz * plane + yp * nx + xv * W, tp);
 #pragma unroll
-        for (int i = 0; i < W; ++i) acc[i] += c[1][R - j] * tm[i] + c[1][R + j] * tp[i];
+        for (int i = 0; i < W; ++i) acc[i] = fma(c[1][R + j], tp[i], fma(c[1][R - j], tm[i], acc[i]));
       }
     }
     if (NDIM >= 3) {
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(kThreads) k_stencil_vec(InRef<T> xref, OutRef<
         vload<T, W>(x + zm * plane + iy * nx + xv * W, tm);
         vload<T, W>(x + zp * plane + iy * nx + xv * W, tp);
 #pragma unroll
-        for (int i = 0; i < W; ++i) acc[i] += c[2][R - j] * tm[i] + c[2][R + j] * tp[i];
+        for (int i = 0; i < W; ++i) acc[i] = fma(c[2][R + j], tp[i], fma(c[2][R - j], tm[i], acc[i]));
       }
     }
     using VT = typename SVec<T>::type;
@@ -562,7 +563,7 @@ __global__ void __launch_bounds__(kTileXV * kTileY, 2) k_stencil_3d(InRef<T> xre
       for (int i = 0; i < W; ++i) {
         T a = c(0, R) * win[NH * W + i];
 #pragma unroll
-        for (int j = 1; j <= R; ++j) a += c(0, R - j) * win[NH * W + i - j] + c(0, R + j) * win[NH * W + i + j];
+        for (int j = 1; j <= R; ++j) a = fma(c(0, R + j), win[NH * W + i + j], fma(c(0, R - j), win[NH * W + i - j], a));
         acc[i] = a;
       }
 #pragma unroll
@@ -570,14 +571,14 @@ __global__ void __launch_bounds__(kTileXV * kTileY, 2) k_stencil_3d(InRef<T> xre
         const VT tm = slot[(ty + R - j) * SX + tx + NH], tp = slot[(ty + R + j) * SX + tx + NH];
         const T *me = reinterpret_cast<const T *>(&tm), *pe = reinterpret_cast<const T *>(&tp);
 #pragma unroll
-        for (int i = 0; i < W; ++i) acc[i] += c(1, R - j) * me[i] + c(1, R + j) * pe[i];
+        for (int i = 0; i < W; ++i) acc[i] = fma(c(1, R + j), pe[i], fma(c(1, R - j), me[i], acc[i]));
       }
 #pragma unroll
       for (int j = 1; j <= R; ++j) {
         const T *me = reinterpret_cast<const T *>(&q[(u + R - j + QL) % QL]);
         const T *pe = reinterpret_cast<const T *>(&q[(u + R + j) % QL]);
 #pragma unroll
-        for (int i = 0; i < W; ++i) acc[i] += c(2, R - j) * me[i] + c(2, R + j) * pe[i];
+        for (int i = 0; i < W; ++i) acc[i] = fma(c(2, R + j), pe[i], fma(c(2, R - j), me[i], acc[i]));
       }
       VT out;
       T *oe = reinterpret_cast<T *>(&out);
