@@ -370,69 +370,233 @@ __device__ __forceinline__ LevelApply<T> stage_up(const LevelApply<T> &L, T *sm,
   return S;
 }
 
-// Level 0 down: the CTA's rows of v (times *scale) and its groups' factors staged in shared
-// memory, one group per thread (NT groups per CTA).
+// Level 0 down: the CTA's rows of v (times *scale) through a shared-memory tile (coalesced),
+// one group per thread.  The factor blocks are streamed: every thread keeps a private ring of kRing block
+// slots in shared memory (interleaved by thread, element e of slot r at (r B^2 + e) NT + t) and
+// fills it with 4- or 8-byte asynchronous copies of its own group's blocks, in the order
+// the sweep uses them, kRing-1 blocks ahead of the one it consumes.  No thread reads another's
+// slots, so the stream needs no barrier; the ring is small, so many more groups (threads) are
+// resident per SM than when a group's whole factor set is staged first.
+constexpr int kRing = 4;
+
 template <typename T, int B, int NT>
-__global__ void __launch_bounds__(NT) k_down0(const T *__restrict__ v, const double *scale, const int *active,
-                                              LevelApply<T> L, int64_t n) {
+__device__ __forceinline__ void ring_stage(T *ring, int r, const T *arr, int i, int G, int g) {
+  constexpr int BB = B * B;
+#pragma unroll
+  for (int e = 0; e < BB; ++e) cp_async_elem(ring + ((r % kRing) * BB + e) * NT + threadIdx.x, arr + gi(i, e, G, g, BB));
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void ring_commit_empty() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <typename T, int B, int NT>
+__device__ __forceinline__ void ring_take(const T *ring, int r, T (&m)[B][B]) {
+  constexpr int BB = B * B;
+  // kRing-1 blocks were staged ahead of this one: the copies of the kRing-2 newest may still
+  // be in flight, this block's (the oldest outstanding group) must have landed
+  asm volatile("cp.async.wait_group %0;" ::"n"(kRing - 2) : "memory");
+#pragma unroll
+  for (int rr = 0; rr < B; ++rr)
+#pragma unroll
+    for (int c = 0; c < B; ++c) m[rr][c] = ring[((r % kRing) * BB + rr * B + c) * NT + threadIdx.x];
+}
+
+template <typename T, int B>
+__device__ __forceinline__ void mat_sub(T (&y)[B], const T (&m)[B][B], const T (&x)[B]) {
+#pragma unroll
+  for (int r = 0; r < B; ++r) {
+    T s = y[r];
+#pragma unroll
+    for (int c = 0; c < B; ++c) s -= m[r][c] * x[c];
+    y[r] = s;
+  }
+}
+template <typename T, int B>
+__device__ __forceinline__ void mat_vec(T (&y)[B], const T (&m)[B][B], const T (&x)[B]) {
+#pragma unroll
+  for (int r = 0; r < B; ++r) {
+    T s = (T)0;
+#pragma unroll
+    for (int c = 0; c < B; ++c) s += m[r][c] * x[c];
+    y[r] = s;
+  }
+}
+
+// The down sweep's blocks in order of use: Mul[1..Q-1], then Minv[Q-1], Up[Q-2], Minv[Q-2],
+// ..., Up[0], Minv[0], then LoSep, UpSepPrev (3Q blocks).
+template <typename T, int B, int Q>
+__device__ __forceinline__ void down_seq(const LevelApply<T> &L, int k, const T *&arr, int &i) {
+  if (k < Q - 1) { arr = L.Mul; i = k + 1; return; }
+  const int k1 = k - (Q - 1);
+  if (k1 < 2 * Q - 1) {
+    const int j = (k1 + 1) / 2;
+    if (k1 & 1) { arr = L.Up; i = Q - 1 - j; }
+    else { arr = L.Minv; i = Q - 1 - j; }
+    return;
+  }
+  if (k1 == 2 * Q - 1) { arr = L.LoSep; i = 0; return; }
+  arr = L.UpSepPrev;
+  i = 0;
+}
+
+template <typename T, int B, int NT>
+__global__ void __launch_bounds__(NT) k_down0s(const T *__restrict__ v, const double *scale, const int *active,
+                                               LevelApply<T> L, int64_t n) {
   if (active && *active == 0) return;
-  constexpr int SPAN = (kQ0 + 1) * B;
+  constexpr int Q = kQ0;
+  constexpr int SPAN = (Q + 1) * B;
   constexpr int PITCH = SPAN + 1;
+  constexpr int NSEQ = 3 * Q;
   __shared__ T tile[NT * PITCH];
-  extern __shared__ __align__(16) unsigned char bsm[];
+  __shared__ T ring[kRing * B * B * NT];
   const int g0 = blockIdx.x * NT;
   const int g = g0 + threadIdx.x;
-  const LevelApply<T> S = stage_down<T, B>(L, reinterpret_cast<T *>(bsm), kQ0, g, NT);
+  const int G = L.G;
+  const bool mine = g < G;
+  if (mine)
+#pragma unroll
+    for (int k = 0; k < kRing - 1; ++k) {
+      const T *arr;
+      int i;
+      down_seq<T, B, Q>(L, k, arr, i);
+      ring_stage<T, B, NT>(ring, k, arr, i, G, g);
+    }
   const T sc = scale ? (T)(*scale) : (T)1;
   const int64_t row0 = (int64_t)g0 * SPAN;
   for (int e = threadIdx.x; e < NT * SPAN; e += NT) {
     const int64_t row = row0 + e;
     tile[(e / SPAN) * PITCH + (e % SPAN)] = (row < n) ? sc * v[row] : (T)0;
   }
-  cp_async_wait_all();
   __syncthreads();
-  if (g < L.G) {
-    const T *mine = tile + threadIdx.x * PITCH;
-    T f[kQ0][B], sep[B];
+  if (!mine) return;
+  T f[Q][B], sep[B];
+  const T *my = tile + threadIdx.x * PITCH;
 #pragma unroll
-    for (int i = 0; i < kQ0; ++i)
+  for (int i = 0; i < Q; ++i)
 #pragma unroll
-      for (int r = 0; r < B; ++r) f[i][r] = mine[i * B + r];
+    for (int r = 0; r < B; ++r) f[i][r] = my[i * B + r];
 #pragma unroll
-    for (int r = 0; r < B; ++r) sep[r] = mine[kQ0 * B + r];
-    down_group<T, B, kQ0, false>(S, g, f, sep, NT, threadIdx.x);
+  for (int r = 0; r < B; ++r) sep[r] = my[Q * B + r];
+  T m[B][B];
+  int k = 0;
+  auto next = [&]() {
+    ring_take<T, B, NT>(ring, k, m);
+    if (k + kRing - 1 < NSEQ) {
+      const T *arr;
+      int i;
+      down_seq<T, B, Q>(L, k + kRing - 1, arr, i);
+      ring_stage<T, B, NT>(ring, k + kRing - 1, arr, i, G, g);
+    } else {
+      ring_commit_empty();
+    }
+    ++k;
+  };
+  // forward elimination y_i = f_i - Mul_i y_{i-1}
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    next();
+    mat_sub<T, B>(f[i], m, f[i - 1]);
   }
+  // back substitution x_i = Minv_i (y_i - Up_i x_{i+1})
+#pragma unroll
+  for (int i = Q - 1; i >= 0; --i) {
+    if (i < Q - 1) {
+      next();
+      mat_sub<T, B>(f[i], m, f[i + 1]);
+    }
+    next();
+    T x[B];
+    mat_vec<T, B>(x, m, f[i]);
+#pragma unroll
+    for (int r = 0; r < B; ++r) f[i][r] = x[r];
+  }
+#pragma unroll
+  for (int i = 0; i < Q; ++i)
+#pragma unroll
+    for (int r = 0; r < B; ++r) L.p[gi(i, r, G, g, B)] = f[i][r];
+  next();   // LoSep
+  if (G > 1 && g < G - 1) {
+    T c[B];
+    mat_vec<T, B>(c, m, f[Q - 1]);
+#pragma unroll
+    for (int r = 0; r < B; ++r) { L.cR[g * B + r] = -c[r]; L.seprhs[g * B + r] = sep[r]; }
+  }
+  next();   // UpSepPrev
+  if (G > 1 && g > 0) {
+    T c[B];
+    mat_vec<T, B>(c, m, f[0]);
+#pragma unroll
+    for (int r = 0; r < B; ++r) L.cL[g * B + r] = -c[r];
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
-// Level 0 up: x for the CTA's groups staged in shared memory, then written in row order
-// through the epilogue: mode 0 y = x (fixed or ring-column output), mode 1 X += x (FP64).
+// Level 0 up with W and V streamed in order (W_0, V_0, W_1, V_1, ...): x for the CTA's groups
+// goes to the shared-memory tile and is written in row order through the epilogue: mode 0 y = x
+// (fixed or ring-column output), mode 1 X += x (FP64).
 template <typename T, int B, int NT>
-__global__ void __launch_bounds__(NT) k_up0(const int *active, LevelApply<T> L, const T *solnext, OutRef<T> yref,
-                                            double *X, int mode, int64_t n) {
+__global__ void __launch_bounds__(NT) k_up0s(const int *active, LevelApply<T> L, const T *solnext, OutRef<T> yref,
+                                             double *X, int mode, int64_t n) {
   if (active && *active == 0) return;
-  constexpr int SPAN = (kQ0 + 1) * B;
+  constexpr int Q = kQ0;
+  constexpr int SPAN = (Q + 1) * B;
   constexpr int PITCH = SPAN + 1;
+  constexpr int NSEQ = 2 * Q;
   __shared__ T tile[NT * PITCH];
-  extern __shared__ __align__(16) unsigned char bsm[];
+  __shared__ T ring[kRing * B * B * NT];
   const int g0 = blockIdx.x * NT;
   const int g = g0 + threadIdx.x;
-  const LevelApply<T> S = stage_up<T, B>(L, reinterpret_cast<T *>(bsm), kQ0, g, NT);
-  cp_async_wait_all();
-  __syncthreads();
-  if (g < L.G) {
-    T *mine = tile + threadIdx.x * PITCH;
-    auto out = [&](int i, int r, T v) { mine[i * B + r] = v; };
-    up_group<T, B, kQ0, false>(S, g, solnext, out, NT, threadIdx.x);
+  const int G = L.G;
+  const bool mine = g < G;
+  const bool spikes = G > 1;
+  if (mine && spikes)
+#pragma unroll
+    for (int k = 0; k < kRing - 1; ++k) ring_stage<T, B, NT>(ring, k, (k & 1) ? L.Vs : L.W, k >> 1, G, g);
+  if (mine) {
+    T sl[B], sr[B];
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+      sl[r] = (g > 0) ? solnext[(g - 1) * B + r] : (T)0;
+      sr[r] = (g < G - 1) ? solnext[g * B + r] : (T)0;
+    }
+    T *my = tile + threadIdx.x * PITCH;
+    T m[B][B];
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      T x[B];
+#pragma unroll
+      for (int r = 0; r < B; ++r) x[r] = L.p[gi(i, r, G, g, B)];
+      if (spikes) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          ring_take<T, B, NT>(ring, k, m);
+          if (k + kRing - 1 < NSEQ) {
+            const int kk = k + kRing - 1;
+            ring_stage<T, B, NT>(ring, kk, (kk & 1) ? L.Vs : L.W, kk >> 1, G, g);
+          } else {
+            ring_commit_empty();
+          }
+          ++k;
+          mat_sub<T, B>(x, m, h == 0 ? sl : sr);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < B; ++r) my[i * B + r] = x[r];
+    }
+    if (g < G - 1)
+#pragma unroll
+      for (int r = 0; r < B; ++r) my[Q * B + r] = sr[r];
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
   }
   __syncthreads();
   const int64_t row0 = (int64_t)g0 * SPAN;
   T *y = (mode == 0) ? yref.get() : nullptr;
   for (int e = threadIdx.x; e < NT * SPAN; e += NT) {
     const int64_t row = row0 + e;
-    if (row < n && (g0 + e / SPAN) < L.G) {
-      const T v = tile[(e / SPAN) * PITCH + (e % SPAN)];
-      if (mode == 0) y[row] = v;
-      else X[row] += (double)v;
+    if (row < n && (g0 + e / SPAN) < G) {
+      const T val = tile[(e / SPAN) * PITCH + (e % SPAN)];
+      if (mode == 0) y[row] = val;
+      else X[row] += (double)val;
     }
   }
 }
@@ -773,18 +937,13 @@ static void bind_apply_t(const std::vector<LevelShape> &lv, int b, char *&p, con
   }
 }
 
-// Groups per CTA of the level-0 kernels: 64 in FP32, 32 in FP64 (the staged factors of a
-// CTA then take the same ~107 KB of shared memory).
+// Groups (threads) per CTA of the level-0 kernels: 64 in FP32, 32 in FP64 (a CTA's block ring
+// and input tile then take the same ~26 KB of static shared memory).
 template <typename T>
 constexpr int level0_cta() { return sizeof(T) == 4 ? 64 : 32; }
 
 template <typename T, int B>
 static void set_apply_attrs() {
-  constexpr int NT = level0_cta<T>();
-  cudaFuncSetAttribute(k_down0<T, B, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)(down_stage_elems(kQ0, B, NT) * sizeof(T)));
-  cudaFuncSetAttribute(k_up0<T, B, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)(up_stage_elems(kQ0, B, NT) * sizeof(T)));
   cudaFuncSetAttribute(k_down_level<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)(down_stage_elems(kQ, B, kLevelCta) * sizeof(T)));
   cudaFuncSetAttribute(k_up_level<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -850,7 +1009,7 @@ static void apply_b(const BandSolver &bs, const std::vector<LevelApply<T>> &a, c
   constexpr int NT = level0_cta<T>();
   const int L = (int)a.size();
   const int g0 = (a[0].G + NT - 1) / NT;
-  k_down0<T, B, NT><<<g0, NT, down_stage_elems(kQ0, B, NT) * sizeof(T), s>>>(v, scale, active, a[0], bs.n);
+  k_down0s<T, B, NT><<<g0, NT, 0, s>>>(v, scale, active, a[0], bs.n);
   const int tf = bs.tail_first;
   for (int l = 1; l < tf && l < L; ++l)
     k_down_level<T, B><<<(a[l].G + kLevelCta - 1) / kLevelCta, kLevelCta, down_stage_elems(kQ, B, kLevelCta) * sizeof(T),
@@ -859,8 +1018,7 @@ static void apply_b(const BandSolver &bs, const std::vector<LevelApply<T>> &a, c
   for (int l = std::min(tf, L) - 1; l >= 1; --l)
     k_up_level<T, B><<<(a[l].G + kLevelCta - 1) / kLevelCta, kLevelCta, up_stage_elems(kQ, B, kLevelCta) * sizeof(T),
                        s>>>(active, a[l], a[l + 1].sol);
-  k_up0<T, B, NT><<<g0, NT, up_stage_elems(kQ0, B, NT) * sizeof(T), s>>>(active, a[0], L > 1 ? a[1].sol : nullptr, y,
-                                                                         X, mode, bs.n);
+  k_up0s<T, B, NT><<<g0, NT, 0, s>>>(active, a[0], L > 1 ? a[1].sol : nullptr, y, X, mode, bs.n);
 }
 
 template <typename T>
