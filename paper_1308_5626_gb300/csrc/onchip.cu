@@ -35,6 +35,7 @@ constexpr double kOcBreakdownRel = 1e-14;
 constexpr int kOcChunk = 16;   // projections reduced together
 constexpr int kOcMaxWarps = 32;
 constexpr int kOcLdH = kMaxM + 1;
+constexpr int kOcMaxLevels = 16;   // levels of a cached slot (small systems have a handful)
 
 struct OcShared {
   double H[kOcLdH * kMaxM];   // rotated Hessenberg, column-major
@@ -46,7 +47,11 @@ struct OcShared {
   double scal[4];
   double sv[8];   // cyclic correction: K^{-1} y(C)
   int flag[4];
+  double levbuf[kOcMaxLevels * 16];   // level descriptors of the cached factors (LevelApply)
 };
+
+static_assert(sizeof(LevelApply<double>) <= 16 * sizeof(double) && sizeof(LevelApply<float>) <= 16 * sizeof(double),
+              "a level descriptor fits its slot of OcShared::levbuf");
 
 template <typename T> __device__ __forceinline__ T coef_of(const OcShared &sh, int d, int j);
 template <> __device__ __forceinline__ double coef_of<double>(const OcShared &sh, int d, int j) { return sh.coef[d][j]; }
@@ -108,9 +113,8 @@ __device__ __forceinline__ TC oc_apply_A(const OnChipDesc &d, const OcShared &sh
 
 // Banded solve N_b^{-1} v of the partitioned factorisation (all levels in this CTA):
 // y = solution (y != nullptr) or X += solution.
-template <typename T, int B>
-__device__ void oc_band_solve(const OnChipDesc &d, const T *v, T *y, double *X) {
-  const LevelApply<T> *lev = reinterpret_cast<const LevelApply<T> *>(d.lev);
+template <typename T, int B, bool RO>
+__device__ void oc_band_solve(const OnChipDesc &d, const LevelApply<T> *lev, const T *v, T *y, double *X) {
   const int L = d.nlev;
   constexpr int SPAN = (kQ0 + 1) * B;
   const int G0 = lev[0].G;
@@ -129,18 +133,18 @@ __device__ void oc_band_solve(const OnChipDesc &d, const T *v, T *y, double *X) 
       const int row = row0 + kQ0 * B + r;
       sep[r] = row < d.n ? v[row] : (T)0;
     }
-    down_group<T, B, kQ0, true>(lev[0], g, f, sep, G0, g);
+    down_group<T, B, kQ0, RO>(lev[0], g, f, sep, G0, g);
   }
   __syncthreads();
   for (int l = 1; l < L; ++l) {
     const int G = lev[l].G;
-    for (int g = threadIdx.x; g < G; g += blockDim.x) down_level_group<T, B, true>(lev[l], lev[l - 1], g, G, g);
+    for (int g = threadIdx.x; g < G; g += blockDim.x) down_level_group<T, B, RO>(lev[l], lev[l - 1], g, G, g);
     __syncthreads();
   }
   for (int l = L - 1; l >= 1; --l) {
     const int G = lev[l].G;
     const T *solnext = (l + 1 < L) ? lev[l + 1].sol : nullptr;
-    for (int g = threadIdx.x; g < G; g += blockDim.x) up_level_group<T, B, true>(lev[l], solnext, g, G, g);
+    for (int g = threadIdx.x; g < G; g += blockDim.x) up_level_group<T, B, RO>(lev[l], solnext, g, G, g);
     __syncthreads();
   }
   const T *sol1 = L > 1 ? lev[1].sol : nullptr;
@@ -153,7 +157,7 @@ __device__ void oc_band_solve(const OnChipDesc &d, const T *v, T *y, double *X) 
         else X[row] += (double)val;
       }
     };
-    up_group<T, B, kQ0, true>(lev[0], g, sol1, out, G0, g);
+    up_group<T, B, kQ0, RO>(lev[0], g, sol1, out, G0, g);
   }
   __syncthreads();
 }
@@ -163,7 +167,8 @@ __device__ __forceinline__ int oc_corner(int n, int b, int c) { return c < b ? n
 // y = N^{-1} v (y != nullptr) or X += N^{-1} v; N = I without a preconditioner.  Ends with a
 // CTA barrier.
 template <typename T>
-__device__ void oc_precond(const OnChipDesc &d, OcShared &sh, const T *v, T *y, double *X) {
+__device__ void oc_precond(const OnChipDesc &d, OcShared &sh, const LevelApply<T> *lev, bool cached, const T *v, T *y,
+                           double *X) {
   if (!d.lev) {
     for (int r = threadIdx.x; r < d.n; r += blockDim.x) {
       if (y) y[r] = v[r];
@@ -174,11 +179,17 @@ __device__ void oc_precond(const OnChipDesc &d, OcShared &sh, const T *v, T *y, 
   }
   T *yb = d.cyclic ? reinterpret_cast<T *>(d.tmp) : y;
   double *Xb = d.cyclic ? nullptr : X;
-  switch (d.b) {
-    case 1: oc_band_solve<T, 1>(d, v, yb, Xb); break;
-    case 2: oc_band_solve<T, 2>(d, v, yb, Xb); break;
-    case 3: oc_band_solve<T, 3>(d, v, yb, Xb); break;
-    case 4: oc_band_solve<T, 4>(d, v, yb, Xb); break;
+  // factors read through the read-only path from global memory, or plainly from the
+  // shared-memory cache
+  switch (d.b * 2 + (cached ? 1 : 0)) {
+    case 2: oc_band_solve<T, 1, true>(d, lev, v, yb, Xb); break;
+    case 3: oc_band_solve<T, 1, false>(d, lev, v, yb, Xb); break;
+    case 4: oc_band_solve<T, 2, true>(d, lev, v, yb, Xb); break;
+    case 5: oc_band_solve<T, 2, false>(d, lev, v, yb, Xb); break;
+    case 6: oc_band_solve<T, 3, true>(d, lev, v, yb, Xb); break;
+    case 7: oc_band_solve<T, 3, false>(d, lev, v, yb, Xb); break;
+    case 8: oc_band_solve<T, 4, true>(d, lev, v, yb, Xb); break;
+    case 9: oc_band_solve<T, 4, false>(d, lev, v, yb, Xb); break;
     default: break;
   }
   if (!d.cyclic) return;
@@ -277,6 +288,32 @@ __device__ void oc_run(const OnChipDesc &d, OcShared &sh) {
     sh.coef[e / (2 * kMaxR + 1)][e % (2 * kMaxR + 1)] = cv;
     sh.coefF[e / (2 * kMaxR + 1)][e % (2 * kMaxR + 1)] = (float)cv;
   }
+  // the slot's factor arrays, optionally copied into dynamic shared memory (one 16-byte
+  // chunk per thread and round); the level descriptors then point there
+  const LevelApply<T> *lev = reinterpret_cast<const LevelApply<T> *>(d.lev);
+  const bool cached = d.lev && d.cache_bytes > 0 && d.nlev <= kOcMaxLevels;
+  if (cached) {
+    extern __shared__ __align__(16) unsigned char oc_dyn[];
+    LevelApply<T> *sl = reinterpret_cast<LevelApply<T> *>(sh.levbuf);
+    unsigned char *cur = oc_dyn;
+    const int BB = d.b * d.b;
+    for (int l = 0; l < d.nlev; ++l) {
+      LevelApply<T> L = lev[l];
+      const size_t gq = (size_t)L.G * L.q * BB, gs = (size_t)L.G * BB;
+      const T **arr[7] = {&L.Mul, &L.Minv, &L.Up, &L.W, &L.Vs, &L.LoSep, &L.UpSepPrev};
+      const size_t cnt[7] = {gq, gq, gq, gq, gq, gs, gs};
+      for (int a = 0; a < 7; ++a) {
+        const size_t n16 = (cnt[a] * sizeof(T) + 15) / 16;
+        const uint4 *src = reinterpret_cast<const uint4 *>(*arr[a]);
+        uint4 *dst = reinterpret_cast<uint4 *>(cur);
+        for (size_t e = tid; e < n16; e += NT) dst[e] = __ldg(src + e);
+        *arr[a] = reinterpret_cast<const T *>(cur);
+        cur += n16 * 16;
+      }
+      if (tid == 0) sl[l] = L;
+    }
+    lev = sl;
+  }
   const double tol = st->tol, inner = st->inner_tol;
   int first = st->first;
   double bnorm = st->bnorm, eps_abs = st->eps_abs;
@@ -341,7 +378,7 @@ __device__ void oc_run(const OnChipDesc &d, OcShared &sh) {
       T *vk = V + (int64_t)k * ld, *vn = V + (int64_t)(k + 1) * ld;
       const int col = (hb + 1 + k) % mmax;
       T *pcol = Px + (int64_t)col * ld, *ycol = Py + (int64_t)col * ld;
-      oc_precond<T>(d, sh, vk, pcol, nullptr);
+      oc_precond<T>(d, sh, lev, cached, vk, pcol, nullptr);
       T w0[1] = {(T)0};
       for (int r = tid; r < n; r += NT) {
         const T w = oc_apply_A<T, T>(d, sh, pcol, r);
@@ -412,7 +449,7 @@ __device__ void oc_run(const OnChipDesc &d, OcShared &sh) {
         Z[r] = z;
       }
       __syncthreads();
-      oc_precond<T>(d, sh, Z, nullptr, d.X);
+      oc_precond<T>(d, sh, lev, cached, Z, nullptr, d.X);
     }
     hist_count = hb + 1 + k_end;
     if (status & kStBreakdown) any_brk = kStBreakdown;
@@ -485,13 +522,18 @@ __global__ void __launch_bounds__(kOnChipMaxThreads) k_onchip(const OnChipDesc *
 bool onchip_threads_ok(int threads) { return threads >= 64 && threads <= kOnChipMaxThreads && threads % 32 == 0; }
 
 template <typename T>
-void launch_onchip(const OnChipDesc *descs, int count, int *counter, int threads, int grid, cudaStream_t s) {
+void launch_onchip(const OnChipDesc *descs, int count, int *counter, int threads, int grid, cudaStream_t s,
+                   int cache_bytes) {
   if (count <= 0) return;
+  static const bool attr = [] {   // opt in to the factor cache's dynamic shared memory (once)
+    return cudaFuncSetAttribute(k_onchip<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOnChipCacheMax) ==
+           cudaSuccess;
+  }();
   cudaMemsetAsync(counter, 0, sizeof(int), s);
-  k_onchip<T><<<std::max(1, grid), threads, 0, s>>>(descs, count, counter);
+  k_onchip<T><<<std::max(1, grid), threads, attr ? cache_bytes : 0, s>>>(descs, count, counter);
 }
 
-template void launch_onchip<float>(const OnChipDesc *, int, int *, int, int, cudaStream_t);
-template void launch_onchip<double>(const OnChipDesc *, int, int *, int, int, cudaStream_t);
+template void launch_onchip<float>(const OnChipDesc *, int, int *, int, int, cudaStream_t, int);
+template void launch_onchip<double>(const OnChipDesc *, int, int *, int, int, cudaStream_t, int);
 
 }  // namespace psp

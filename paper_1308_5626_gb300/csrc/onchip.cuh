@@ -40,9 +40,14 @@ struct OnChipDesc {
   const void *smwZ, *smwK;    // cyclic band: Z (n x 2b) and K^{-1} (2b x 2b) in the Krylov precision
   void *tmp;                  // n values: the banded part of a cyclic solve
   int max_cycles;             // cycles this launch may run (1 for a candidate's trial cycle)
-  int pad;
+  int cache_bytes;            // > 0: the slot's factor blocks are staged in this much dynamic
+                              // shared memory once per launch (a single small system)
   OnChipResult *res;
 };
+
+// Dynamic shared memory the factor cache of a slot needs (0 if the slot does not fit
+// kOnChipCacheMax): every factor array of every level, each rounded up to 16 bytes.
+constexpr int kOnChipCacheMax = 160 * 1024;
 
 // Largest system of the on-chip path, and the largest that takes it by default (opts.onchip
 // = -1) when stepped on its own: below it a step's cycle graphs are bound by launch latency.
@@ -59,6 +64,7 @@ inline int onchip_threads_for(int64_t n) {
 // Run the cycles of descs[0..count) (T = float: the mixed form, double: FP64), `grid` CTAs of
 // `threads` threads taking systems from *counter (reset by the launcher).
 template <typename T>
-void launch_onchip(const OnChipDesc *descs, int count, int *counter, int threads, int grid, cudaStream_t s);
+void launch_onchip(const OnChipDesc *descs, int count, int *counter, int threads, int grid, cudaStream_t s,
+                   int cache_bytes = 0);
 
 }  // namespace psp

@@ -907,6 +907,20 @@ OnChipDesc onchip_desc(psp_ctx *h, int which, int max_cycles, OnChipResult *res_
   return d;
 }
 
+// Dynamic shared memory of the on-chip factor cache for h's factor slots (every array of every
+// level rounded up to 16 bytes, as the kernel copies them), or 0 when it exceeds the cache.
+int onchip_cache_bytes(const psp_ctx *h) {
+  const size_t es = h->mixed ? 4 : 8;
+  const size_t BB = (size_t)h->b * h->b;
+  size_t total = 0;
+  if (h->bs.levels.size() > 16) return 0;
+  for (const LevelShape &l : h->bs.levels) {
+    const size_t gq = (size_t)l.G * l.q * BB * es, gs = (size_t)l.G * BB * es;
+    total += 5 * ((gq + 15) / 16 * 16) + 2 * ((gs + 15) / 16 * 16);
+  }
+  return total <= (size_t)kOnChipCacheMax ? (int)total : 0;
+}
+
 Segment segment_of(const OnChipResult &o) {
   Segment sg;
   sg.cycles = o.cycles;
@@ -927,9 +941,12 @@ psp_status run_segment(psp_ctx *h, int which, int max_cycles, Segment *out, int 
   cudaStream_t s = h->stream;
   if (h->onchip) {
     *h->oc_desc_host = onchip_desc(h, which, max_cycles, h->oc_res);
+    // a single system's launch caches its factors in shared memory when they fit
+    const int cache = which > 0 ? onchip_cache_bytes(h) : 0;
+    h->oc_desc_host->cache_bytes = cache;
     PSP_CUDA(cudaMemcpyAsync(h->oc_desc, h->oc_desc_host, sizeof(OnChipDesc), cudaMemcpyHostToDevice, s));
-    if (h->mixed) launch_onchip<float>(h->oc_desc, 1, h->dev_int + 8, h->oc_threads, 1, s);
-    else launch_onchip<double>(h->oc_desc, 1, h->dev_int + 8, h->oc_threads, 1, s);
+    if (h->mixed) launch_onchip<float>(h->oc_desc, 1, h->dev_int + 8, h->oc_threads, 1, s, cache);
+    else launch_onchip<double>(h->oc_desc, 1, h->dev_int + 8, h->oc_threads, 1, s, cache);
     PSP_CUDA(cudaGetLastError());
     PSP_CUDA(cudaMemcpyAsync(h->oc_res_host, h->oc_res, sizeof(OnChipResult), cudaMemcpyDeviceToHost, s));
     PSP_CUDA(host_wait(h, s));
