@@ -60,6 +60,9 @@ enum { PSP_FP64 = 0, PSP_MIXED = 1 };
 #define PSP_FLAG_FACTOR_FAILED 0x8      /* a fitted N had a zero pivot and was dropped */
 #define PSP_FLAG_BREAKDOWN 0x10         /* an Arnoldi breakdown ended a cycle */
 #define PSP_FLAG_FITTED 0x20            /* Algorithm 2 fitted a candidate N after this step */
+#define PSP_FLAG_DF_RESTART 0x40        /* mixed form: a cycle's restart residual r = B - A X_0 was
+                                           computed in double-float FP32 pairs (about 48 bits;
+                                           taken when tol >= 2^-42 sum|coefficients of A|) */
 
 /* Periodic grid of Eq. 1: ndim in {1,2,3}, n[d] points on [0, length[d]), h = length/n. */
 typedef struct {
@@ -196,7 +199,8 @@ const char *psp_last_error(void);
  * Algorithm 2 fit of a candidate N for the next step (not made while the acceptance
  * rule's back-off keeps the next step from trying a candidate).  u_n and u_np1 are device arrays
  * of n doubles and must not overlap.  `info` (host) may be NULL.  The history persists
- * across steps while dt is unchanged and is cleared when dt changes.
+ * across steps while dt is unchanged and is cleared when dt changes.  The work runs on the
+ * handle's stream and u_np1 is complete when the call returns.
  * Returns PSP_ERR_NOCONV after max_restarts cycles (u_np1 = last iterate).
  */
 psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, double tol,

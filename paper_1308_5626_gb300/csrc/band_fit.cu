@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "dfloat.cuh"
 #include "psp_kernels.cuh"
 
 namespace psp {
@@ -122,36 +123,6 @@ constexpr int kFm2Rows = 2 * kFm2Threads;        // rows per CTA
 constexpr int kFm2Cols = 8;                      // history columns per staged chunk
 constexpr int kFm2Lead = 4;                      // staged rows before the CTA's first row (>= B, 16-byte aligned)
 constexpr int kFm2Span = kFm2Rows + 12;          // staged P_x rows: r0-4 .. r0+kFm2Rows+7 (covers i+1+2B for B <= 4)
-
-__device__ __forceinline__ uint64_t f2pack(float a, float b) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void f2unpack(uint64_t v, float &a, float &b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ uint64_t f2mul(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ uint64_t f2fma(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ uint64_t f2add(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ uint64_t f2sub(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ uint64_t f2neg(uint64_t a) { return a ^ 0x8000000080000000ull; }
 
 // A pair of double-float accumulators (hi, lo packed per row).
 struct Acc2 {

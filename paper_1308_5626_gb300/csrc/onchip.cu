@@ -484,6 +484,7 @@ __device__ void oc_run(const OnChipDesc &d, OcShared &sh) {
     res.k_last = k_last;
     res.first_k = first_k < 0 ? 0 : first_k;
     res.error = st->error;
+    res.hist_count = hist_count;
     res.first_beta = first_beta;
     res.last_beta = last_beta;
     res.last_R = last_R;

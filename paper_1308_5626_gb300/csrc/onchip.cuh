@@ -14,6 +14,7 @@ struct OnChipResult {
   int k_last;         // iterations of the last cycle
   int first_k;        // iterations of the first cycle
   int error;          // device error flag (a misconfigured launch)
+  int hist_count;     // history columns written since the history was cleared, after the launch
   double first_beta;  // ||B - A X_0|| at the start of the first cycle
   double last_beta;   // ... of the last cycle
   double last_R;      // R(k_last) of the last cycle (its beta if k_last == 0)

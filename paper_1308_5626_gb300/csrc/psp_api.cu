@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <type_traits>
 #include <atomic>
 #include <mutex>
 #include <chrono>
@@ -145,6 +146,7 @@ struct psp_ctx {
   cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};   // [0] N = I, [1] slot 0, [2] slot 1
   int graph_kernels[3] = {0, 0, 0};                          // kernel nodes per graph
   bool profiling = false;
+  bool restart_df_ok = false;        // the mixed cycle graphs hold the double-float restart
   cudaEvent_t ev[3][kMaxM][6] = {};                          // profiling events per graph
   psp_profile prof{};
   double *hostbuf = nullptr;   // pinned staging for psp_step_host
@@ -194,7 +196,14 @@ void enqueue_cycle(psp_ctx *h, int slot, cudaStream_t s) {
   T *Py = reinterpret_cast<T *>(h->Py);
   T *Z = reinterpret_cast<T *>(h->Z);
   const Geometry &g = h->geo;
-  launch_restart<T, T>(g, h->X, h->B, Px, Py, h->ld, V, h->st, h->partial, h->mixed ? 1 : 0, s);
+  if constexpr (std::is_same<T, float>::value) {
+    // columns 1 and 2 of the basis are free until the first iteration writes v_1
+    float *Xh = h->m >= 2 ? V + h->ld : nullptr;
+    h->restart_df_ok =
+        launch_restart_mixed(g, h->X, h->B, Px, Py, h->ld, V, Xh, Xh ? Xh + h->ld : nullptr, h->st, h->partial, s);
+  } else {
+    launch_restart<T, T>(g, h->X, h->B, Px, Py, h->ld, V, h->st, h->partial, h->mixed ? 1 : 0, s);
+  }
   const int *active = &h->st->active;
   const int which = slot + 1;
   // iteration j: Y_j = N^{-1} v_j -> P_x ring column hist_base+1+j, w_j = A Y_j -> P_y column,
@@ -334,6 +343,35 @@ psp_status fit_into(psp_ctx *h, const TH *Px, const TH *Py, int64_t ld, int M, d
   PSP_CUDA(cudaMemcpyAsync(h->int_host + 1, h->dev_int + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   PSP_CUDA(host_wait(h, h->stream));
   if (singular) *singular = h->int_host[1];
+  return PSP_OK;
+}
+
+// Algorithm 2's fit of the candidate band (into band_cand) from the first M history columns
+// and its factorisation into slot `slot`, with one host synchronisation for both outcomes:
+// *singular = the fit's degenerate rows; PSP_ERR_NUMERIC if a pivot (or the cyclic band's
+// capacitance matrix) failed.
+template <typename TH>
+psp_status fit_and_factor(psp_ctx *h, const TH *Px, const TH *Py, int M, int slot, int *singular) {
+  PSP_CUDA(cudaMemsetAsync(h->dev_int, 0, 2 * sizeof(int), h->stream));
+  launch_fit<TH>(h->b, h->opts.intercept, h->geo.n, M, Px, Py, h->ld, h->moments, h->band_cand, h->dev_int + 1,
+                 h->stream, h->opts.cyclic);
+  {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(PSP_ERR_CUDA, std::string("band fit launch: ") + cudaGetErrorString(e));
+  }
+  h->bs.factor(slot, h->band_cand, h->dev_int, h->stream);
+  {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(PSP_ERR_CUDA, std::string("band factorisation launch: ") + cudaGetErrorString(e));
+  }
+  PSP_CUDA(cudaMemcpyAsync(h->int_host, h->dev_int, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  PSP_CUDA(host_wait(h, h->stream));
+  *singular = h->int_host[1];
+  if (h->int_host[0]) return fail(PSP_ERR_NUMERIC, "band factorisation: zero or non-finite pivot");
+  if (h->bs.cyclic && !h->bs.prepare_cyclic(slot, h->band_cand, h->stream)) {
+    cudaGetLastError();
+    return fail(PSP_ERR_NUMERIC, "cyclic band: singular capacitance matrix");
+  }
   return PSP_OK;
 }
 
@@ -662,6 +700,8 @@ namespace {
 // max_cycles cycles) as the step's host logic sees it.
 struct Segment {
   int cycles = 0, iters = 0, k_last = 0, status = 0, error = 0;
+  bool df_restart = false;   // the cycle's restart ran in double-float
+  int hist_count = 0;        // DevState::hist_count after the segment
   double beta_first = 0.0, beta_last = 0.0, R_last = 0.0, bnorm = 0.0;
 };
 
@@ -678,6 +718,7 @@ struct StepRun {
   double trial_beta = -1.0, trial_R = 0.0, main_beta = -1.0, main_R = 0.0;
   int trial_iters = 0, main_iters = 0;
   int hist_before_trial = 0, prev_adopted = -1;
+  int hist_count = 0;        // DevState::hist_count as of the last segment (or the rollback)
   bool adopted_now = false;
   psp_status status = PSP_OK;
 };
@@ -703,6 +744,13 @@ psp_status step_begin(psp_ctx *h, StepRun &r, const double *u_n, double *u_np1, 
   set_coef(h, dt, h->st_host->coef);
   h->st_host->tol = tol;
   h->st_host->first = 1;
+  // the mixed form's restart residual in double-float (about 2^-45 sum|c| |x| of rounding)
+  // when tol is well above it, else in FP64
+  double csum = 0.0;
+  for (int d = 0; d < 3; ++d)
+    for (int j = 0; j < 2 * kMaxR + 1; ++j) csum += std::fabs(h->st_host->coef[d][j]);
+  h->st_host->restart_df = (h->mixed && tol >= std::ldexp(csum, -42)) ? 1 : 0;
+  PSP_CUDA(cudaMemcpyAsync(&h->st->restart_df, &h->st_host->restart_df, sizeof(int), cudaMemcpyHostToDevice, s));
   PSP_CUDA(cudaMemcpyAsync(h->st->coef, h->st_host->coef, sizeof(h->st_host->coef), cudaMemcpyHostToDevice, s));
   PSP_CUDA(cudaMemcpyAsync(&h->st->tol, &h->st_host->tol, sizeof(double), cudaMemcpyHostToDevice, s));
   PSP_CUDA(cudaMemcpyAsync(&h->st->first, &h->st_host->first, sizeof(int), cudaMemcpyHostToDevice, s));
@@ -714,6 +762,7 @@ psp_status step_begin(psp_ctx *h, StepRun &r, const double *u_n, double *u_np1, 
   r.cur = r.try_cand ? h->cand : h->adopted;
   r.prev_adopted = h->adopted;
   r.hist_before_trial = h->hist_count_host;   // the history length to restore if the trial breaks
+  r.hist_count = h->hist_count_host;
   return PSP_OK;
 }
 
@@ -735,6 +784,8 @@ psp_status step_after_segment(psp_ctx *h, StepRun &r, const Segment &sg, int lau
   r.launches += launches;
   r.c += sg.cycles;
   r.bnorm = sg.bnorm;
+  r.hist_count = sg.hist_count;
+  if (sg.df_restart) r.flags |= PSP_FLAG_DF_RESTART;
   if (sg.error) {
     r.done = true;
     return fail(PSP_ERR_DEVICE, "device error flag " + std::to_string(sg.error) +
@@ -752,6 +803,7 @@ psp_status step_after_segment(psp_ctx *h, StepRun &r, const Segment &sg, int lau
     h->int_host[3] = r.hist_before_trial;
     PSP_CUDA(cudaMemcpyAsync(&h->st->hist_count, h->int_host + 3, sizeof(int), cudaMemcpyHostToDevice, s));
     PSP_CUDA(host_wait(h, s));
+    r.hist_count = r.hist_before_trial;
     if (r.adopted_now) {
       h->adopted = r.prev_adopted;
       h->adopted_version += 1;
@@ -824,33 +876,29 @@ psp_status step_finish(psp_ctx *h, StepRun &r, psp_step_info *info) {
   else if (!r.converged) result = fail(PSP_ERR_NOCONV, "max_restarts reached");
   PSP_CUDA(cudaMemcpyAsync(r.u_np1, h->X, n * 8, cudaMemcpyDeviceToDevice, s));
 
-  // progressive fit of the candidate for the next step (Algorithm 2)
-  int hist = 0;
-  {
-    PSP_CUDA(cudaMemcpyAsync(h->int_host + 2, &h->st->hist_count, sizeof(int), cudaMemcpyDeviceToHost, s));
-    PSP_CUDA(host_wait(h, s));
-    h->hist_count_host = h->int_host[2];
-    hist = std::min(h->int_host[2], h->mmax);
-  }
+  // progressive fit of the candidate for the next step (Algorithm 2); the history length is
+  // the one the last segment's summary reported
+  h->hist_count_host = r.hist_count;
+  const int hist = std::min(r.hist_count, h->mmax);
   const int need = 2 * h->b + (h->opts.intercept ? 2 : 1);
   int singular = 0;
   // a fit is only worth making when the next step tries it: while the acceptance rule's
   // back-off still runs (wait > 0) the next step keeps the adopted N, and the step after
   // it fits afresh from the longer history, so the skipped fit could never be used
   if (!r.numeric && hist >= need && h->wait == 0) {
-    psp_status fs = h->mixed ? fit_into<float>(h, (const float *)h->Px, (const float *)h->Py, h->ld, hist,
-                                               h->band_cand, &singular)
-                             : fit_into<double>(h, (const double *)h->Px, (const double *)h->Py, h->ld, hist,
-                                                h->band_cand, &singular);
-    if (fs != PSP_OK) return fs;
+    const int slot = (h->adopted == 0) ? 1 : 0;
+    psp_status f2 = h->mixed ? fit_and_factor<float>(h, (const float *)h->Px, (const float *)h->Py, hist, slot,
+                                                     &singular)
+                             : fit_and_factor<double>(h, (const double *)h->Px, (const double *)h->Py, hist, slot,
+                                                      &singular);
+    if (f2 != PSP_OK && f2 != PSP_ERR_NUMERIC) return f2;
     r.flags |= PSP_FLAG_FITTED;
     if (singular) r.flags |= PSP_FLAG_SINGULAR_FIT;
-    const int slot = (h->adopted == 0) ? 1 : 0;
     r.launches += 2 + 2 * (int)h->bs.levels.size() - 1;   // fit + factor/assemble per level
-    psp_status f2 = factor_into(h, slot, h->band_cand);
     if (f2 == PSP_OK) h->cand = slot;
-    else if (f2 == PSP_ERR_NUMERIC) { r.flags |= PSP_FLAG_FACTOR_FAILED; h->cand = -1; }
-    else return f2;
+    else { r.flags |= PSP_FLAG_FACTOR_FAILED; h->cand = -1; }
+  } else {
+    PSP_CUDA(host_wait(h, s));   // u_np1 is complete when psp_step returns (the fit's wait covers it)
   }
   h->last_singular = singular;
   if (info) {
@@ -932,6 +980,7 @@ Segment segment_of(const OnChipResult &o) {
   sg.beta_last = o.last_beta;
   sg.R_last = o.last_R;
   sg.bnorm = o.bnorm;
+  sg.hist_count = o.hist_count;
   return sg;
 }
 
@@ -969,6 +1018,8 @@ psp_status run_segment(psp_ctx *h, int which, int max_cycles, Segment *out, int 
   sg.beta_first = sg.beta_last = sm.beta;
   sg.R_last = sm.R_end;
   sg.bnorm = sm.bnorm;
+  sg.hist_count = sm.hist_count;
+  sg.df_restart = h->mixed && h->restart_df_ok && h->st_host->restart_df;
   *out = sg;
   *launches = h->graph_kernels[which];
   return PSP_OK;

@@ -43,7 +43,8 @@ struct DevState {
   int hist_base;     // ring column of the current cycle's restart pair (X_0, A X_0)
   int mmax;          // history ring length
   int m;             // restart length
-  int pad0, pad1;
+  int restart_df;    // 1: the mixed form's restart runs in double-float (k_restart_df), else FP64
+  int pad1;
   double beta;       // ||B - A X_0|| at the start of the cycle
   double eps_abs;    // step bound on R(k): tol * ||B||
   double eps_cycle;  // cycle bound on R(k): eps_abs (FP64) or max(eps_abs, inner*beta)

@@ -108,7 +108,13 @@ void launch_stencil(const Geometry &g, InRef<TI> x, OutRef<TO> y, const DevState
                     const double *scale = nullptr);
 template <typename TH, typename TV>
 void launch_restart(const Geometry &g, const double *X, const double *B, TH *Px, TH *Py, int64_t ldh,
-                    TV *V1, DevState *st, double *partial, int mixed, cudaStream_t s);
+                    TV *V1, DevState *st, double *partial, int mixed, cudaStream_t s,
+                    const int *skip = nullptr);   // skip: the kernel returns at once while *skip != 0
+// The mixed form's restart (FP32 history and basis) with its FP64-grade arithmetic in
+// double-float where the grid allows and DevState::restart_df asks for it (returns whether
+// the double-float kernels were enqueued); Xh, Xl: two scratch columns of n floats.
+bool launch_restart_mixed(const Geometry &g, const double *X, const double *B, float *Px, float *Py, int64_t ldh,
+                          float *V1, float *Xh, float *Xl, DevState *st, double *partial, cudaStream_t s);
 
 // arnoldi.cu
 int arnoldi_grid();   // CTAs of the Gram-Schmidt passes (one per SM)

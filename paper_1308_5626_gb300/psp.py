@@ -26,6 +26,7 @@ PSP_FLAG_CANDIDATE_ACCEPTED = 0x4
 PSP_FLAG_FACTOR_FAILED = 0x8
 PSP_FLAG_BREAKDOWN = 0x10
 PSP_FLAG_FITTED = 0x20
+PSP_FLAG_DF_RESTART = 0x40
 
 STATUS_NAMES = {0: "PSP_OK", 1: "PSP_ERR_ARG", 2: "PSP_ERR_CUDA", 3: "PSP_ERR_OOM", 4: "PSP_ERR_NOCONV",
                 5: "PSP_ERR_NUMERIC", 6: "PSP_ERR_DEVICE"}
@@ -52,6 +53,8 @@ class psp_step_info(ctypes.Structure):
                 ("singular_rows", ctypes.c_int), ("launches", ctypes.c_int)]
 
 
+# kernel classes of psp_profile (index = class)
+PSP_K_PRECOND, PSP_K_STENCIL, PSP_K_CGS1, PSP_K_CGS2, PSP_K_CGS3, PSP_K_COUNT = 0, 1, 2, 3, 4, 5
 PSP_K_NAMES = ["precond", "stencil", "orth_dots", "unused", "orth_update"]
 
 
@@ -61,7 +64,8 @@ class psp_tuning_class(ctypes.Structure):
 
 
 class psp_profile(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 5), ("bytes", ctypes.c_double * 5), ("launches", ctypes.c_int64 * 5)]
+    _fields_ = [("ms", ctypes.c_double * PSP_K_COUNT), ("bytes", ctypes.c_double * PSP_K_COUNT),
+                ("launches", ctypes.c_int64 * PSP_K_COUNT)]
 
 
 # name -> (argtypes)
@@ -442,3 +446,23 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def workload_dt(w) -> float:
+    """A workload's time step: w.dt, or for a spectral-radius rule (rho(L) dt = w.rho_dt)
+    rho = max |lambda| of the library's own stencil of L (psp_get_stencil) over the grid's
+    Fourier modes, lambda(theta) = sum_d sum_j w_dj e^{i j theta_d}."""
+    if w.dt is not None:
+        return float(w.dt)
+    import numpy as np
+    s = Solver(w.shape, w.order, w.terms, w.b, 2, max_hist_cols=4)
+    wst, R = psp_get_stencil(s.handle)
+    s.close()
+    lam = np.zeros(tuple(reversed(w.shape)), dtype=np.complex128)
+    for d, nd in enumerate(w.shape):
+        th = 2.0 * np.pi * np.arange(nd) / nd
+        ld = sum(wst[d][j + R] * np.exp(1j * j * th) for j in range(-R, R + 1))
+        shp = [1] * len(w.shape)
+        shp[len(w.shape) - 1 - d] = nd
+        lam = lam + ld.reshape(shp)
+    return float(w.rho_dt / np.abs(lam).max())

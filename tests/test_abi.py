@@ -41,6 +41,21 @@ def test_binding_covers_the_header():
         assert name in psp._SIGS, name
 
 
+def test_binding_constants_match_the_header():
+    """Every #define PSP_* value of include/psp.h (status codes, precisions, flags) is the
+    binding's constant of the same name."""
+    import os
+    import re
+    from paper_1308_5626_gb300 import psp
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "psp.h")).read()
+    found = re.findall(r"^#define (PSP_[A-Z0-9_]+) +(0x[0-9a-fA-F]+|[0-9]+)\b", hdr, re.M)
+    found += re.findall(r"\b(PSP_[A-Z0-9_]+) = (0x[0-9a-fA-F]+|[0-9]+)\b", hdr)   # enumerators
+    assert len(found) >= 15
+    for name, val in found:
+        assert hasattr(psp, name), name
+        assert getattr(psp, name) == int(val, 0), name
+
+
 def test_default_opts_without_gpu(libpsp):
     from paper_1308_5626_gb300 import psp
     o = psp.psp_default_opts()

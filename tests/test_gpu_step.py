@@ -140,6 +140,45 @@ def test_3d_tiled_stencil_steps(dev, precision, onchip):
     s.close()
 
 
+@pytest.mark.parametrize("w", [inputs.c1(1000), inputs.c2(48, 40), inputs.c2(45, 40), inputs.c3(16, kmax=4),
+                               _box3d()], ids=lambda w: w.name)
+def test_mixed_restart_double_float(dev, w):
+    """The mixed form's restart residual r = B - A X_0 in double-float FP32 pairs (rows of
+    whole 16-byte vectors, nx % 4 == 0) or in FP64 (nx = 45).  At tol 1e-10 the steps flag
+    PSP_FLAG_DF_RESTART exactly where the grid takes it and meet the FP64 form's bounds:
+    cond(A) 2 tol in the 2-norm and the element-wise bound.  At tol 1e-13, below the
+    double-float rounding (2^-42 sum|c| is about 2e-11 here), the FP64 restart runs and the
+    step still meets cond(A) 2 tol; the FP64 form never takes the double-float restart."""
+    from paper_1308_5626_gb300 import psp
+    op = Operator(w.shape, w.order, w.terms)
+    dt = _dt(w, op)
+    kappa = exact.condition_number(op, dt)
+    inv = inv_inf_norm(op, dt)
+    df_grid = w.shape[0] % 4 == 0
+    s = _solver(w, precision=psp.PSP_MIXED, onchip=0)
+    u = t64(w.u0, dev)
+    un = w.u0
+    for step in range(3):
+        u, info = s.step(u, dt, 1e-10)
+        ref = exact.solve_fourier(op, un, dt)
+        got = u.cpu().numpy()
+        assert info.status == 0
+        assert bool(info.flags & psp.PSP_FLAG_DF_RESTART) == df_grid, (step, info.flags)
+        assert rel(got, ref) <= kappa * 2e-10, (step, rel(got, ref))
+        assert rel_max(got, ref) <= elementwise_bound(inv, 1e-10, un, ref), (step, rel_max(got, ref))
+        un = got
+    u, info = s.step(u, dt, 1e-13)
+    ref = exact.solve_fourier(op, un, dt)
+    assert info.status == 0
+    assert not (info.flags & psp.PSP_FLAG_DF_RESTART)
+    assert rel(u.cpu().numpy(), ref) <= kappa * 2e-13
+    s.close()
+    s = _solver(w, precision=psp.PSP_FP64, onchip=0)
+    _, info = s.step(t64(w.u0, dev), dt, 1e-10)
+    assert info.status == 0 and not (info.flags & psp.PSP_FLAG_DF_RESTART)
+    s.close()
+
+
 @PATHS
 @pytest.mark.parametrize("w", [inputs.c1(1000), inputs.c3(12, kmax=3)], ids=lambda w: w.name)
 def test_iterations_follow_the_oracle(dev, w, onchip):
