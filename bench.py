@@ -163,33 +163,43 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-# The translation unit of the kernels whose DRAM traffic profiles/traffic.json records (the
-# two Gram-Schmidt passes) and the headers it includes: a change to any of them makes the
-# recorded traffic stale.
-TRAFFIC_SOURCES = ("paper_1308_5626_gb300/csrc/arnoldi.cu", "paper_1308_5626_gb300/csrc/psp_kernels.cuh",
-                   "paper_1308_5626_gb300/csrc/psp_common.cuh", "include/psp.h")
+# The sources of each kernel class whose DRAM traffic profiles/traffic.json records: the
+# translation unit of its kernel and the device header it includes.  A change to their code
+# (comments and blank space aside) makes the recorded traffic stale.
+TRAFFIC_SOURCES = {
+    "orth_dots": ("paper_1308_5626_gb300/csrc/arnoldi.cu", "paper_1308_5626_gb300/csrc/psp_common.cuh"),
+    "orth_update": ("paper_1308_5626_gb300/csrc/arnoldi.cu", "paper_1308_5626_gb300/csrc/psp_common.cuh"),
+    "stencil": ("paper_1308_5626_gb300/csrc/stencil.cu", "paper_1308_5626_gb300/csrc/psp_common.cuh"),
+}
 
 
-def _kernel_source_hash() -> str:
+def _strip_comments(src: str) -> str:
+    import re
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(" ".join(line.split()) for line in src.splitlines() if line.strip())
+
+
+def _kernel_source_hash(kernel: str) -> str:
     h = hashlib.sha256()
-    for f in TRAFFIC_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+    for f in TRAFFIC_SOURCES[kernel]:
+        with open(os.path.join(ROOT, f)) as fh:
+            h.update(_strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
 def _traffic_for(kernel: str, workload: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on
-    the current kernel sources; otherwise None."""
+    the current code of the kernel's sources; otherwise None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(p):
+    if kernel not in TRAFFIC_SOURCES or not os.path.exists(p):
         return None
     with open(p) as fh:
         d = json.load(fh)
-    wl = d.get("kernels", {}).get(workload, {})
-    if wl.get("source_hash", d.get("source_hash")) != _kernel_source_hash():
+    ent = d.get("kernels", {}).get(workload, {}).get(kernel)
+    if not ent or ent.get("source_hash") != _kernel_source_hash(kernel):
         return None
-    return wl.get(kernel)
+    return ent
 
 
 def _dist():
@@ -228,24 +238,10 @@ def aggregate_value(steps: int, world: int, max_ms: float) -> float:
 # --------------------------------------------------------------------------------------
 
 def library_dt(w) -> float:
-    """The workload's time step: w.dt, or for a spectral-radius rule (rho(L) dt = w.rho_dt)
-    rho = max |lambda| of the library's own stencil of L (psp_get_stencil) over the grid's
-    Fourier modes, lambda(theta) = sum_d sum_j w_dj e^{i j theta_d}."""
-    if w.dt is not None:
-        return float(w.dt)
-    import numpy as np
+    """The workload's time step (psp.workload_dt: w.dt, or rho(L) dt = w.rho_dt with rho from
+    the library's own stencil)."""
     from paper_1308_5626_gb300 import psp
-    s = psp.Solver(w.shape, w.order, w.terms, w.b, 2, max_hist_cols=4)
-    wst, R = psp.psp_get_stencil(s.handle)
-    s.close()
-    lam = np.zeros(tuple(reversed(w.shape)), dtype=np.complex128)
-    for d, nd in enumerate(w.shape):
-        th = 2.0 * np.pi * np.arange(nd) / nd
-        ld = sum(wst[d][j + R] * np.exp(1j * j * th) for j in range(-R, R + 1))
-        shp = [1] * len(w.shape)
-        shp[len(w.shape) - 1 - d] = nd
-        lam = lam + ld.reshape(shp)
-    return float(w.rho_dt / np.abs(lam).max())
+    return psp.workload_dt(w)
 
 
 def _time_form(w, precision, steps, warmup, device, world, profile, dt):
@@ -796,14 +792,17 @@ def _roofline(prof, workload, hbm_peak, peak_kind):
         kernels[name]["share_of_profiled"] = prof[name]["ms"] / tot
     if not kernels:
         return None, kernels
+    # DRAM traffic per mean launch: the capture is one launch at one iteration j; traffic
+    # scales with the columns streamed, so it is scaled to the mean launch by its
+    # algorithmic bytes (None without a capture of the class's current code)
+    for name, kd in kernels.items():
+        ent = _traffic_for(name, workload)
+        kd["traffic"] = None
+        if ent and ent.get("algorithmic_bytes"):
+            kd["traffic"] = ent["dram_bytes_per_launch"] / ent["algorithmic_bytes"] * kd["bytes_per_launch"]
     dom = max(kernels, key=lambda k: prof[k]["ms"])
     kd = kernels[dom]
-    ent = _traffic_for(dom, workload)
-    # the capture is one launch at one iteration j; traffic scales with the columns
-    # streamed, so it is scaled to the mean launch by its algorithmic bytes
-    traffic = None
-    if ent and ent.get("algorithmic_bytes"):
-        traffic = ent["dram_bytes_per_launch"] / ent["algorithmic_bytes"] * kd["bytes_per_launch"]
+    traffic = kd["traffic"]
     roof = {"kernel": dom, "bound": "hbm", "achieved": kd["gbs"], "peak": hbm_peak, "unit": "GB/s",
             "frac": kd["gbs"] / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
             "bytes_per_launch": kd["bytes_per_launch"], "ms_per_launch": kd["ms_per_launch"]}
