@@ -126,6 +126,14 @@ typedef struct {
                         CTA per system).  Its Gram-Schmidt is classical applied twice (CGS2).
                         GMRES only (BiCGSTAB handles take the cycle graphs); the profiling mode
                         does not time it. */
+  int cycle_loop;    /* 1 (default): on the captured-graph path the restart loop runs on the
+                        device -- one graph launch runs cycle after cycle (a CUDA graph WHILE
+                        node) until the step converges, a cycle breaks or the segment's cycle
+                        budget is spent, and the host waits once per segment (the acceptance
+                        rule's trial cycle is a segment of one cycle).  0: one graph launch and
+                        one host round trip per restart cycle.  Same iterates either way; the
+                        profiling mode runs per cycle.  Falls back to 0 if the runtime refuses
+                        the conditional graph. */
 } psp_opts;
 
 typedef struct {

@@ -149,7 +149,7 @@ __device__ __forceinline__ void grid_sums(const TP *partial, int nvals, int nb, 
 // R(kk+1) and the finish test; run by one thread with the rotations staged in shared
 // memory (sC, sS, sG hold C, S, G).  Returns true when the cycle ends.
 __device__ bool givens_column(DevState *st, int kk, double *hcol, double *sC, double *sS, double *sG, bool brk,
-                              bool force_end, int mixed) {
+                              bool force_end, int mixed, bool bad = false) {
   const int k = kk + 1;
   for (int i = 0; i < kk; ++i) {   // old rotations
     const double d = hcol[i];
@@ -180,7 +180,7 @@ __device__ bool givens_column(DevState *st, int kk, double *hcol, double *sC, do
   const double R = fabs(gk);
   st->R[kk] = R;
   int status = st->status;
-  if (!isfinite(R) || !isfinite(gamma)) status |= kStNumeric;
+  if (!isfinite(R) || !isfinite(gamma) || bad) status |= kStNumeric;
   if (brk) status |= kStBreakdown;
   if (!mixed && R <= st->eps_abs) status |= kStConverged;
   st->status = status;
@@ -245,10 +245,13 @@ __device__ void dcgs_scalar(DevState *st, int j, int final_step, const T *partia
     if (lane == 0) {
       const T alpha = s_sum[j];
       const T nu2 = alpha - aa;
-      const bool brk = !(nu2 > (T)(kBreakdownRel * kBreakdownRel) * alpha) || !isfinite(nu2);
-      s_sc[0] = brk ? (T)0 : sqrt(nu2);
+      // an overflowed ||w_j|| (a preconditioner whose solve blew up in the Krylov precision)
+      // is a numeric failure (dc_brk = 2), not a breakdown that would end the cycle as converged
+      const bool bad = !isfinite(nu2) || !isfinite(alpha);
+      const bool brk = !bad && !(nu2 > (T)(kBreakdownRel * kBreakdownRel) * alpha);
+      s_sc[0] = (brk || bad) ? (T)0 : sqrt(nu2);
       s_sc[2] = ab;
-      st->dc_brk = brk ? 1 : 0;
+      st->dc_brk = bad ? 2 : (brk ? 1 : 0);
     }
   }
   __syncthreads();
@@ -333,10 +336,17 @@ __device__ void dcgs_givens(DevState *st, int j, int final_step, int mixed, doub
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    const bool brk = st->dc_brk != 0;
+    const bool bad = st->dc_brk == 2;
+    const bool brk = st->dc_brk == 1;
     bool end = false;
     if (j >= 1) {
-      end = givens_column(st, j - 1, s_hcol, sC, sS, sG, brk, final_step != 0, mixed);
+      end = givens_column(st, j - 1, s_hcol, sC, sS, sG, brk, final_step != 0, mixed, bad);
+    } else if (bad) {
+      end = true;   // ||v_0|| overflowed
+      st->status |= kStNumeric;
+      st->sum.status = st->status;
+      st->k_end = 0;
+      st->sum.k_end = 0;
     } else if (brk || final_step) {
       end = true;   // v_0 = 0: nothing to do
       st->k_end = 0;
@@ -825,9 +835,11 @@ template void launch_arnoldi<double>(int, int, int64_t, double *, int64_t, const
 bool fused_matvec_ok(const Geometry &g, int elem_bytes) {
   const int W = 16 / elem_bytes;
   const int nh = (g.R + W - 1) / W;
-  // a 3D grid that the z-marching tiled stencil takes keeps its own matvec kernel: folded,
-  // each vector would gather its 4R+2NH+1 neighbour vectors from L2 one by one
-  if (g.ndim == 3 && stencil_3d_tiled(g, elem_bytes)) return false;
+  // FP32 3D grids fold the matvec too (each vector gathers its 4R+2NH+1 neighbour vectors
+  // from L2, under pass A's stream: measured faster on the 256^3 workload than the z-marching
+  // stencil kernel, which needs its own pass over v and w); the FP64 form, bound by the FP64
+  // pipe, keeps the z-marching kernel on the grids it takes
+  if (g.ndim == 3 && elem_bytes == 8 && stencil_3d_tiled(g, elem_bytes)) return false;
   return g.R >= 1 && g.R <= kMaxR && g.ndim >= 1 && g.ndim <= 3 && g.nx % W == 0 && g.nx / W > nh;
 }
 template void launch_scale_copy<float>(int, int64_t, const float *, int64_t, OutRef<float>, const DevState *,

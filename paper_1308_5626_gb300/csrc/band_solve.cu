@@ -441,6 +441,7 @@ __device__ __forceinline__ void down_seq(const LevelApply<T> &L, int k, const T 
 template <typename T, int B, int NT>
 __global__ void __launch_bounds__(NT) k_down0s(const T *__restrict__ v, const double *scale, const int *active,
                                                LevelApply<T> L, int64_t n) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");   // programmatic dependent: inputs complete
   if (active && *active == 0) return;
   constexpr int Q = kQ0;
   constexpr int SPAN = (Q + 1) * B;
@@ -536,6 +537,7 @@ __global__ void __launch_bounds__(NT) k_down0s(const T *__restrict__ v, const do
 template <typename T, int B, int NT>
 __global__ void __launch_bounds__(NT) k_up0s(const int *active, LevelApply<T> L, const T *solnext, OutRef<T> yref,
                                              double *X, int mode, int64_t n) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");   // programmatic dependent: inputs complete
   if (active && *active == 0) return;
   constexpr int Q = kQ0;
   constexpr int SPAN = (Q + 1) * B;
@@ -605,6 +607,7 @@ constexpr int kLevelCta = 64;   // groups per CTA of the level kernels
 
 template <typename T, int B>
 __global__ void __launch_bounds__(kLevelCta) k_down_level(const int *active, LevelApply<T> L, LevelApply<T> P) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");   // programmatic dependent: inputs complete
   if (active && *active == 0) return;
   extern __shared__ __align__(16) unsigned char bsm[];
   const int g = blockIdx.x * kLevelCta + threadIdx.x;
@@ -616,6 +619,7 @@ __global__ void __launch_bounds__(kLevelCta) k_down_level(const int *active, Lev
 
 template <typename T, int B>
 __global__ void __launch_bounds__(kLevelCta) k_up_level(const int *active, LevelApply<T> L, const T *solnext) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");   // programmatic dependent: inputs complete
   if (active && *active == 0) return;
   extern __shared__ __align__(16) unsigned char bsm[];
   const int g = blockIdx.x * kLevelCta + threadIdx.x;
@@ -664,6 +668,7 @@ __device__ __forceinline__ T *carve_s(unsigned char *&cur, size_t count) {
 
 template <typename T, int B>
 __global__ void __launch_bounds__(512) k_tail(const int *active, const LevelApply<T> *lv, int first, int last) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");   // programmatic dependent: inputs complete
   if (active && *active == 0) return;
   extern __shared__ __align__(16) unsigned char tail_smem[];
   __shared__ LevelApply<T> S[kMaxLevels];
@@ -1009,16 +1014,21 @@ static void apply_b(const BandSolver &bs, const std::vector<LevelApply<T>> &a, c
   constexpr int NT = level0_cta<T>();
   const int L = (int)a.size();
   const int g0 = (a[0].G + NT - 1) / NT;
-  k_down0s<T, B, NT><<<g0, NT, 0, s>>>(v, scale, active, a[0], bs.n);
+  // every kernel of the solve is a programmatic dependent of the one before it (each waits
+  // for its inputs before touching memory), so its CTAs are scheduled while that one drains
+  launch_pdl(k_down0s<T, B, NT>, dim3(g0), dim3(NT), 0, s, v, scale, active, a[0], bs.n);
   const int tf = bs.tail_first;
   for (int l = 1; l < tf && l < L; ++l)
-    k_down_level<T, B><<<(a[l].G + kLevelCta - 1) / kLevelCta, kLevelCta, down_stage_elems(kQ, B, kLevelCta) * sizeof(T),
-                         s>>>(active, a[l], a[l - 1]);
-  if (L > 1) k_tail<T, B><<<1, 512, bs.tail_smem_bytes(tf, L - 1, sizeof(T)), s>>>(active, dev, tf, L - 1);
+    launch_pdl(k_down_level<T, B>, dim3((a[l].G + kLevelCta - 1) / kLevelCta), dim3(kLevelCta),
+               (int)(down_stage_elems(kQ, B, kLevelCta) * sizeof(T)), s, active, a[l], a[l - 1]);
+  if (L > 1)
+    launch_pdl(k_tail<T, B>, dim3(1), dim3(512), (int)bs.tail_smem_bytes(tf, L - 1, sizeof(T)), s, active, dev, tf,
+               L - 1);
   for (int l = std::min(tf, L) - 1; l >= 1; --l)
-    k_up_level<T, B><<<(a[l].G + kLevelCta - 1) / kLevelCta, kLevelCta, up_stage_elems(kQ, B, kLevelCta) * sizeof(T),
-                       s>>>(active, a[l], a[l + 1].sol);
-  k_up0s<T, B, NT><<<g0, NT, 0, s>>>(active, a[0], L > 1 ? a[1].sol : nullptr, y, X, mode, bs.n);
+    launch_pdl(k_up_level<T, B>, dim3((a[l].G + kLevelCta - 1) / kLevelCta), dim3(kLevelCta),
+               (int)(up_stage_elems(kQ, B, kLevelCta) * sizeof(T)), s, active, a[l], (const T *)a[l + 1].sol);
+  launch_pdl(k_up0s<T, B, NT>, dim3(g0), dim3(NT), 0, s, active, a[0], (const T *)(L > 1 ? a[1].sol : nullptr), y, X,
+             mode, bs.n);
 }
 
 template <typename T>

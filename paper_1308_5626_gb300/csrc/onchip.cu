@@ -395,14 +395,17 @@ __device__ void oc_run(const OnChipDesc &d, OcShared &sh) {
       oc_reduce<T, 1>(ss, sh, sh.scal + 1, 1);
       if (tid == 0) {
         const double nu2 = sh.scal[1], a2 = sh.scal[2];
-        const bool brk = !(nu2 > kOcBreakdownRel * kOcBreakdownRel * a2) || !isfinite(nu2);
-        const double nu = brk ? 0.0 : sqrt(nu2);
+        // an overflowed ||U_k|| (a preconditioner whose solve blew up in the Krylov precision)
+        // is a numeric failure, not a breakdown: it must not end the cycle as if it converged
+        const bool bad = !isfinite(nu2) || !isfinite(a2);
+        const bool brk = !bad && !(nu2 > kOcBreakdownRel * kOcBreakdownRel * a2);
+        const double nu = (brk || bad) ? 0.0 : sqrt(nu2);
         double *hc = sh.H + (int64_t)k * kOcLdH;
         for (int i = 0; i <= k; ++i) hc[i] = sh.h[i] + sh.h2[i];
         hc[k + 1] = nu;
         const double Rk = oc_givens(sh, k);
         int fl = 0;
-        if (!isfinite(Rk)) fl |= kStNumeric;
+        if (!isfinite(Rk) || bad) fl |= kStNumeric;
         if (brk) fl |= kStBreakdown;
         if (!mixed && Rk <= eps_abs) fl |= kStConverged;
         sh.flag[0] = fl;

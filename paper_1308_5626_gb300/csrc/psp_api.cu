@@ -145,6 +145,12 @@ struct psp_ctx {
 
   cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};   // [0] N = I, [1] slot 0, [2] slot 1
   int graph_kernels[3] = {0, 0, 0};                          // kernel nodes per graph
+  // segment graphs: the cycle graph's body in a WHILE node, the restart loop on the device
+  cudaGraphExec_t seg_graph[3] = {nullptr, nullptr, nullptr};
+  int seg_kernels[3] = {0, 0, 0};    // kernel nodes of one cycle of the body
+  bool seg_ok = true;                // false once building a segment graph failed (per-cycle graphs then)
+  SegSummary *seg_dev = nullptr;     // device
+  SegSummary *seg_host = nullptr;    // pinned: [0] the launch's initial state, [1] the result
   bool profiling = false;
   bool restart_df_ok = false;        // the mixed cycle graphs hold the double-float restart
   cudaEvent_t ev[3][kMaxM][6] = {};                          // profiling events per graph
@@ -190,7 +196,7 @@ void set_coef(const psp_ctx *h, double dt, double (*coef)[2 * kMaxR + 1]) {
 }
 
 template <typename T>
-void enqueue_cycle(psp_ctx *h, int slot, cudaStream_t s) {
+void enqueue_cycle(psp_ctx *h, int slot, cudaStream_t s, bool summary_copy = true) {
   T *V = reinterpret_cast<T *>(h->V);
   T *Px = reinterpret_cast<T *>(h->Px);
   T *Py = reinterpret_cast<T *>(h->Py);
@@ -240,13 +246,13 @@ void enqueue_cycle(psp_ctx *h, int slot, cudaStream_t s) {
     launch_update_z<T>(g.n, V, h->ld, Z, h->X, 0, h->st, s);
     h->bs.apply<T>(slot, Z, nullptr, &h->st->k_end, fixed_out<T>(nullptr), h->X, 1, s);
   }
-  cudaMemcpyAsync(h->sum_host, &h->st->sum, sizeof(CycleSummary), cudaMemcpyDeviceToHost, s);
+  if (summary_copy) cudaMemcpyAsync(h->sum_host, &h->st->sum, sizeof(CycleSummary), cudaMemcpyDeviceToHost, s);
 }
 
 // One restart cycle of BiCGSTAB (FP64): the restart (true residual, restart pair), then m
 // iterations, each storing its two matvec pairs (scaled by 1/||r||) at ring columns
 // hist_base+1+2j and hist_base+2+2j; X is updated every iteration.
-void enqueue_bicgstab_cycle(psp_ctx *h, int slot, cudaStream_t s) {
+void enqueue_bicgstab_cycle(psp_ctx *h, int slot, cudaStream_t s, bool summary_copy = true) {
   double *V = reinterpret_cast<double *>(h->V);
   double *Px = reinterpret_cast<double *>(h->Px);
   double *Py = reinterpret_cast<double *>(h->Py);
@@ -279,7 +285,7 @@ void enqueue_bicgstab_cycle(psp_ctx *h, int slot, cudaStream_t s) {
                  ring_in<double>(Px, ld, &st->hist_base, h->mmax, c2),
                  ring_in<double>(Py, ld, &st->hist_base, h->mmax, c2), st, h->partial, s);
   }
-  cudaMemcpyAsync(h->sum_host, &h->st->sum, sizeof(CycleSummary), cudaMemcpyDeviceToHost, s);
+  if (summary_copy) cudaMemcpyAsync(h->sum_host, &h->st->sum, sizeof(CycleSummary), cudaMemcpyDeviceToHost, s);
 }
 
 psp_status capture(psp_ctx *h, int which) {
@@ -310,6 +316,71 @@ psp_status capture(psp_ctx *h, int which) {
 psp_status ensure_graph(psp_ctx *h, int which) {
   if (h->graph[which]) return PSP_OK;
   return capture(h, which);
+}
+
+// The segment graph of slot `which`: a WHILE conditional node whose body is one restart cycle
+// (the cycle graph's kernels, then k_seg_control, which sets the condition), followed by the
+// copy of the segment summary to the host.  Returns false (and leaves no graph) when the
+// runtime refuses any step of it; the caller then runs the per-cycle graphs.
+bool capture_segment(psp_ctx *h, int which) {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphConditionalHandle cond = 0;
+  cudaGraphNode_t loop = nullptr;
+  bool ok = cudaGraphCreate(&g, 0) == cudaSuccess &&
+            cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  cudaGraph_t body = nullptr;
+  if (ok) {
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = cond;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    ok = cudaGraphAddNode(&loop, g, nullptr, nullptr, 0, &p) == cudaSuccess;
+    if (ok) body = p.conditional.phGraph_out[0];
+  }
+  if (ok) {
+    ok = cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+         cudaSuccess;
+    if (ok) {
+      const int slot = which - 1;
+      if (h->opts.solver == PSP_SOLVER_BICGSTAB) enqueue_bicgstab_cycle(h, slot, h->cap, false);
+      else if (h->mixed) enqueue_cycle<float>(h, slot, h->cap, false);
+      else enqueue_cycle<double>(h, slot, h->cap, false);
+      launch_seg_control(h->st, h->seg_dev, cond, h->cap);
+      cudaGraph_t out = nullptr;
+      ok = cudaStreamEndCapture(h->cap, &out) == cudaSuccess;
+    }
+  }
+  if (ok) {
+    ok = cudaStreamBeginCaptureToGraph(h->cap, g, &loop, nullptr, 1, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      cudaMemcpyAsync(h->seg_host + 1, h->seg_dev, sizeof(SegSummary), cudaMemcpyDeviceToHost, h->cap);
+      cudaGraph_t out = nullptr;
+      ok = cudaStreamEndCapture(h->cap, &out) == cudaSuccess;
+    }
+  }
+  if (ok) {
+    size_t nn = 0;
+    cudaGraphGetNodes(body, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(body, nodes.data(), &nn);
+    int kn = 0;
+    for (size_t i = 0; i < nn; ++i) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kn;
+    }
+    h->seg_kernels[which] = kn;
+    ok = cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+  }
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    cudaGetLastError();   // a refused step must not surface as a later launch error
+    if (exec) cudaGraphExecDestroy(exec);
+    return false;
+  }
+  h->seg_graph[which] = exec;
+  return true;
 }
 
 // Factor band (device) into `slot`; returns PSP_ERR_NUMERIC on a failed pivot.
@@ -472,6 +543,7 @@ psp_status psp_default_opts(psp_opts *o) {
   o->cyclic = 0;
   o->solver = PSP_SOLVER_GMRES;
   o->onchip = -1;
+  o->cycle_loop = 1;
   return PSP_OK;
 }
 
@@ -524,6 +596,8 @@ psp_status psp_destroy(psp_handle h) {
   if (!h) return PSP_OK;
   for (auto &g : h->graph)
     if (g) cudaGraphExecDestroy(g);
+  for (auto &g : h->seg_graph)
+    if (g) cudaGraphExecDestroy(g);
   for (auto &a : h->ev)
     for (auto &b : a)
       for (auto &e : b)
@@ -531,12 +605,13 @@ psp_status psp_destroy(psp_handle h) {
   void *dev[] = {h->V, h->Px, h->Py, h->Z, h->X, h->B, h->partial, h->st, h->api_st, h->moments,
                  h->band_adopted, h->band_cand, h->dev_int, h->slot_mem[0], h->slot_mem[1], h->slot_mem[2],
                  h->band_T, h->Ab, h->Ab32, h->apply_mem, h->grad_dev,
-                 h->dev_un, h->dev_unp1, h->int_rhs, h->int_u1, h->oc_desc, h->oc_res};
+                 h->dev_un, h->dev_unp1, h->int_rhs, h->int_u1, h->oc_desc, h->oc_res, h->seg_dev};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (h->oc_desc_host) cudaFreeHost(h->oc_desc_host);
   if (h->oc_res_host) cudaFreeHost(h->oc_res_host);
   if (h->sum_host) cudaFreeHost(h->sum_host);
+  if (h->seg_host) cudaFreeHost(h->seg_host);
   if (h->st_host) cudaFreeHost(h->st_host);
   if (h->int_host) cudaFreeHost(h->int_host);
   if (h->hostbuf) cudaFreeHost(h->hostbuf);
@@ -670,6 +745,8 @@ psp_status psp_create(const psp_grid *grid, int order, const psp_term *terms, in
     if (ok) h->bs.bind_apply(h->apply_mem);
   }
   ok = ok && cudaMallocHost((void **)&h->sum_host, sizeof(CycleSummary)) == cudaSuccess;
+  ok = ok && cudaMallocHost((void **)&h->seg_host, 2 * sizeof(SegSummary)) == cudaSuccess;
+  ok = ok && dalloc((void **)&h->seg_dev, sizeof(SegSummary));
   ok = ok && cudaMallocHost((void **)&h->st_host, sizeof(DevState)) == cudaSuccess;
   ok = ok && cudaMallocHost((void **)&h->int_host, 64) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) == cudaSuccess;
@@ -1002,6 +1079,34 @@ psp_status run_segment(psp_ctx *h, int which, int max_cycles, Segment *out, int 
     *out = segment_of(*h->oc_res_host);
     *launches = 1;
     return PSP_OK;
+  }
+  if (h->opts.cycle_loop && h->seg_ok && !h->profiling) {
+    // the restart loop on the device: up to max_cycles cycles in one launch
+    if (!h->seg_graph[which] && !capture_segment(h, which)) h->seg_ok = false;
+    if (h->seg_ok) {
+      SegSummary init{};
+      init.max_cycles = max_cycles;
+      h->seg_host[0] = init;
+      PSP_CUDA(cudaMemcpyAsync(h->seg_dev, h->seg_host, sizeof(SegSummary), cudaMemcpyHostToDevice, s));
+      PSP_CUDA(cudaGraphLaunch(h->seg_graph[which], s));
+      PSP_CUDA(host_wait(h, s));
+      const SegSummary g = h->seg_host[1];
+      Segment sg;
+      sg.cycles = g.cycles;
+      sg.iters = g.iters;
+      sg.k_last = g.k_last;
+      sg.status = g.status;
+      sg.error = g.error;
+      sg.beta_first = g.first_beta;
+      sg.beta_last = g.last_beta;
+      sg.R_last = g.last_R;
+      sg.bnorm = g.bnorm;
+      sg.hist_count = g.hist_count;
+      sg.df_restart = h->mixed && h->restart_df_ok && h->st_host->restart_df;
+      *out = sg;
+      *launches = h->seg_kernels[which] * std::max(1, g.cycles);
+      return PSP_OK;
+    }
   }
   psp_status ps = ensure_graph(h, which);
   if (ps != PSP_OK) return ps;

@@ -71,7 +71,7 @@ struct DevState {
   float cAF[kMaxM];
   float cDF[kMaxM];
   float c3F[4];
-  int dc_brk;                         // breakdown seen by this iteration's scalar engine
+  int dc_brk;                         // this iteration's scalar engine saw 1: a breakdown, 2: an overflowed norm
   int pad2;
   // stencil coefficients of A = I - dt L for the current dt: coef[d][j + kMaxR]
   double coef[3][2 * kMaxR + 1];

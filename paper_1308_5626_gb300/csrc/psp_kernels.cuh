@@ -116,6 +116,39 @@ void launch_restart(const Geometry &g, const double *X, const double *B, TH *Px,
 bool launch_restart_mixed(const Geometry &g, const double *X, const double *B, float *Px, float *Py, int64_t ldh,
                           float *V1, float *Xh, float *Xl, DevState *st, double *partial, cudaStream_t s);
 
+// Launch `kernel` as a programmatic dependent of the previous kernel in the stream: its CTAs
+// may be scheduled while that kernel drains; the kernel itself must wait
+// (griddepcontrol.wait) before it touches memory.
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, int smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// cycle_loop.cu: the summary of one segment (up to max_cycles restart cycles in one graph
+// launch, the loop on the device), folded together from the cycles' summaries.
+struct SegSummary {
+  int cycles;       // cycles run
+  int iters;        // Arnoldi iterations of those cycles
+  int k_last;       // iterations of the last cycle
+  int status;       // kSt* bits of the last cycle, kStBreakdown if any cycle broke down
+  int error;        // internal error flag
+  int hist_count;   // history columns written since the history was cleared
+  int max_cycles;   // the segment's cycle budget (set by the host before the launch)
+  int pad;
+  double first_beta, last_beta, last_R, bnorm;
+};
+void launch_seg_control(const DevState *st, SegSummary *seg, cudaGraphConditionalHandle cond, cudaStream_t s);
+
 // arnoldi.cu
 int arnoldi_grid();   // CTAs of the Gram-Schmidt passes (one per SM)
 void arnoldi_setup(); // grid size and shared-memory attributes; call once outside capture

@@ -44,7 +44,7 @@ class psp_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("intercept", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("max_hist_cols", ctypes.c_int), ("inner_tol", ctypes.c_double), ("accept_rule", ctypes.c_int),
                 ("fuse_matvec", ctypes.c_int), ("adjoint", ctypes.c_int), ("cyclic", ctypes.c_int),
-                ("solver", ctypes.c_int), ("onchip", ctypes.c_int)]
+                ("solver", ctypes.c_int), ("onchip", ctypes.c_int), ("cycle_loop", ctypes.c_int)]
 
 
 class psp_step_info(ctypes.Structure):
@@ -368,12 +368,13 @@ def psp_get_profile(h, reset: bool = False) -> dict:
 # --------------------------------------------------------------------------------------
 
 def _opts(precision, intercept, max_restarts, max_hist_cols, inner_tol, accept_rule, fuse_matvec, adjoint, cyclic=0,
-          solver=0, onchip=-1):
+          solver=0, onchip=-1, cycle_loop=1):
     o = psp_default_opts()
     o.precision, o.intercept, o.max_restarts = int(precision), int(intercept), int(max_restarts)
     o.max_hist_cols, o.inner_tol, o.accept_rule = int(max_hist_cols), float(inner_tol), int(accept_rule)
     o.fuse_matvec, o.adjoint, o.cyclic, o.solver = int(fuse_matvec), int(adjoint), int(cyclic), int(solver)
     o.onchip = int(onchip)
+    o.cycle_loop = int(cycle_loop)
     return o
 
 
@@ -390,10 +391,10 @@ class Solver:
 
     def __init__(self, shape, order, terms, b, m, precision=PSP_FP64, intercept=1, max_restarts=200,
                  max_hist_cols=0, inner_tol=1e-5, accept_rule=1, fuse_matvec=1, adjoint=0, stream=None, cyclic=0,
-                 solver=0, onchip=-1):
+                 solver=0, onchip=-1, cycle_loop=1):
         import torch
         o = _opts(precision, intercept, max_restarts, max_hist_cols, inner_tol, accept_rule, fuse_matvec, adjoint,
-                  cyclic, solver, onchip)
+                  cyclic, solver, onchip, cycle_loop)
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s
         self.shape = tuple(int(v) for v in shape)
@@ -405,11 +406,12 @@ class Solver:
 
     @classmethod
     def banded(cls, A_band, w, b, m, precision=PSP_FP64, intercept=1, max_restarts=200, max_hist_cols=0,
-               inner_tol=1e-5, accept_rule=1, adjoint=0, stream=None, onchip=-1):
+               inner_tol=1e-5, accept_rule=1, adjoint=0, stream=None, onchip=-1, cycle_loop=1):
         """A solver whose operator is the explicit banded matrix A_band (device float64, n x (2w+1))."""
         import torch
         obj = cls.__new__(cls)
-        o = _opts(precision, intercept, max_restarts, max_hist_cols, inner_tol, accept_rule, 0, adjoint, 0, 0, onchip)
+        o = _opts(precision, intercept, max_restarts, max_hist_cols, inner_tol, accept_rule, 0, adjoint, 0, 0, onchip,
+                  cycle_loop)
         s = stream if stream is not None else torch.cuda.current_stream()
         obj.stream = s
         obj.n = A_band.numel() // (2 * int(w) + 1)

@@ -140,6 +140,26 @@ def test_3d_tiled_stencil_steps(dev, precision, onchip):
     s.close()
 
 
+@PATHS
+def test_overflowing_preconditioner_is_numeric(dev, onchip):
+    """An adopted N whose FP32 solve overflows ||A N^{-1} v||^2 (N = 1e-25 I) ends the mixed
+    step with PSP_ERR_NUMERIC at once.  Read as an Arnoldi breakdown instead, the overflow gave
+    a zero residual estimate, every cycle ended as converged, X never moved and the step ran
+    out of restarts; a fresh candidate of that kind passed the acceptance trial."""
+    import torch
+    from paper_1308_5626_gb300 import psp
+    w = inputs.c1(1000)
+    op = Operator(w.shape, w.order, w.terms)
+    s = _solver(w, precision=psp.PSP_MIXED, onchip=onchip, max_restarts=20)
+    band = np.zeros((w.n, 2 * w.b + 1))
+    band[:, w.b] = 1e-25
+    psp.psp_set_band(s.handle, t64(band, dev))
+    with pytest.raises(psp.PspError) as e:
+        s.step(t64(w.u0, dev), _dt(w, op), 1e-10)
+    assert e.value.status == psp.PSP_ERR_NUMERIC
+    s.close()
+
+
 @pytest.mark.parametrize("w", [inputs.c1(1000), inputs.c2(48, 40), inputs.c2(45, 40), inputs.c3(16, kmax=4),
                                _box3d()], ids=lambda w: w.name)
 def test_mixed_restart_double_float(dev, w):
