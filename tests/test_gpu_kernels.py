@@ -165,6 +165,35 @@ def test_fit_random(dev, n, b, M, intercept):
     s.close()
 
 
+def test_fit_fp32_history_wide_range(dev):
+    """FP32 history whose rows span 1e-18 .. 1e18 (every product of two entries stays a normal
+    FP32 value, as the double-float moments need): the row solves run in double-float on the
+    design scaled by a power of two, and the rows whose scaled design still leaves FP32's range
+    (1e-18 rows beside 1e18 rows) take the FP64 solve; both against the oracle, per row within
+    1e-9 plus the row's Gram condition number times 50 M 2^-46 (double-float rounding)."""
+    import torch
+    from paper_1308_5626_gb300 import psp
+    n, b, M = 3000, 3, 21
+    rng = np.random.default_rng(77)
+    scale = 10.0 ** rng.uniform(-18, 18, size=n)
+    scale[1000:1010] = 1e-18
+    scale[1010:1020] = 1e18
+    Px = (rng.standard_normal((n, M)) * scale[:, None]).astype(np.float32)
+    Py = (rng.standard_normal((n, M)) * scale[:, None]).astype(np.float32)
+    ref, sing = mrep.mrep(Px.astype(np.float64), Py.astype(np.float64), b, True)
+    s = psp.Solver((n,), 2, [(2, 0, 1.0)], b, 8)
+    out = torch.empty((n, 2 * b + 1), dtype=torch.float64, device=dev)
+    ns = psp.psp_fit_band(s.handle, t32(Px.T, dev), t32(Py.T, dev), out)
+    assert ns == int(sing.sum())
+    got = out.cpu().numpy()
+    for i in range(b, n - b):
+        P = np.vstack([np.ones(M), Px[i - b:i + b + 1].astype(np.float64)])
+        tol = 1e-9 + 50 * M * 2.0 ** -46 * np.linalg.cond(P @ P.T)
+        err = np.abs(got[i] - ref[i]).max() / max(np.abs(ref[i]).max(), 1e-300)
+        assert err <= tol, (i, err, tol)
+    s.close()
+
+
 def test_fit_ld_and_exact_recovery(dev):
     import torch
     from paper_1308_5626_gb300 import psp
