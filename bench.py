@@ -75,7 +75,17 @@ def _args():
     ap.add_argument("--n3", type=int, default=256, help="3D grid points per direction (default: the full workload)")
     ap.add_argument("--nx", type=int, default=1024, help="2D grid points per direction (default: the full workload)")
     ap.add_argument("--no-c2", action="store_true", help="skip the 2D workload's extra line")
-    return ap.parse_args()
+    ap.add_argument("--cycle-loop", type=int, default=1, choices=[0, 1],
+                    help="1 (default): the restart loop on the device (segment graphs); 0: one graph launch per "
+                         "cycle (ncu profiles no kernel inside a conditional graph body, so launch lists use 0)")
+    a = ap.parse_args()
+    global CYCLE_LOOP
+    CYCLE_LOOP = a.cycle_loop
+    return a
+
+
+# restart loop of the timed handles (--cycle-loop)
+CYCLE_LOOP = 1
 
 
 # --------------------------------------------------------------------------------------
@@ -249,7 +259,8 @@ def _time_form(w, precision, steps, warmup, device, world, profile, dt):
     from paper_1308_5626_gb300 import psp
     stream = torch.cuda.Stream(device=device)
     with torch.cuda.stream(stream):
-        solver = psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=precision, stream=stream)
+        solver = psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=precision, stream=stream,
+                            cycle_loop=CYCLE_LOOP)
         u = torch.tensor(w.u0, dtype=torch.float64, device=device)
         out = torch.empty_like(u)
         infos = []
@@ -576,7 +587,7 @@ def _batch_line(device, count: int, steps: int, nthreads: int, onchip: int = -1,
     for w in ws:
         s = torch.cuda.Stream(device=device)
         solvers.append(psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=psp.PSP_MIXED, stream=s,
-                                  onchip=onchip))
+                                  onchip=onchip, cycle_loop=CYCLE_LOOP))
         us.append(torch.tensor(w.u0, dtype=torch.float64, device=device))
         outs.append(torch.empty(w.n, dtype=torch.float64, device=device))
     t_create = time.perf_counter() - t0
@@ -624,7 +635,8 @@ def _e2e(w, precision, steps, device, dt):
     from paper_1308_5626_gb300 import psp
     stream = torch.cuda.Stream(device=device)
     with torch.cuda.stream(stream):
-        solver = psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=precision, stream=stream)
+        solver = psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=precision, stream=stream,
+                            cycle_loop=CYCLE_LOOP)
         a = torch.tensor(w.u0, dtype=torch.float64).pin_memory()
         b = torch.empty_like(a).pin_memory()
         for _ in range(2):
