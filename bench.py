@@ -75,9 +75,9 @@ def _args():
     ap.add_argument("--n3", type=int, default=256, help="3D grid points per direction (default: the full workload)")
     ap.add_argument("--nx", type=int, default=1024, help="2D grid points per direction (default: the full workload)")
     ap.add_argument("--no-c2", action="store_true", help="skip the 2D workload's extra line")
-    ap.add_argument("--cycle-loop", type=int, default=1, choices=[0, 1],
-                    help="1 (default): the restart loop on the device (segment graphs); 0: one graph launch per "
-                         "cycle (ncu profiles no kernel inside a conditional graph body, so launch lists use 0)")
+    ap.add_argument("--cycle-loop", type=int, default=0, choices=[0, 1],
+                    help="0 (default): one graph launch per restart cycle; 1: the restart loop on the device "
+                         "(segment graphs; ncu profiles no kernel inside a conditional graph body)")
     a = ap.parse_args()
     global CYCLE_LOOP
     CYCLE_LOOP = a.cycle_loop
@@ -85,7 +85,7 @@ def _args():
 
 
 # restart loop of the timed handles (--cycle-loop)
-CYCLE_LOOP = 1
+CYCLE_LOOP = 0
 
 
 # --------------------------------------------------------------------------------------
@@ -575,8 +575,9 @@ def _bicgstab_line(w, device, steps: int = 3):
 def _batch_line(device, count: int, steps: int, nthreads: int, onchip: int = -1, tune: bool = False):
     """The batched workload: `count` independent instances (inputs.c4_instance: 1D/2D, n from
     2^10 to 2^18, orders 2-8, b 1-4, CFL 1-20, mixed form, tol 1e-8), each on its own stream,
-    stepped together by psp_step_batch with `nthreads` host threads.  One untimed step
-    (graph captures), then `steps` timed batch steps: aggregate implicit steps/s over all
+    stepped together by psp_step_batch with `nthreads` host threads.  Two untimed steps
+    (graph captures, the first fits; after the autotuner's four measured calls when it is on),
+    then `steps` timed batch steps: aggregate implicit steps/s over all
     instances, and p50 / p99 of the per-instance step times (host wall clock)."""
     import statistics as st
     import torch
@@ -593,10 +594,11 @@ def _batch_line(device, count: int, steps: int, nthreads: int, onchip: int = -1,
     t_create = time.perf_counter() - t0
     hs = [s.handle for s in solvers]
     dts = [w.dt for w in ws]
-    # untimed: one step (graph captures, the first fits), and with the autotuner on, one step per
-    # candidate it measures for every size class
+    # untimed: with the autotuner on, one step per candidate it measures (4), then two steps on
+    # the executions it chose (the graph captures of the slots a first trial needs, the first
+    # fits); without it, the same two steps
     psp.psp_batch_tuner(1 if tune else 0)
-    for _ in range(1 + (4 if tune else 0)):
+    for _ in range(2 + (4 if tune else 0)):
         psp.psp_step_batch(hs, us, outs, dts, 1e-8, nthreads=nthreads, allow_noconv=True)
         us, outs = outs, us
     table = psp.psp_batch_tuner(-1) if tune else None

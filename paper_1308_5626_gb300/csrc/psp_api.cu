@@ -543,7 +543,7 @@ psp_status psp_default_opts(psp_opts *o) {
   o->cyclic = 0;
   o->solver = PSP_SOLVER_GMRES;
   o->onchip = -1;
-  o->cycle_loop = 1;
+  o->cycle_loop = 0;
   return PSP_OK;
 }
 
@@ -1134,8 +1134,10 @@ psp_status run_segment(psp_ctx *h, int which, int max_cycles, Segment *out, int 
 // first calls of psp_step_batch, every execution of a step -- the captured cycle graphs, and
 // the on-chip path with CTAs of 128, 256 and 512 threads (tile shapes of 4 rows per thread
 // at these sizes and up) -- one candidate per call for all instances of the class, and keeps
-// the one with the least measured time per Arnoldi iteration (each instance's time: its
-// device time on the on-chip path, its host wall time on the graph path).
+// the one whose calls had the least wall time per Arnoldi iteration of the whole batch.  The
+// classes share the GPU during a call, so one instance's own time (device time on the
+// on-chip path, host wall time on the graph path) does not show what its execution costs
+// the batch; the call's wall time does.
 constexpr int kTuneCands = 4;                      // graphs, on-chip 128 / 256 / 512
 constexpr int kTuneThreads[kTuneCands] = {0, 128, 256, 512};
 struct TuneClass {
@@ -1415,6 +1417,7 @@ psp_status psp_step_batch(psp_handle *hs, int count, const double *const *u_n, d
   std::vector<psp_status> sts(count, PSP_OK);
   // the tuner's plan for this call: every instance of a size class runs the class's candidate
   std::vector<int> cand(count, -1);
+  const auto t_call = std::chrono::steady_clock::now();
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     if (g_tune.on) {
@@ -1486,11 +1489,24 @@ psp_status psp_step_batch(psp_handle *hs, int count, const double *const *u_n, d
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     if (g_tune.on) {
+      // the call's wall time per Arnoldi iteration of all its instances, credited once to
+      // every class with the candidate it ran (a call with a failed instance is not counted)
+      const double wall = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_call).count();
+      double iters = 0.0;
+      bool all_ok = true;
       for (int i = 0; i < count; ++i) {
-        if (cand[i] < 0 || sts[i] != PSP_OK) continue;
-        TuneClass &tc = g_tune.cls[size_class(hs[i]->geo.n)];
-        tc.t[cand[i]] += secs[i];
-        tc.it[cand[i]] += std::max(1, inf[i].iters);
+        iters += std::max(1, inf[i].iters);
+        all_ok = all_ok && (sts[i] == PSP_OK || sts[i] == PSP_ERR_NOCONV);
+      }
+      std::vector<int> seen(32, -1);
+      for (int i = 0; i < count && all_ok; ++i) {
+        if (cand[i] < 0) continue;
+        const int c = size_class(hs[i]->geo.n);
+        if (seen[c] == cand[i]) continue;
+        seen[c] = cand[i];
+        TuneClass &tc = g_tune.cls[c];
+        tc.t[cand[i]] += wall;
+        tc.it[cand[i]] += iters;
         tc.cnt[cand[i]] += 1;
       }
       g_tune.calls += 1;

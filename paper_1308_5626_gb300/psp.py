@@ -368,7 +368,7 @@ def psp_get_profile(h, reset: bool = False) -> dict:
 # --------------------------------------------------------------------------------------
 
 def _opts(precision, intercept, max_restarts, max_hist_cols, inner_tol, accept_rule, fuse_matvec, adjoint, cyclic=0,
-          solver=0, onchip=-1, cycle_loop=1):
+          solver=0, onchip=-1, cycle_loop=0):
     o = psp_default_opts()
     o.precision, o.intercept, o.max_restarts = int(precision), int(intercept), int(max_restarts)
     o.max_hist_cols, o.inner_tol, o.accept_rule = int(max_hist_cols), float(inner_tol), int(accept_rule)
@@ -391,7 +391,7 @@ class Solver:
 
     def __init__(self, shape, order, terms, b, m, precision=PSP_FP64, intercept=1, max_restarts=200,
                  max_hist_cols=0, inner_tol=1e-5, accept_rule=1, fuse_matvec=1, adjoint=0, stream=None, cyclic=0,
-                 solver=0, onchip=-1, cycle_loop=1):
+                 solver=0, onchip=-1, cycle_loop=0):
         import torch
         o = _opts(precision, intercept, max_restarts, max_hist_cols, inner_tol, accept_rule, fuse_matvec, adjoint,
                   cyclic, solver, onchip, cycle_loop)
@@ -406,7 +406,7 @@ class Solver:
 
     @classmethod
     def banded(cls, A_band, w, b, m, precision=PSP_FP64, intercept=1, max_restarts=200, max_hist_cols=0,
-               inner_tol=1e-5, accept_rule=1, adjoint=0, stream=None, onchip=-1, cycle_loop=1):
+               inner_tol=1e-5, accept_rule=1, adjoint=0, stream=None, onchip=-1, cycle_loop=0):
         """A solver whose operator is the explicit banded matrix A_band (device float64, n x (2w+1))."""
         import torch
         obj = cls.__new__(cls)

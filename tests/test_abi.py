@@ -83,7 +83,7 @@ def test_opts_layout_matches_the_header(libpsp):
     assert all(b == 0xAB for b in bytes(buf)[size:])
     o = psp.psp_opts.from_buffer_copy(bytes(buf)[:size])
     assert o.adjoint == 0 and o.cyclic == 0 and o.solver == psp.PSP_SOLVER_GMRES
-    assert o.onchip == -1 and o.cycle_loop == 1
+    assert o.onchip == -1 and o.cycle_loop == 0
 
 
 def _create(shape, order=2, b=2, m=8, **opt):

@@ -140,6 +140,33 @@ def test_3d_tiled_stencil_steps(dev, precision, onchip):
     s.close()
 
 
+@pytest.mark.parametrize("precision,solver", [(0, 0), (1, 0), (0, 1)], ids=["fp64", "mixed", "bicgstab"])
+@pytest.mark.parametrize("w", [inputs.c1(1000), inputs.c2(48, 40), _box3d()], ids=lambda w: w.name)
+def test_segment_graphs_match_per_cycle_graphs(dev, w, precision, solver):
+    """The restart loop on the device (opts.cycle_loop = 1: a WHILE node runs cycle after
+    cycle, the host waits once per segment) gives bit-identical steps, iteration and cycle
+    counts and flags to one graph launch per cycle, over steps that fit, try and adopt
+    candidates."""
+    from paper_1308_5626_gb300 import psp
+    op = Operator(w.shape, w.order, w.terms)
+    dt = _dt(w, op)
+    tol = 1e-10
+    runs = []
+    for loop in (0, 1):
+        s = _solver(w, precision=precision, solver=solver, onchip=0, cycle_loop=loop)
+        u = t64(w.u0, dev)
+        got = []
+        for step in range(4):
+            u, info = s.step(u, dt, tol)
+            assert info.status == 0
+            got.append((u.cpu().numpy().copy(), info.iters, info.cycles, info.flags))
+        runs.append(got)
+        s.close()
+    for (u0, i0, c0, f0), (u1, i1, c1, f1) in zip(*runs):
+        assert (i0, c0, f0) == (i1, c1, f1)
+        assert np.array_equal(u0, u1)
+
+
 @PATHS
 def test_overflowing_preconditioner_is_numeric(dev, onchip):
     """An adopted N whose FP32 solve overflows ||A N^{-1} v||^2 (N = 1e-25 I) ends the mixed
