@@ -315,63 +315,7 @@ __device__ __forceinline__ bool chol_solve(double (&G)[Q][Q], double (&rhs)[Q], 
   return true;
 }
 
-// The same Cholesky solve in double-float on the FP32 pipe (the FP64 pipe is a small fraction
-// of it on GB300): G and rhs hold the design scaled by a power of two, so every entry lies in
-// FP32's range; about 48 significant bits.  Returns false if degenerate.
-template <int Q>
-__device__ __forceinline__ bool chol_solve_df(DF (&G)[Q][Q], DF (&rhs)[Q], int q) {
-  DF L[Q][Q], rd[Q];
-  const float rel = (float)kRelPivot;
-#pragma unroll
-  for (int j = 0; j < Q; ++j) {
-    if (j >= q) break;
-    DF d = G[j][j];
-#pragma unroll
-    for (int l = 0; l < Q; ++l) if (l < j) d = df_fms(d, L[j][l], L[j][l]);
-    if (!(G[j][j].hi > 0.0f) || !(d.hi > rel * G[j][j].hi)) return false;
-    const DF r = df_rsqrt(d);
-    L[j][j] = df_mul(d, r);
-    rd[j] = r;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      if (i > j && i < q) {
-        DF t = G[i][j];
-#pragma unroll
-        for (int l = 0; l < Q; ++l) if (l < j) t = df_fms(t, L[i][l], L[j][l]);
-        L[i][j] = df_mul(t, r);
-      }
-    }
-  }
-  DF z[Q];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    if (i < q) {
-      DF t = rhs[i];
-#pragma unroll
-      for (int l = 0; l < Q; ++l) if (l < i) t = df_fms(t, L[i][l], z[l]);
-      z[i] = df_mul(t, rd[i]);
-    }
-  }
-#pragma unroll
-  for (int i = Q - 1; i >= 0; --i) {
-    if (i < q) {
-      DF t = z[i];
-#pragma unroll
-      for (int l = 0; l < Q; ++l) if (l > i && l < q) t = df_fms(t, L[l][i], rhs[l]);
-      rhs[i] = df_mul(t, rd[i]);
-    }
-  }
-  return true;
-}
-
-// Exponent e of x = m 2^e, 1 <= |m| < 2 (x normal).
-__device__ __forceinline__ int exponent_of(double x) {
-  return (int)(((uint32_t)__double2hiint(x) >> 20) & 0x7ffu) - 1023;
-}
-
-// DFS: the interior rows' Cholesky in double-float (FP32 histories, whose moments carry about
-// 48 bits already); rows whose scaled design leaves FP32's range take the FP64 solve.
-template <int B, int INTERCEPT, bool DFS>
+template <int B, int INTERCEPT>
 __global__ void __launch_bounds__(128) k_fit_solve(int64_t n, int M, const double *__restrict__ mom,
                                                    double *__restrict__ band, int *singular_count, int cyclic) {
   constexpr int intercept = INTERCEPT;
@@ -392,68 +336,34 @@ __global__ void __launch_bounds__(128) k_fit_solve(int64_t n, int M, const doubl
     return mom + r * NM;
   };
   if (interior) {
+    double G[Q][Q], rhs[Q];
     const int o = intercept ? 1 : 0;
     const int q = W + o;
-    // the design of row i (lower triangle and diagonal, as the Cholesky reads them): entry
-    // (r, c) and the right-hand side, each through `put`
-    auto assemble = [&](auto &&put, auto &&put_rhs) {
-      if (intercept) {
-        put(0, 0, (double)M);
-#pragma unroll
-        for (int p = 0; p < W; ++p) put(1 + p, 0, mrow(p)[4 * B + 2]);
-        put_rhs(0, mi[4 * B + 3]);
-      }
+    if (intercept) {
+      G[0][0] = (double)M;
 #pragma unroll
       for (int p = 0; p < W; ++p) {
-#pragma unroll
-        for (int qq = 0; qq <= p; ++qq) put(o + p, o + qq, mrow(qq)[p - qq]);
-        put_rhs(o + p, mi[W + p]);
+        const double s = mrow(p)[4 * B + 2];
+        G[0][1 + p] = s;
+        G[1 + p][0] = s;
       }
-      if (!intercept) {
-        put(Q - 1, Q - 1, 1.0);
-        put_rhs(Q - 1, 0.0);
-      }
-    };
-    bool done = false;
-    if constexpr (DFS) {
-      // scale by 2^-shift, shift the largest exponent of the diagonal (exact; the solution
-      // is unchanged), then split every entry into an FP32 pair
-      int shift = intercept ? exponent_of((double)M) : -1022;
-#pragma unroll
-      for (int p = 0; p < W; ++p) {
-        const double dg = mrow(p)[0];
-        if (dg > 0.0) shift = max(shift, exponent_of(dg));
-      }
-      DF Gd[Q][Q], rd[Q];
-      bool inrange = true;
-#pragma unroll
-      for (int r = 0; r < Q; ++r) {
-        rd[r] = DF{0.0f, 0.0f};
-#pragma unroll
-        for (int c = 0; c < Q; ++c) Gd[r][c] = DF{0.0f, 0.0f};
-      }
-      assemble([&](int r, int c, double v) { split_double_scaled(v, shift, Gd[r][c].hi, Gd[r][c].lo, inrange); },
-               [&](int r, double v) { split_double_scaled(v, shift, rd[r].hi, rd[r].lo, inrange); });
-      if (inrange) {
-        ok = chol_solve_df<Q>(Gd, rd, q);
-#pragma unroll
-        for (int p = 0; p < W; ++p) out[p] = ok ? df_value(rd[o + p]) : (p == B ? 1.0 : 0.0);
-        done = true;
-      }
+      rhs[0] = mi[4 * B + 3];
     }
-    if (!done) {
-      double G[Q][Q], rhs[Q];
 #pragma unroll
-      for (int r = 0; r < Q; ++r) {
-        rhs[r] = 0.0;
+    for (int p = 0; p < W; ++p) {
 #pragma unroll
-        for (int c = 0; c < Q; ++c) G[r][c] = 0.0;
+      for (int qq = 0; qq < W; ++qq) {
+        const int lo = p < qq ? p : qq;
+        const int lag = p < qq ? qq - p : p - qq;
+        const double v = mrow(lo)[lag];
+        if (intercept) G[1 + p][1 + qq] = v; else G[p][qq] = v;
       }
-      assemble([&](int r, int c, double v) { G[r][c] = v; }, [&](int r, double v) { rhs[r] = v; });
-      ok = chol_solve<Q>(G, rhs, q);
-#pragma unroll
-      for (int p = 0; p < W; ++p) out[p] = ok ? rhs[o + p] : (p == B ? 1.0 : 0.0);
+      rhs[o + p] = mi[W + p];
     }
+    if (!intercept) { G[Q - 1][Q - 1] = 1.0; rhs[Q - 1] = 0.0; }
+    ok = chol_solve<Q>(G, rhs, q);
+#pragma unroll
+    for (int p = 0; p < W; ++p) out[p] = ok ? rhs[o + p] : (p == B ? 1.0 : 0.0);
   } else {
     double G[2][2], rhs[2];
     if (intercept) {
@@ -493,10 +403,8 @@ void launch_fit(int b, int intercept, int64_t n, int M, const TH *Px, const TH *
     } else {                                                                                     \
       k_fit_moments<TH, B_><<<g1, kFitRows, 0, s>>>(n, M, Px, Py, ld, moments, cyclic);          \
     }                                                                                            \
-    if (intercept) k_fit_solve<B_, 1, std::is_same<TH, float>::value><<<g2, 128, 0, s>>>(n, M, moments, band,   \
-                                                                                      singular_count, cyclic); \
-    else k_fit_solve<B_, 0, std::is_same<TH, float>::value><<<g2, 128, 0, s>>>(n, M, moments, band,             \
-                                                                               singular_count, cyclic);        \
+    if (intercept) k_fit_solve<B_, 1><<<g2, 128, 0, s>>>(n, M, moments, band, singular_count, cyclic); \
+    else k_fit_solve<B_, 0><<<g2, 128, 0, s>>>(n, M, moments, band, singular_count, cyclic);           \
     break;
     PSP_FIT(1) PSP_FIT(2) PSP_FIT(3) PSP_FIT(4)
 #undef PSP_FIT

@@ -167,10 +167,10 @@ def test_fit_random(dev, n, b, M, intercept):
 
 def test_fit_fp32_history_wide_range(dev):
     """FP32 history whose rows span 1e-18 .. 1e18 (every product of two entries stays a normal
-    FP32 value, as the double-float moments need): the row solves run in double-float on the
-    design scaled by a power of two, and the rows whose scaled design still leaves FP32's range
-    (1e-18 rows beside 1e18 rows) take the FP64 solve; both against the oracle, per row within
-    1e-9 plus the row's Gram condition number times 50 M 2^-46 (double-float rounding)."""
+    FP32 value, as the double-float moments need; neighbouring rows 36 decades apart give Gram
+    matrices far outside FP32's range, which the FP64 row solves take): against the oracle, per
+    row within 1e-9 plus the row's Gram condition number times 50 M 2^-46 (the moments'
+    double-float rounding)."""
     import torch
     from paper_1308_5626_gb300 import psp
     n, b, M = 3000, 3, 21
