@@ -153,6 +153,7 @@ struct psp_ctx {
   SegSummary *seg_host = nullptr;    // pinned: [0] the launch's initial state, [1] the result
   bool profiling = false;
   bool restart_df_ok = false;        // the mixed cycle graphs hold the double-float restart
+  double last_batch_s = 0.0;         // wall time of its last step on psp_step_batch's graph path
   cudaEvent_t ev[3][kMaxM][6] = {};                          // profiling events per graph
   psp_profile prof{};
   double *hostbuf = nullptr;   // pinned staging for psp_step_host
@@ -1374,6 +1375,7 @@ void step_batch_graphs(psp_ctx **hs, const std::vector<int> &idx, const double *
       psp_step_info info{};
       const psp_status st = psp_step(hs[i], u_n[i], u_np1[i], dt[i], tol, &info);
       const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      hs[i]->last_batch_s = sec;
       if (infos) infos[i] = info;
       if (seconds) seconds[i] = sec;
       if (statuses) statuses[i] = st;
@@ -1444,6 +1446,13 @@ psp_status psp_step_batch(psp_handle *hs, int count, const double *const *u_n, d
       gr.push_back(i);
     }
   }
+  // longest first (its last step's wall time, else its size): the host threads take the
+  // instances from a shared counter, so the long ones no longer start last and stretch the call
+  std::stable_sort(gr.begin(), gr.end(), [&](int a, int b) {
+    const double ka = hs[a]->last_batch_s > 0.0 ? hs[a]->last_batch_s : 1e-9 * (double)hs[a]->geo.n;
+    const double kb = hs[b]->last_batch_s > 0.0 ? hs[b]->last_batch_s : 1e-9 * (double)hs[b]->geo.n;
+    return ka > kb;
+  });
   std::atomic<int> first_err{(int)PSP_OK};
   std::atomic<bool> noconv{false};
   psp_status oc_status = PSP_OK;
