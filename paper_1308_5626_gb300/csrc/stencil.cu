@@ -946,6 +946,21 @@ void launch_restart(const Geometry &g, const double *X, const double *B, TH *Px,
                                                     g.nz, mixed, nullptr, 0, skip))));
 }
 
+// Grid of k_restart_df: one wave of resident CTAs.  The grid-stride loop then walks the grid
+// in lockstep, a few planes at a time, so every neighbour plane is in L2 when it is read; with
+// more CTAs than fit, the waves scatter over the grid and the neighbours come from DRAM again.
+template <int NDIM, int R>
+static int restart_df_grid(int64_t n) {
+  static const int resident = [] {   // thread-safe one-time initialisation
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_restart_df<NDIM, R>, kThreads, 0);
+    return std::max(1, sms) * std::max(1, per);
+  }();
+  return std::max(1, std::min(reduce_grid(n), resident));
+}
+
 // The mixed form's restart.  On stencil grids the double-float kernels take (k_split_x into
 // the scratch columns Xh and Xl, then k_restart_df) all three kernels are enqueued and
 // DevState::restart_df, set per step, picks the double-float pair or the FP64 kernel (the
@@ -964,8 +979,7 @@ bool launch_restart_mixed(const Geometry &g, const double *X, const double *B, f
   const int nvec = (int)(g.n / 4);
   const int gs = std::max(1, std::min((nvec + kThreads - 1) / kThreads, 152 * 8));
   k_split_x<<<gs, kThreads, 0, s>>>(X, Xh, Xl, nvec, st);
-  const int grid = reduce_grid(g.n);
-  PSP_DISPATCH_NDIM(g.ndim, PSP_DISPATCH_R(g.R, (k_restart_df<DD, RR><<<grid, kThreads, 0, s>>>(
+  PSP_DISPATCH_NDIM(g.ndim, PSP_DISPATCH_R(g.R, (k_restart_df<DD, RR><<<restart_df_grid<DD, RR>(g.n), kThreads, 0, s>>>(
                                                     Xh, Xl, B, Px, Py, ldh, V1, st, partial, g.nx, g.ny, g.nz))));
   launch_restart<float, float>(g, X, B, Px, Py, ldh, V1, st, partial, 1, s, &st->restart_df);
   return true;
