@@ -607,11 +607,17 @@ constexpr int kLevelCta = 64;   // groups per CTA of the level kernels
 
 template <typename T, int B>
 __global__ void __launch_bounds__(kLevelCta) k_down_level(const int *active, LevelApply<T> L, LevelApply<T> P) {
-  asm volatile("griddepcontrol.wait;" ::: "memory");   // programmatic dependent: inputs complete
-  if (active && *active == 0) return;
+  // the next level's CTAs may be placed now; the factor blocks (constant during the solve)
+  // are staged before the wait for the previous level's outputs, so the copies overlap it
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   extern __shared__ __align__(16) unsigned char bsm[];
   const int g = blockIdx.x * kLevelCta + threadIdx.x;
   const LevelApply<T> S = stage_down<T, B>(L, reinterpret_cast<T *>(bsm), kQ, g, kLevelCta);
+  asm volatile("griddepcontrol.wait;" ::: "memory");   // programmatic dependent: inputs complete
+  if (active && *active == 0) {
+    cp_async_wait_all();   // no copies left in flight when the CTA exits
+    return;
+  }
   cp_async_wait_all();
   __syncthreads();
   if (g < L.G) down_level_group<T, B, false>(S, P, g, kLevelCta, threadIdx.x);
@@ -619,11 +625,16 @@ __global__ void __launch_bounds__(kLevelCta) k_down_level(const int *active, Lev
 
 template <typename T, int B>
 __global__ void __launch_bounds__(kLevelCta) k_up_level(const int *active, LevelApply<T> L, const T *solnext) {
-  asm volatile("griddepcontrol.wait;" ::: "memory");   // programmatic dependent: inputs complete
-  if (active && *active == 0) return;
+  // as k_down_level: dependents placed now, the spikes staged before the wait
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   extern __shared__ __align__(16) unsigned char bsm[];
   const int g = blockIdx.x * kLevelCta + threadIdx.x;
   const LevelApply<T> S = stage_up<T, B>(L, reinterpret_cast<T *>(bsm), kQ, g, kLevelCta);
+  asm volatile("griddepcontrol.wait;" ::: "memory");   // programmatic dependent: inputs complete
+  if (active && *active == 0) {
+    cp_async_wait_all();   // no copies left in flight when the CTA exits
+    return;
+  }
   cp_async_wait_all();
   __syncthreads();
   if (g < L.G) up_level_group<T, B, false>(S, solnext, g, kLevelCta, threadIdx.x);
@@ -668,8 +679,9 @@ __device__ __forceinline__ T *carve_s(unsigned char *&cur, size_t count) {
 
 template <typename T, int B>
 __global__ void __launch_bounds__(512) k_tail(const int *active, const LevelApply<T> *lv, int first, int last) {
-  asm volatile("griddepcontrol.wait;" ::: "memory");   // programmatic dependent: inputs complete
-  if (active && *active == 0) return;
+  // dependents placed now; the levels' factors (constant during the solve) are staged before
+  // the wait for the level below, which is the only input written by the previous kernel
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   extern __shared__ __align__(16) unsigned char tail_smem[];
   __shared__ LevelApply<T> S[kMaxLevels];
   if (last - first + 1 > kMaxLevels) return;
@@ -693,6 +705,8 @@ __global__ void __launch_bounds__(512) k_tail(const int *active, const LevelAppl
     if (threadIdx.x == 0) S[l - first] = L;
   }
   __syncthreads();
+  asm volatile("griddepcontrol.wait;" ::: "memory");   // programmatic dependent: inputs complete
+  if (active && *active == 0) return;
   for (int l = first; l <= last; ++l) {
     const LevelApply<T> L = S[l - first];
     const LevelApply<T> P = (l == first) ? lv[l - 1] : S[l - 1 - first];
