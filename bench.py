@@ -574,8 +574,9 @@ def _bicgstab_line(w, device, steps: int = 3):
 
 def _batch_line(device, count: int, steps: int, nthreads: int, onchip: int = -1, tune: bool = False):
     """The batched workload: `count` independent instances (inputs.c4_instance: 1D/2D, n from
-    2^10 to 2^18, orders 2-8, b 1-4, CFL 1-20, mixed form, tol 1e-8), each on its own stream,
-    stepped together by psp_step_batch with `nthreads` host threads.  Two untimed steps
+    2^10 to 2^18, orders 2-8, b 1-4, CFL 1-20, mixed form, tol 1e-8), each handle given a
+    stream of torch's pool (shared by several handles), stepped together by psp_step_batch
+    with `nthreads` host threads.  Two untimed steps
     (graph captures, the first fits; after the autotuner's four measured calls when it is on),
     then `steps` timed batch steps: aggregate implicit steps/s over all
     instances, and p50 / p99 of the per-instance step times (host wall clock)."""
@@ -626,7 +627,7 @@ def _batch_line(device, count: int, steps: int, nthreads: int, onchip: int = -1,
                      "on-chip path's shared persistent launches with one CTA per system); per-instance time = host "
                      "wall time of its step (graphs) or device time of its cycles plus host time of its fit "
                      "(on-chip); aggregate from the host wall clock") if tune else
-                    ("concurrent per-instance cycle graphs on per-instance streams, driven by psp_step_batch's "
+                    ("concurrent per-instance cycle graphs on the streams of psp_step_batch's "
                      "host threads; host wall clock")}
 
 

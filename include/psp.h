@@ -223,9 +223,11 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
  * first one's precision) run the restart cycles of all their steps in shared persistent
  * launches, one CTA per system taken from a work counter, largest first, one launch per CTA
  * size and per round of the acceptance rule's decisions; the other handles are stepped
- * concurrently by nthreads host threads, each stepping one handle at a time on that handle's
- * stream, so up to nthreads instances' cycle graphs run on the GPU concurrently; handles
- * should therefore be created with distinct streams.  The batched launches take device and
+ * concurrently by nthreads host threads, each stepping one handle at a time on a stream of its
+ * own (created by the library on first use and kept), so up to nthreads instances' cycle
+ * graphs run on the GPU concurrently even where handles share a stream.  A handle's work in
+ * the call follows the work already enqueued on its stream, and work enqueued on that stream
+ * later follows it (event joins at both ends).  The batched launches take device and
  * pinned buffers made on the first such call (and grown for a larger batch).  infos, seconds
  * and statuses are host arrays of count entries or NULL; seconds is each instance's time:
  * host wall time of its step on the graph path, device time of its cycles (the GPU clock) plus

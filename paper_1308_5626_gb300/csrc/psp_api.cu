@@ -163,6 +163,10 @@ struct psp_ctx {
   // when it runs more threads than the host has cores
   bool blocking_wait = false;
   cudaEvent_t wait_ev = nullptr;
+  // psp_step_batch's graph path steps the handle on a stream of its own host thread; this
+  // event orders that work after the work already on the handle's stream, and later work on
+  // the handle's stream after it
+  cudaEvent_t join_ev = nullptr;
   // integrators (psp_step_bdf2, psp_step_sdirk2): right-hand side and first-stage vectors
   double *int_rhs = nullptr, *int_u1 = nullptr;
   int hist_count_host = 0;   // history columns at the end of the last step (0 after a clear)
@@ -618,6 +622,7 @@ psp_status psp_destroy(psp_handle h) {
   if (h->hostbuf) cudaFreeHost(h->hostbuf);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->wait_ev) cudaEventDestroy(h->wait_ev);
+  if (h->join_ev) cudaEventDestroy(h->join_ev);
   delete h;
   return PSP_OK;
 }
@@ -1341,9 +1346,30 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
 
 namespace {
 
+// Streams of psp_step_batch's host threads, one per thread and device, created on first use
+// and kept for the process: instances stepped at the same time never share a stream, whatever
+// streams their handles were given (a framework's pooled streams are often shared by many
+// handles, and instances on one stream would run one after another).
+bool batch_streams(int dev, int nt, std::vector<cudaStream_t> &out) {
+  static std::mutex mu;
+  static std::vector<std::vector<cudaStream_t>> per_dev;
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev < 0) return false;
+  if ((int)per_dev.size() <= dev) per_dev.resize(dev + 1);
+  std::vector<cudaStream_t> &v = per_dev[dev];
+  while ((int)v.size() < nt) {
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return false;
+    v.push_back(s);
+  }
+  out.assign(v.begin(), v.begin() + nt);
+  return true;
+}
+
 // The graph-path instances of a batch: nthreads host threads take them in order, each stepping
-// one handle at a time on that handle's own stream, so the GPU runs nthreads instances' cycle
-// graphs concurrently while each thread waits for its instance's cycle summaries.
+// one handle at a time on the thread's own stream (joined to the handle's stream by the
+// handle's event at both ends), so the GPU runs nthreads instances' cycle graphs concurrently
+// while each thread waits for its instance's cycle summaries.
 void step_batch_graphs(psp_ctx **hs, const std::vector<int> &idx, const double *const *u_n, double *const *u_np1,
                        const double *dt, double tol, int nthreads, psp_step_info *infos, double *seconds,
                        psp_status *statuses, std::atomic<int> &first_err, std::atomic<bool> &noconv) {
@@ -1352,6 +1378,18 @@ void step_batch_graphs(psp_ctx **hs, const std::vector<int> &idx, const double *
   int dev = 0;
   cudaGetDevice(&dev);
   const int nt = std::max(1, std::min(nthreads < 1 ? 1 : nthreads, count));
+  std::vector<cudaStream_t> ts;
+  bool ok = batch_streams(dev, nt, ts);
+  // the batch's work on a handle follows the work already enqueued on the handle's stream
+  for (int i : idx) {
+    ok = ok && (hs[i]->join_ev || cudaEventCreateWithFlags(&hs[i]->join_ev, cudaEventDisableTiming) == cudaSuccess);
+    ok = ok && cudaEventRecord(hs[i]->join_ev, hs[i]->stream) == cudaSuccess;
+  }
+  if (!ok) {
+    int expected = (int)PSP_OK;
+    first_err.compare_exchange_strong(expected, (int)PSP_ERR_CUDA);
+    return;
+  }
   // more threads than cores: the threads wait on blocking-sync events instead of spinning
   const unsigned cores = std::thread::hardware_concurrency();
   const bool block = cores > 0 && (unsigned)nt > cores;
@@ -1365,15 +1403,27 @@ void step_batch_graphs(psp_ctx **hs, const std::vector<int> &idx, const double *
     hs[i]->blocking_wait = block;
   }
   std::atomic<int> next{0};
-  auto work = [&]() {
+  auto work = [&](int t) {
     cudaSetDevice(dev);
+    const cudaStream_t s = ts[t];
     for (;;) {
       const int k = next.fetch_add(1);
       if (k >= count) break;
       const int i = idx[k];
+      psp_ctx *h = hs[i];
       const auto t0 = std::chrono::steady_clock::now();
       psp_step_info info{};
-      const psp_status st = psp_step(hs[i], u_n[i], u_np1[i], dt[i], tol, &info);
+      psp_status st = PSP_ERR_CUDA;
+      if (cudaStreamWaitEvent(s, h->join_ev, 0) == cudaSuccess) {
+        const cudaStream_t own = h->stream;
+        h->stream = s;
+        st = psp_step(h, u_n[i], u_np1[i], dt[i], tol, &info);
+        h->stream = own;
+        if (cudaEventRecord(h->join_ev, s) != cudaSuccess && (st == PSP_OK || st == PSP_ERR_NOCONV))
+          st = fail(PSP_ERR_CUDA, "psp_step_batch: cudaEventRecord failed");
+      } else {
+        st = fail(PSP_ERR_CUDA, "psp_step_batch: cudaStreamWaitEvent failed");
+      }
       const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       hs[i]->last_batch_s = sec;
       if (infos) infos[i] = info;
@@ -1388,10 +1438,17 @@ void step_batch_graphs(psp_ctx **hs, const std::vector<int> &idx, const double *
     }
   };
   std::vector<std::thread> pool;
-  for (int t = 1; t < nt; ++t) pool.emplace_back(work);
-  work();
+  for (int t = 1; t < nt; ++t) pool.emplace_back(work, t);
+  work(0);
   for (auto &th : pool) th.join();
-  for (int i : idx) hs[i]->blocking_wait = false;
+  for (int i : idx) {
+    hs[i]->blocking_wait = false;
+    // later work on the handle's stream follows the batch's
+    if (cudaStreamWaitEvent(hs[i]->stream, hs[i]->join_ev, 0) != cudaSuccess) {
+      int expected = (int)PSP_OK;
+      first_err.compare_exchange_strong(expected, (int)PSP_ERR_CUDA);
+    }
+  }
 }
 
 }  // namespace

@@ -1,10 +1,12 @@
 """GPU parity of the batched step (psp_step_batch): independent instances of the batched
-workload's recipe, each on its own stream, stepped together by a pool of host threads.
+workload's recipe, stepped together by a pool of host threads.
 
 * Every instance's result equals the exact solve of its own step (Fourier, oracle) within
   kappa * 2 tol (mixed form, tol 1e-8 as the batched configuration asks).
 * The batch is deterministic and free of cross-instance interference: each instance equals
   the same instance stepped alone by psp_step on a twin handle, to 1e-13.
+* Handles that share one stream still run concurrently and in order: the batch reads inputs
+  that were written on that stream behind a long kernel, without a host synchronisation.
 * A handle listed twice is refused (PSP_ERR_ARG) before any instance is stepped.
 """
 import numpy as np
@@ -61,6 +63,45 @@ def test_batch_matches_exact_and_single(dev, onchip):
             assert info.iters == infos[i].iters, (step, i)
             refs[i] = got
         us, outs = outs, us
+    for s in batch + twins:
+        s.close()
+
+
+def test_batch_on_one_shared_stream_follows_its_inputs(dev):
+    """All handles on one stream (as when a framework hands out pooled streams): the inputs are
+    written on that stream behind a ~25 ms spin kernel and the batch is called at once; every
+    instance must step the new inputs (the batch's work follows the stream's), equal to its
+    twin stepped alone, and later work on the stream must see the results."""
+    import torch
+    from paper_1308_5626_gb300 import psp
+    ws = [inputs.c4_instance(i, e_range=(9, 12)) for i in range(8)]
+    shared = torch.cuda.Stream(device=dev)
+    batch = [psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=psp.PSP_MIXED, stream=shared, onchip=0)
+             for w in ws]
+    twins = [psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=psp.PSP_MIXED, onchip=0) for w in ws]
+    src = [t64(w.u0, dev) for w in ws]
+    us = [torch.zeros_like(u) for u in src]
+    outs = [torch.empty_like(u) for u in src]
+    tol = 1e-8
+    torch.cuda.synchronize()
+    with torch.cuda.stream(shared):
+        torch.cuda._sleep(50_000_000)
+        for u, x in zip(us, src):
+            u.copy_(x)
+    infos, secs, sts = psp.psp_step_batch([s.handle for s in batch], us, outs, [w.dt for w in ws], tol, nthreads=4)
+    assert all(st == 0 for st in sts), sts
+    with torch.cuda.stream(shared):
+        copies = [o.clone() for o in outs]
+    torch.cuda.synchronize()
+    for i, w in enumerate(ws):
+        single, info = twins[i].step(src[i], w.dt, tol)
+        torch.cuda.synchronize()
+        got = copies[i].cpu().numpy()
+        assert rel(got, single.cpu().numpy()) <= 1e-13, i
+        assert info.iters == infos[i].iters, i
+        op = Operator(w.shape, w.order, w.terms)
+        ref = exact.solve_fourier(op, w.u0, w.dt)
+        assert rel(got, ref) <= exact.condition_number(op, w.dt) * 2 * tol, i
     for s in batch + twins:
         s.close()
 
