@@ -134,8 +134,8 @@ typedef struct {
                         launch and one host round trip per restart cycle.  Same iterates either
                         way; the profiling mode runs per cycle.  Falls back to 0 if the runtime
                         refuses the conditional graph.  Measured: no change on a 256^3 step,
-                        0.5% faster at 1024^2 (30 cycles per step), 40% slower aggregate for
-                        512 concurrent small instances (psp_step_batch). */
+                        0.5% faster at 1024^2 (30 cycles per step), 22-25% slower aggregate
+                        for 512 concurrent small instances (psp_step_batch). */
 } psp_opts;
 
 typedef struct {
