@@ -631,9 +631,11 @@ def _batch_line(device, count: int, steps: int, nthreads: int, onchip: int = -1,
                      "host threads; host wall clock")}
 
 
-def _e2e(w, precision, steps, device, dt):
+def _e2e(w, precision, steps, warmup, device, dt):
     """Same metric through the C ABI with host buffers: psp_step_host copies u^n from pinned
-    host memory to the device and u^{n+1} back every step."""
+    host memory to the device and u^{n+1} back every step.  The same window of the time
+    series as the device-timed line (`warmup` untimed steps from u^0, then `steps`), so the
+    two see the same iterations; the host wall clock around the timed steps."""
     import torch
     from paper_1308_5626_gb300 import psp
     stream = torch.cuda.Stream(device=device)
@@ -642,20 +644,22 @@ def _e2e(w, precision, steps, device, dt):
                             cycle_loop=CYCLE_LOOP)
         a = torch.tensor(w.u0, dtype=torch.float64).pin_memory()
         b = torch.empty_like(a).pin_memory()
-        for _ in range(2):
+        for _ in range(warmup):
             psp.psp_step_host(solver.handle, a, b, dt, w.tol)
             a, b = b, a
         torch.cuda.synchronize(device)
+        its = 0
         t0 = time.perf_counter()
         for _ in range(steps):
-            psp.psp_step_host(solver.handle, a, b, dt, w.tol)
+            info = psp.psp_step_host(solver.handle, a, b, dt, w.tol)
+            its += info.iters
             a, b = b, a
         torch.cuda.synchronize(device)
         dt_s = time.perf_counter() - t0
         solver.close()
     n = w.n
     return {"seconds": dt_s, "unit": "implicit steps/s", "h2d_bytes_per_step": 8 * n,
-            "d2h_bytes_per_step": 8 * n}
+            "d2h_bytes_per_step": 8 * n, "iters_per_step": its / max(steps, 1)}
 
 
 # --------------------------------------------------------------------------------------
@@ -921,7 +925,7 @@ def main():
 
     e2e = None
     if not a.no_e2e:
-        e = _e2e(w, psp.PSP_MIXED, a.steps, device, dt)
+        e = _e2e(w, psp.PSP_MIXED, a.steps, a.warmup, device, dt)
         secs = _max_over_ranks(e.pop("seconds"), world, device)
         e2e = {"value": world * a.steps / secs}
         e2e.update(e)
