@@ -21,11 +21,17 @@
  *    n x (2b+1) doubles: band[i*(2b+1) + p] = N(i, i + p - b).  Entries whose column
  *    falls outside [0, n) are ignored on input and written as 0 on output.
  *  - The library owns its workspace (Krylov basis, history ring, Hessenberg data, band
- *    factors) and allocates all of it in psp_create; no other call allocates device
- *    memory.
- *  - All device work is enqueued on the stream given to psp_create.  psp_step,
+ *    factors) and allocates it when the handle is created.  Some calls allocate more on
+ *    their first use and keep it: psp_step_host and the integrators (two n-vectors each),
+ *    and psp_step_batch (its batched-launch buffers and its host threads' streams);
+ *    psp_fit_band_static allocates nothing.
+ *  - All device work is enqueued on the stream given to psp_create, except on
+ *    psp_step_batch's graph path, which steps a handle on a stream of the library that is
+ *    joined to the handle's stream by events at both ends of the call.  psp_step,
  *    psp_fit_band*, psp_set_band and psp_step_host synchronise that stream before they
  *    return; the other calls are asynchronous.
+ *  - The host-side phases (psp_step, each segment of restart cycles, the fit, the batch
+ *    calls, psp_step_host) are marked by NVTX ranges for timeline tools.
  *  - No exception crosses the ABI.  A failing call returns a status other than PSP_OK
  *    and leaves a thread-local message for psp_last_error().
  *  - A handle must not be used by two host threads at once.

@@ -21,12 +21,24 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "band_solve.cuh"
 #include "onchip.cuh"
 
 namespace {
 
 thread_local std::string g_last_error;
+
+// A host-side NVTX range for the scope (a step, a segment of restart cycles, a fit, a batch):
+// a profiler's timeline shows the library's phases; without a tool attached a range costs a
+// branch.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 psp_status fail(psp_status s, const std::string &msg) {
   g_last_error = msg;
@@ -428,6 +440,7 @@ psp_status fit_into(psp_ctx *h, const TH *Px, const TH *Py, int64_t ld, int M, d
 // capacitance matrix) failed.
 template <typename TH>
 psp_status fit_and_factor(psp_ctx *h, const TH *Px, const TH *Py, int M, int slot, int *singular) {
+  NvtxRange range("psp_fit");
   PSP_CUDA(cudaMemsetAsync(h->dev_int, 0, 2 * sizeof(int), h->stream));
   launch_fit<TH>(h->b, h->opts.intercept, h->geo.n, M, Px, Py, h->ld, h->moments, h->band_cand, h->dev_int + 1,
                  h->stream, h->opts.cyclic);
@@ -1070,6 +1083,7 @@ Segment segment_of(const OnChipResult &o) {
 // One segment of handle h's step with slot `which`: one captured cycle graph, or an on-chip
 // launch of up to max_cycles cycles.  Returns the kernels launched in *launches.
 psp_status run_segment(psp_ctx *h, int which, int max_cycles, Segment *out, int *launches) {
+  NvtxRange range("psp_segment");
   cudaStream_t s = h->stream;
   if (h->onchip) {
     *h->oc_desc_host = onchip_desc(h, which, max_cycles, h->oc_res);
@@ -1220,6 +1234,7 @@ psp_status batch_buffers(int count) {
 // the steps run from nthreads host threads, each instance on its own stream.
 psp_status step_batch_onchip(psp_ctx **hs, int count, const double *const *u_n, double *const *u_np1, const double *dt,
                              double tol, int nthreads, psp_step_info *infos, double *seconds, psp_status *statuses) {
+  NvtxRange range("psp_batch_onchip");
   std::lock_guard<std::mutex> lock(g_batch_mu);
   psp_status bs = batch_buffers(count);
   if (bs != PSP_OK) return bs;
@@ -1328,6 +1343,7 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
   if (!(tol > 0.0) || !std::isfinite(dt)) return fail(PSP_ERR_ARG, "tol must be > 0 and dt finite");
   const int64_t n = h->geo.n;
   if ((u_n < u_np1 + n) && (u_np1 < u_n + n)) return fail(PSP_ERR_ARG, "u_n and u_np1 overlap");
+  NvtxRange range("psp_step");
   StepRun r;
   psp_status st = step_begin(h, r, u_n, u_np1, dt, tol);
   if (st != PSP_OK) return st;
@@ -1469,6 +1485,7 @@ psp_status psp_step_batch(psp_handle *hs, int count, const double *const *u_n, d
       return fail(PSP_ERR_ARG, "a handle appears twice in the batch");
   }
   if (count == 0) return PSP_OK;
+  NvtxRange range("psp_step_batch");
   // per-instance times and iterations are needed by the tuner even when the caller does not
   // ask for them
   std::vector<double> secs(count, 0.0);
@@ -1699,6 +1716,7 @@ psp_status psp_step_sdirk2(psp_handle h, const double *u_n, double *u_np1, doubl
 psp_status psp_step_host(psp_handle h, const double *u_n_host, double *u_np1_host, double dt, double tol,
                          psp_step_info *info) {
   if (!h || !u_n_host || !u_np1_host) return fail(PSP_ERR_ARG, "NULL argument");
+  NvtxRange range("psp_step_host");
   const int64_t n = h->geo.n;
   if (!h->dev_un) {
     if (cudaMalloc((void **)&h->dev_un, n * 8) != cudaSuccess || cudaMalloc((void **)&h->dev_unp1, n * 8) != cudaSuccess)
