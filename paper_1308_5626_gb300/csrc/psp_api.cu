@@ -182,6 +182,10 @@ struct psp_ctx {
   // integrators (psp_step_bdf2, psp_step_sdirk2): right-hand side and first-stage vectors
   double *int_rhs = nullptr, *int_u1 = nullptr;
   int hist_count_host = 0;   // history columns at the end of the last step (0 after a clear)
+  // the history length a rolled-back segment reached (a broken trial, a step with a
+  // non-finite residual): ring slots [count, hist_poison) mod mmax hold its pairs until
+  // later pairs overwrite them (0 after a clear)
+  int hist_poison = 0;
   // on-chip path (one CTA runs all cycles of a step): its descriptor and result
   bool onchip = false;
   int oc_threads = 256;        // CTA size of this system's on-chip launches
@@ -193,6 +197,15 @@ struct psp_ctx {
 namespace {
 
 // Wait for everything enqueued on s so far (see psp_ctx::blocking_wait).
+// History pairs valid at history length `count`: the last min(count, mmax), less the ring
+// slots that still hold the pairs of a rolled-back segment.  Those lie inside the ring's
+// valid window only once the ring has wrapped past them (hist_poison > mmax).
+int hist_valid(const psp_ctx *h, int count) {
+  int c = std::min(count, h->mmax);
+  if (h->hist_poison > h->mmax) c = std::min(c, std::max(0, count + h->mmax - h->hist_poison));
+  return c;
+}
+
 cudaError_t host_wait(psp_ctx *h, cudaStream_t s) {
   if (h->blocking_wait && h->wait_ev) {
     cudaError_t e = cudaEventRecord(h->wait_ev, s);
@@ -835,6 +848,7 @@ psp_status step_begin(psp_ctx *h, StepRun &r, const double *u_n, double *u_np1, 
     h->wait = 0;
     h->wait_len = 1;
     h->hist_count_host = 0;
+    h->hist_poison = 0;
     PSP_CUDA(cudaMemsetAsync(&h->st->hist_count, 0, sizeof(int), s));
   }
   set_coef(h, dt, h->st_host->coef);
@@ -896,6 +910,7 @@ psp_status step_after_segment(psp_ctx *h, StepRun &r, const Segment &sg, int lau
     r.flags |= PSP_FLAG_CANDIDATE_TRIED;
     r.flags &= ~PSP_FLAG_CANDIDATE_ACCEPTED;
     PSP_CUDA(cudaMemcpyAsync(h->X, r.u_n, n * 8, cudaMemcpyDeviceToDevice, s));
+    h->hist_poison = std::max(h->hist_poison, r.hist_count);
     h->int_host[3] = r.hist_before_trial;
     PSP_CUDA(cudaMemcpyAsync(&h->st->hist_count, h->int_host + 3, sizeof(int), cudaMemcpyHostToDevice, s));
     PSP_CUDA(host_wait(h, s));
@@ -961,8 +976,21 @@ psp_status step_after_segment(psp_ctx *h, StepRun &r, const Segment &sg, int lau
 psp_status step_finish(psp_ctx *h, StepRun &r, psp_step_info *info) {
   const int64_t n = h->geo.n;
   cudaStream_t s = h->stream;
-  if (r.main_iters > 0 && r.main_beta > 0.0) h->rate_ref = rate_of(r.main_R, r.main_beta, r.main_iters);
-  else if (r.trial_iters > 0 && r.trial_beta > 0.0) h->rate_ref = rate_of(r.trial_R, r.trial_beta, r.trial_iters);
+  if (r.numeric) {
+    // a step that ended with a non-finite residual keeps none of its matvec pairs (they would
+    // enter the next fit: the history length goes back to the one the step started with) and
+    // leaves the acceptance rule's reference rate as it was
+    if (r.hist_count != r.hist_before_trial) {
+      h->hist_poison = std::max(h->hist_poison, r.hist_count);
+      h->int_host[3] = r.hist_before_trial;
+      PSP_CUDA(cudaMemcpyAsync(&h->st->hist_count, h->int_host + 3, sizeof(int), cudaMemcpyHostToDevice, s));
+      r.hist_count = r.hist_before_trial;
+    }
+  } else if (r.main_iters > 0 && r.main_beta > 0.0) {
+    h->rate_ref = rate_of(r.main_R, r.main_beta, r.main_iters);
+  } else if (r.trial_iters > 0 && r.trial_beta > 0.0) {
+    h->rate_ref = rate_of(r.trial_R, r.trial_beta, r.trial_iters);
+  }
 
   if (r.adopted_now)
     PSP_CUDA(cudaMemcpyAsync(h->band_adopted, h->band_cand, (size_t)n * (2 * h->b + 1) * 8,
@@ -981,7 +1009,8 @@ psp_status step_finish(psp_ctx *h, StepRun &r, psp_step_info *info) {
   // a fit is only worth making when the next step tries it: while the acceptance rule's
   // back-off still runs (wait > 0) the next step keeps the adopted N, and the step after
   // it fits afresh from the longer history, so the skipped fit could never be used
-  if (!r.numeric && hist >= need && h->wait == 0) {
+  // (the fit reads ring slots [0, hist): none may still hold a rolled-back segment's pairs)
+  if (!r.numeric && hist >= need && h->wait == 0 && hist_valid(h, r.hist_count) == hist) {
     const int slot = (h->adopted == 0) ? 1 : 0;
     psp_status f2 = h->mixed ? fit_and_factor<float>(h, (const float *)h->Px, (const float *)h->Py, hist, slot,
                                                      &singular)
@@ -1832,7 +1861,7 @@ psp_status psp_get_history(psp_handle h, double *Px, double *Py, int64_t ld, int
   PSP_CUDA(cudaMemcpyAsync(h->int_host + 4, &h->st->hist_count, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   PSP_CUDA(cudaStreamSynchronize(h->stream));
   const int count = h->int_host[4];
-  const int c = std::min(count, h->mmax);
+  const int c = hist_valid(h, count);
   *cols = c;
   if (!Px || !Py) return PSP_OK;   // query only
   if (ld < h->geo.n || max_cols < c) return fail(PSP_ERR_ARG, "need ld >= n and max_cols >= the valid columns");
@@ -1966,6 +1995,7 @@ psp_status psp_reset(psp_handle h) {
   h->wait_len = 1;
   h->hist_dt = NAN;
   h->hist_count_host = 0;
+  h->hist_poison = 0;
   PSP_CUDA(cudaMemsetAsync(&h->st->hist_count, 0, sizeof(int), h->stream));
   PSP_CUDA(cudaStreamSynchronize(h->stream));
   return PSP_OK;

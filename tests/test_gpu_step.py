@@ -187,6 +187,56 @@ def test_overflowing_preconditioner_is_numeric(dev, onchip):
     s.close()
 
 
+@PATHS
+@pytest.mark.parametrize("hist", [400, None], ids=["ring400", "ring62"])
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_non_finite_input_is_numeric_and_the_handle_recovers(dev, precision, hist, onchip):
+    """Host-side fault injection: a NaN in u^n ends the step with PSP_ERR_NUMERIC (no hang, no
+    fault) and the failed step's matvec pairs never reach a fit: in a ring of 400 columns (room
+    for the two steps before it) the history holds what it held before the step; in the default
+    ring of 2(m+1) = 62 columns, which those steps have wrapped, the pairs it overwrote are
+    dropped too.  Every pair the handle reports is finite, and the next steps on valid data
+    still equal their exact solves (FP64: cond(A) 2 tol; mixed: 1e-8)."""
+    import torch
+    from paper_1308_5626_gb300 import psp
+    w = inputs.c1(1000)
+    op = Operator(w.shape, w.order, w.terms)
+    dt = _dt(w, op)
+    tol = 1e-10
+    bound = exact.condition_number(op, dt) * 2 * tol if precision == psp.PSP_FP64 else 1e-8
+    kw = {} if hist is None else {"max_hist_cols": hist}
+    s = _solver(w, precision=precision, onchip=onchip, **kw)
+    u = t64(w.u0, dev)
+    for _ in range(2):
+        u, info = s.step(u, dt, tol)
+        assert info.status == 0
+    cols = psp.psp_get_history(s.handle, w.n)[0].shape[0]
+    if hist is not None:
+        assert cols < hist   # the ring has room: the failed step overwrites no valid pair
+    bad = u.clone()
+    bad[7] = float("nan")
+    with pytest.raises(psp.PspError) as e:
+        s.step(bad, dt, tol)
+    assert e.value.status == psp.PSP_ERR_NUMERIC
+    Px, Py = psp.psp_get_history(s.handle, w.n)
+    if hist is not None:
+        assert Px.shape[0] == cols
+    else:
+        assert Px.shape[0] <= cols
+    assert bool(torch.isfinite(Px).all()) and bool(torch.isfinite(Py).all())
+    un = u.cpu().numpy()
+    for step in range(4):
+        u, info = s.step(u, dt, tol)
+        got = u.cpu().numpy()
+        assert info.status == 0, step
+        assert np.all(np.isfinite(got)), step
+        assert rel(got, exact.solve_fourier(op, un, dt)) <= bound, step
+        Px, Py = psp.psp_get_history(s.handle, w.n)
+        assert bool(torch.isfinite(Px).all()) and bool(torch.isfinite(Py).all()), step
+        un = got
+    s.close()
+
+
 @pytest.mark.parametrize("w", [inputs.c1(1000), inputs.c2(48, 40), inputs.c2(45, 40), inputs.c3(16, kmax=4),
                                _box3d()], ids=lambda w: w.name)
 def test_mixed_restart_double_float(dev, w):
