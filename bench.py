@@ -25,7 +25,8 @@ Arms
   iteration time to implicit steps/s by the oracle's own record of iterations and cycles
   per step of this workload.
 
-Multi-GPU: replicas (the step does not shard; see the design notes).  Every rank runs
+Multi-GPU: replicas (one step does not shard without a halo exchange per matvec and two
+allreductions per Arnoldi iteration).  Every rank runs
 its own copy of the workload; value = total steps of all ranks / max-over-ranks time.
 
 Timing: W untimed warm-up steps, then K steps between CUDA events on the solver's stream,

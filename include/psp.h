@@ -223,8 +223,8 @@ psp_status psp_step(psp_handle h, const double *u_n, double *u_np1, double dt, d
                     psp_step_info *info);
 
 /*
- * One implicit step of many independent handles (the batched form of the blueprint's
- * configuration 4): handle i steps u_n[i] -> u_np1[i] with dt[i] and the common tolerance
+ * One implicit step of many independent handles (a batch of independent systems, e.g.
+ * 512 1D and 2D grids of 2^10 to 2^18 points): handle i steps u_n[i] -> u_np1[i] with dt[i] and the common tolerance
  * tol, exactly as psp_step would.  The handles on the on-chip path (opts.onchip; those of the
  * first one's precision) run the restart cycles of all their steps in shared persistent
  * launches, one CTA per system taken from a work counter, largest first, one launch per CTA
@@ -396,7 +396,8 @@ psp_status psp_reset(psp_handle h);
  * 9, ...), and psp_step adds the device time of those that ran (k <= k_end) to a running
  * psp_profile,
  * together with each launch's algorithmic bytes (the reads and writes the operation needs
- * at least once: see the design notes).  psp_get_profile copies the running totals to
+ * at least once: (j+3) s n for pass A with the matvec folded in, (j+4) s n for pass B,
+ * (2b+3) s n for a band solve, s the element size).  psp_get_profile copies the running totals to
  * *out (host) and, if reset != 0, zeroes them. */
 psp_status psp_set_profiling(psp_handle h, int enable);
 

@@ -12,7 +12,7 @@ Written in the algorithm's own order and notation:
 * Q = H^{-1} G on the completed k x k triangle, Z = sum_j Q(j) V(:, j),
   X = X_0 + N^{-1} Z, X_0 = X; leave when the finish flag is set.
 
-Readings of passages the paper leaves open (listed with the others in the design notes):
+Readings of passages the paper leaves open:
 
 * Gram-Schmidt: the paper's loop is modified Gram-Schmidt (``gs="mgs"``).  ``gs="cgs2"``
   is classical Gram-Schmidt applied twice, equal in exact arithmetic.

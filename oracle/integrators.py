@@ -4,8 +4,7 @@ Test infrastructure: only the tests and the bench's CPU legs use this module.
 
 The paper advances with implicit Euler, whose building block is one solve of
 (I - dt L) x = rhs.  Two classical second-order integrators reuse exactly that solve, with
-another right-hand side and a scaled time step (not in the paper; the blueprint's fourth
-"next" row):
+another right-hand side and a scaled time step (not in the paper):
 
 * BDF2 (two-step backward differentiation):
       (I - 2/3 dt L) u^{n+1} = (4 u^n - u^{n-1}) / 3,

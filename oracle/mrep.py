@@ -11,7 +11,7 @@ is a least-squares fit of P_y(i, :) on rows of P_x:
   intercept; N*(j) for j >= 2 multiplies P_x(i - d + j - 2, :) and goes to
   N(i, i - d + j - 2).
 
-Readings (listed with the others in the design notes):
+Readings:
 
 * The printed scatter index N(i, i - j - d + 1) leaves the band (d = 1, j = 4 gives
   column i - 4); it is read as N(i, i - d + j - 2), the column of the regressor that

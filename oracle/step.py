@@ -1,7 +1,7 @@
 """One implicit-Euler step (Eq. 4) solved by Algorithm 1, with the progressive preconditioner.
 
 The step solves A u^{n+1} = u^n with A = I - dt L.  Readings of what the paper leaves
-open (listed with the others in the design notes):
+open:
 
 * X_0 = u^n and B = u^n; the first step runs with N = I (no fitted N exists yet).
 * tol is relative: eps = tol * ||u^n|| is handed to Algorithm 1 as its absolute bound.

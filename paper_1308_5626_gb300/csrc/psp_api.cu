@@ -866,7 +866,10 @@ psp_status step_begin(psp_ctx *h, StepRun &r, const double *u_n, double *u_np1, 
   PSP_CUDA(cudaMemcpyAsync(&h->st->first, &h->st_host->first, sizeof(int), cudaMemcpyHostToDevice, s));
   PSP_CUDA(cudaMemcpyAsync(h->B, u_n, n * 8, cudaMemcpyDeviceToDevice, s));
   PSP_CUDA(cudaMemcpyAsync(h->X, u_n, n * 8, cudaMemcpyDeviceToDevice, s));
-  // the first cycle may try the candidate (acceptance rule: see the design notes)
+  // the first cycle may try the candidate (the acceptance rule: a fresh candidate runs the
+  // step's first cycle and is adopted if that cycle converges or reduces the residual per
+  // iteration at least as fast as the last step's cycles did; else it is dropped and the
+  // next fit waits a number of steps that doubles with every rejection)
   r.try_cand = (h->cand >= 0 && h->wait == 0);
   if (!r.try_cand && h->wait > 0) h->wait -= 1;
   r.cur = r.try_cand ? h->cand : h->adopted;
