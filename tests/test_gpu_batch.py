@@ -7,6 +7,8 @@ workload's recipe, stepped together by a pool of host threads.
   the same instance stepped alone by psp_step on a twin handle, to 1e-13.
 * Handles that share one stream still run concurrently and in order: the batch reads inputs
   that were written on that stream behind a long kernel, without a host synchronisation.
+* FP64 and mixed handles in one batch: the batched on-chip launches take one precision, the
+  host threads step the rest, each still equal to its single step.
 * A handle listed twice is refused (PSP_ERR_ARG) before any instance is stepped.
 """
 import numpy as np
@@ -102,6 +104,46 @@ def test_batch_on_one_shared_stream_follows_its_inputs(dev):
         op = Operator(w.shape, w.order, w.terms)
         ref = exact.solve_fourier(op, w.u0, w.dt)
         assert rel(got, ref) <= exact.condition_number(op, w.dt) * 2 * tol, i
+    for s in batch + twins:
+        s.close()
+
+
+def test_batch_of_mixed_precisions(dev):
+    """FP64 and mixed handles in one batch, all asking for the on-chip path: the batched
+    on-chip launches take the first handle's precision, and the host threads step the other
+    handles one at a time on their own streams (psp_step, here each on its single-system
+    on-chip launch), both at once.  Every instance equals its twin stepped alone by psp_step
+    (to 1e-13; same iterations) and its exact solve (cond(A) 2 tol)."""
+    import torch
+    from paper_1308_5626_gb300 import psp
+    ws = [inputs.c4_spec(k % 2 == 1, 10 + k % 3, 2 + 2 * (k % 4), 1 + k % 4, 4.0 + k, seed=900 + k) for k in range(6)]
+    precs = [psp.PSP_FP64 if k % 2 == 0 else psp.PSP_MIXED for k in range(6)]
+
+    def make(w, p):
+        return psp.Solver(w.shape, w.order, w.terms, w.b, w.m, precision=p, stream=torch.cuda.Stream(device=dev),
+                          onchip=1)
+
+    batch = [make(w, p) for w, p in zip(ws, precs)]
+    twins = [make(w, p) for w, p in zip(ws, precs)]
+    us = [t64(w.u0, dev) for w in ws]
+    outs = [torch.empty_like(u) for u in us]
+    tol = 1e-8
+    for step in range(2):
+        torch.cuda.synchronize()
+        infos, secs, sts = psp.psp_step_batch([s.handle for s in batch], us, outs, [w.dt for w in ws], tol,
+                                              nthreads=3)
+        torch.cuda.synchronize()
+        assert all(st == 0 for st in sts), sts
+        for i, w in enumerate(ws):
+            got = outs[i].cpu().numpy()
+            single, info = twins[i].step(us[i], w.dt, tol)
+            torch.cuda.synchronize()
+            assert rel(got, single.cpu().numpy()) <= 1e-13, (step, i)
+            assert info.iters == infos[i].iters, (step, i)
+            op = Operator(w.shape, w.order, w.terms)
+            ref = exact.solve_fourier(op, us[i].cpu().numpy(), w.dt)
+            assert rel(got, ref) <= exact.condition_number(op, w.dt) * 2 * tol, (step, i)
+        us, outs = outs, us
     for s in batch + twins:
         s.close()
 
