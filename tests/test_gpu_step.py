@@ -187,12 +187,14 @@ def test_overflowing_preconditioner_is_numeric(dev, onchip):
     s.close()
 
 
-@PATHS
+@pytest.mark.parametrize("path", [{"onchip": 0}, {"onchip": 0, "cycle_loop": 1}, {"onchip": 1}],
+                         ids=["graphs", "segments", "onchip"])
 @pytest.mark.parametrize("hist", [400, None], ids=["ring400", "ring62"])
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
-def test_non_finite_input_is_numeric_and_the_handle_recovers(dev, precision, hist, onchip):
-    """Host-side fault injection: a NaN in u^n ends the step with PSP_ERR_NUMERIC (no hang, no
-    fault) and the failed step's matvec pairs never reach a fit: in a ring of 400 columns (room
+def test_non_finite_input_is_numeric_and_the_handle_recovers(dev, precision, hist, path):
+    """Host-side fault injection, on the per-cycle graphs, the segment graphs (the restart
+    loop on the device) and the on-chip path: a NaN in u^n ends the step with PSP_ERR_NUMERIC
+    (no hang, no fault) and the failed step's matvec pairs never reach a fit: in a ring of 400 columns (room
     for the two steps before it) the history holds what it held before the step; in the default
     ring of 2(m+1) = 62 columns, which those steps have wrapped, the pairs it overwrote are
     dropped too.  Every pair the handle reports is finite, and the next steps on valid data
@@ -204,8 +206,8 @@ def test_non_finite_input_is_numeric_and_the_handle_recovers(dev, precision, his
     dt = _dt(w, op)
     tol = 1e-10
     bound = exact.condition_number(op, dt) * 2 * tol if precision == psp.PSP_FP64 else 1e-8
-    kw = {} if hist is None else {"max_hist_cols": hist}
-    s = _solver(w, precision=precision, onchip=onchip, **kw)
+    kw = dict(path) if hist is None else dict(path, max_hist_cols=hist)
+    s = _solver(w, precision=precision, **kw)
     u = t64(w.u0, dev)
     for _ in range(2):
         u, info = s.step(u, dt, tol)
