@@ -73,6 +73,28 @@ def test_argument_errors_need_no_gpu(libpsp):
     assert psp.lib().psp_step(None, None, None, 0.1, 1e-8, None) == psp.PSP_ERR_ARG
 
 
+def test_batch_entry_points_without_gpu(libpsp):
+    """The batch call refuses NULL arrays, a negative count and a non-positive tolerance, and
+    an empty batch does nothing; the tuner's switch and report are host state (a fresh tuner
+    has measured no class) and an unknown mode is refused."""
+    from paper_1308_5626_gb300 import psp
+    L = psp.lib()
+    assert L.psp_step_batch(None, 1, None, None, None, 1e-8, 4, None, None, None) == psp.PSP_ERR_ARG
+    hs = (ctypes.c_void_p * 1)()
+    ui = (ctypes.c_void_p * 1)()
+    uo = (ctypes.c_void_p * 1)()
+    dts = (ctypes.c_double * 1)(0.1)
+    assert L.psp_step_batch(hs, -1, ui, uo, dts, 1e-8, 4, None, None, None) == psp.PSP_ERR_ARG
+    assert L.psp_step_batch(hs, 0, ui, uo, dts, 0.0, 4, None, None, None) == psp.PSP_ERR_ARG
+    assert L.psp_step_batch(hs, 1, ui, uo, dts, 1e-8, 4, None, None, None) == psp.PSP_ERR_ARG   # NULL handle
+    assert L.psp_step_batch(hs, 0, ui, uo, dts, 1e-8, 4, None, None, None) == psp.PSP_OK
+    k = ctypes.c_int(-1)
+    assert L.psp_batch_tuner(1, None, 0, ctypes.byref(k)) == psp.PSP_OK and k.value == 0
+    assert L.psp_batch_tuner(-1, None, 0, ctypes.byref(k)) == psp.PSP_OK and k.value == 0
+    assert L.psp_batch_tuner(0, None, 0, None) == psp.PSP_OK
+    assert L.psp_batch_tuner(2, None, 0, None) == psp.PSP_ERR_ARG
+
+
 def test_opts_layout_matches_the_header(libpsp):
     """psp_default_opts writes exactly the ctypes psp_opts: a C struct with a field the
     binding lacks would write past it (guard bytes), and the new options default to off."""
