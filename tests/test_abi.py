@@ -73,6 +73,28 @@ def test_argument_errors_need_no_gpu(libpsp):
     assert psp.lib().psp_step(None, None, None, 0.1, 1e-8, None) == psp.PSP_ERR_ARG
 
 
+NULL_HANDLE_CALLS = ["psp_default_opts", "psp_step", "psp_step_host", "psp_step_bdf2", "psp_step_sdirk2",
+                     "psp_matvec", "psp_matvec_f32", "psp_apply_L", "psp_fit_band", "psp_fit_band_f32",
+                     "psp_get_history", "psp_set_band", "psp_set_band_from", "psp_adjoint_grads", "psp_get_band",
+                     "psp_apply_precond", "psp_apply_precond_f32", "psp_get_stencil", "psp_reset",
+                     "psp_set_profiling", "psp_get_profile", "psp_last_cycle_residuals", "psp_fit_band_static",
+                     "psp_create_banded"]
+
+
+@pytest.mark.parametrize("name", NULL_HANDLE_CALLS)
+def test_null_arguments_are_refused_without_gpu(libpsp, name):
+    """Every entry point called with NULL pointers (and a NULL handle where it takes one)
+    returns PSP_ERR_ARG with a message, before touching the device; psp_destroy(NULL) is a
+    no-op that returns PSP_OK."""
+    from paper_1308_5626_gb300 import psp
+    fn = getattr(psp.lib(), name)
+    args = [0.1 if t is ctypes.c_double else (1 if t in (ctypes.c_int, ctypes.c_int64) else None)
+            for t in fn.argtypes]
+    assert fn(*args) == psp.PSP_ERR_ARG
+    assert len(psp.lib().psp_last_error()) > 0
+    assert psp.lib().psp_destroy(None) == psp.PSP_OK
+
+
 def test_batch_entry_points_without_gpu(libpsp):
     """The batch call refuses NULL arrays, a negative count and a non-positive tolerance, and
     an empty batch does nothing; the tuner's switch and report are host state (a fresh tuner
